@@ -1,0 +1,237 @@
+"""FP64 CPU oracle of the lattice Boltzmann stream-and-collide step.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+CPU-baseline leg of the benchmark, never by the library.  It shares no code,
+table or constant with the CUDA path.
+
+Contents:
+  lbm_oracle.c   the oracle proper (plain C, FP64, node by node; AB pull)
+  np_oracle.py   a second, independent NumPy formulation (push streaming with
+                 np.roll) used to pin the C oracle's streaming and walls
+  mlp_oracle.py  FP64 forward / backward / Adam of the alpha surrogate
+
+The C file is compiled by build() with plain flags (-O2, no fast-math, no FP
+contraction) into oracle/_lib/liboracle.so and loaded with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+# model / alpha-mode codes of the oracle's parameter block
+BGK, MRT, ELBM = 0, 1, 2
+NEWTON, SERIES_GUARDED, MLP_GUARDED, FIXED2 = 0, 1, 2, 3
+# per-node alpha outcomes
+AL_CONV, AL_SKIP, AL_CLAMP, AL_NOCONV, AL_FIXED, AL_GUARDED = range(6)
+
+# d'Humieres et al. (2002) D3Q19 rates: conserved moments 0, shear moments
+# (3pxx, pww, pxy, pyz, pxz) 1/tau, the rest their stabilising values.
+def default_mrt_rates(tau: float) -> np.ndarray:
+    w = 1.0 / tau
+    s = np.zeros(19)
+    s[1] = 1.19
+    s[2] = 1.4
+    s[4] = s[6] = s[8] = 1.2
+    s[9] = s[11] = s[13] = s[14] = s[15] = w
+    s[10] = s[12] = 1.4
+    s[16] = s[17] = s[18] = 1.98
+    return s
+
+
+class OracleParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("D", ctypes.c_int), ("model", ctypes.c_int), ("alpha_mode", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("feq_variant", ctypes.c_int),
+        ("nthreads", ctypes.c_int), ("guard_steps", ctypes.c_int),
+        ("tau", ctypes.c_double), ("force", ctypes.c_double * 3),
+        ("s", ctypes.c_double * 19), ("tol", ctypes.c_double),
+        ("skip_eps", ctypes.c_double), ("guard_tol", ctypes.c_double),
+        ("mlp", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile lbm_oracle.c into oracle/_lib/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        PP = ctypes.POINTER(OracleParams)
+        L.oracle_lattice.argtypes = [ctypes.c_int, ip, dp, ip]
+        L.oracle_feq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        L.oracle_mrt_matrix.argtypes = [dp, dp]
+        L.oracle_collide.argtypes = [PP, dp, dp, dp, dp]
+        L.oracle_elbm_g.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
+        L.oracle_elbm_alpha.argtypes = [PP, dp, dp, dp]
+        L.oracle_elbm_features.argtypes = [ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_mlp_guess.argtypes = [dp, dp]
+        L.oracle_mlp_guess.restype = ctypes.c_double
+        L.oracle_init.argtypes = [PP, dp, dp, dp]
+        L.oracle_run.argtypes = [PP, dp, dp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
+                                 dp, dp, dp, dp]
+        L.oracle_max_threads.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def Q_of(D: int) -> int:
+    return 9 if D == 2 else 19
+
+
+def lattice(D: int):
+    """(e [Q,3] int, w [Q], opp [Q]) in the oracle's enumeration order."""
+    Q = Q_of(D)
+    e = np.zeros((Q, 3), dtype=np.int32)
+    w = np.zeros(Q)
+    opp = np.zeros(Q, dtype=np.int32)
+    lib().oracle_lattice(D, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
+                         opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return e, w, opp
+
+
+def feq(D: int, rho: float, u, kind: int = 0) -> np.ndarray:
+    """kind 0 polynomial, 1 entropic product, 2 entropic with moments restored."""
+    uu = np.zeros(3)
+    uu[:len(u)] = u
+    out = np.zeros(Q_of(D))
+    r = lib().oracle_feq(D, kind, float(rho), _dp(uu), _dp(out))
+    assert r == 0
+    return out
+
+
+def mrt_matrix():
+    M = np.zeros((19, 19))
+    Mi = np.zeros((19, 19))
+    lib().oracle_mrt_matrix(_dp(M), _dp(Mi))
+    return M, Mi
+
+
+def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0),
+                s=None, alpha_mode=NEWTON, max_iter=20, feq_variant=0, tol=1e-12,
+                skip_eps=1e-3, guard_tol=1e-6, guard_steps=2, mlp=None, nthreads=0):
+    p = OracleParams()
+    p.nx, p.ny, p.nz, p.D, p.model = nx, ny, nz, D, model
+    p.alpha_mode, p.max_iter, p.feq_variant = alpha_mode, max_iter, feq_variant
+    p.nthreads, p.guard_steps = nthreads, guard_steps
+    p.tau = tau
+    for a in range(3):
+        p.force[a] = float(force[a]) if a < len(force) else 0.0
+    ss = default_mrt_rates(tau) if s is None else np.asarray(s, dtype=np.float64)
+    for k in range(19):
+        p.s[k] = float(ss[k])
+    p.tol, p.skip_eps, p.guard_tol = tol, skip_eps, guard_tol
+    if mlp is not None:
+        arr = np.ascontiguousarray(mlp, dtype=np.float64)
+        p._mlp_keep = arr  # keep alive with the struct
+        p.mlp = _dp(arr)
+    return p
+
+
+def collide(p: OracleParams, f) -> tuple:
+    """One node: returns (f_post, rho, v[3], info[alpha, evals, status, |g|/a2])."""
+    ff = np.array(f, dtype=np.float64)
+    rho = np.zeros(1)
+    v = np.zeros(3)
+    info = np.zeros(4)
+    r = lib().oracle_collide(ctypes.byref(p), _dp(ff), _dp(rho), _dp(v), _dp(info))
+    assert r == 0
+    return ff, rho[0], v, info
+
+
+def elbm_g(D, f, fe, alpha):
+    g = np.zeros(1)
+    gp = np.zeros(1)
+    lib().oracle_elbm_g(D, _dp(np.ascontiguousarray(f, dtype=np.float64)),
+                        _dp(np.ascontiguousarray(fe, dtype=np.float64)), float(alpha),
+                        _dp(g), _dp(gp))
+    return g[0], gp[0]
+
+
+def elbm_alpha(p: OracleParams, f, fe):
+    out = np.zeros(4)
+    lib().oracle_elbm_alpha(ctypes.byref(p), _dp(np.ascontiguousarray(f, dtype=np.float64)),
+                            _dp(np.ascontiguousarray(fe, dtype=np.float64)), _dp(out))
+    return out
+
+
+def elbm_features(D, f, fe):
+    feat = np.zeros(8)
+    ak = np.zeros(7)
+    lib().oracle_elbm_features(D, _dp(np.ascontiguousarray(f, dtype=np.float64)),
+                               _dp(np.ascontiguousarray(fe, dtype=np.float64)),
+                               _dp(feat), _dp(ak))
+    return feat, ak
+
+
+def mlp_guess(P, feat) -> float:
+    return lib().oracle_mlp_guess(_dp(np.ascontiguousarray(P, dtype=np.float64)),
+                                  _dp(np.ascontiguousarray(feat, dtype=np.float64)))
+
+
+def init(p: OracleParams, rho: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """F [Q, nz, ny, nx] = f_eq(rho, u); rho [nz,ny,nx], u [D,nz,ny,nx]."""
+    D = p.D
+    N = p.nx * p.ny * p.nz
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(N)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(D * N)
+    F = np.zeros((Q_of(D), p.nz, p.ny, p.nx))
+    r = lib().oracle_init(ctypes.byref(p), _dp(rho), _dp(u), _dp(F))
+    assert r == 0
+    return F
+
+
+def run(p: OracleParams, F: np.ndarray, nsteps: int, mask: np.ndarray | None = None,
+        want_alpha: bool = False):
+    """Advance F in place by nsteps.  Returns (rho, u, alpha|None, stats)."""
+    D = p.D
+    N = p.nx * p.ny * p.nz
+    assert F.shape == (Q_of(D), p.nz, p.ny, p.nx) and F.dtype == np.float64
+    assert F.flags.c_contiguous
+    tmp = np.empty_like(F)
+    rho = np.zeros((p.nz, p.ny, p.nx))
+    u = np.zeros((D, p.nz, p.ny, p.nx))
+    alpha = np.zeros((p.nz, p.ny, p.nx)) if want_alpha else None
+    stats = np.zeros(6)
+    mptr = None
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(N)
+        mptr = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    r = lib().oracle_run(ctypes.byref(p), _dp(F), _dp(tmp), mptr, int(nsteps), _dp(rho),
+                         _dp(u), _dp(alpha) if alpha is not None else None, _dp(stats))
+    assert r == 0
+    return rho, u, alpha, stats
+
+
+def max_threads(nthreads: int = 0) -> int:
+    return lib().oracle_max_threads(nthreads)
