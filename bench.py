@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the stream-and-collide hot path on GB300.
+
+Default workload (the headline metric): D3Q19 LBGK, FP32 arithmetic with
+FP32 shifted storage (f - w), 256^3 periodic Taylor-Green vortex, tau 0.6,
+u0 0.05.  One bench step = one lattice Boltzmann time step over all nodes
+(one fused stream-collide launch).  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tg256|duct|elbm|batch] [--dtype f32s|f16s|bf16s|f32]
+
+For N > 1 (torchrun) every rank runs an independent replica of the workload
+(the domains do not exchange data; weak scaling) and rank 0 reports the
+aggregate.  --impl reference times the FP64 CPU oracle on the host cores on a
+bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B_PER_NODE = {"f32s": 152, "f32": 152, "f16s": 76, "bf16s": 76, "f64": 304}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tg256", choices=["tg256", "duct", "elbm"])
+    ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--size", type=int, default=0,
+                    help="override the cube edge of the 256^3 workloads (profiling runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1311_2404_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, dtype):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since that capture; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(f"{workload}:{dtype}")
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def workload_spec(name, dtype, size=0):
+    spec = _workload_spec(name, dtype)
+    if size and name in ("tg256", "elbm"):
+        spec["n"] = (size, size, size)
+        spec["name"] = spec["name"].replace("256^3", f"{size}^3")
+    return spec
+
+
+def _workload_spec(name, dtype):
+    from paper_1311_2404_gb300 import lbm
+    dmap = {"f32s": lbm.LBM_F32S, "f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S,
+            "bf16s": lbm.LBM_BF16S}
+    if name == "tg256":
+        return dict(name="d3q19_lbgk_taylor_green_256^3", n=(256, 256, 256), lattice=lbm.LBM_D3Q19,
+                    model=lbm.LBM_BGK, tau=0.6, dtype=dmap[dtype], mask=None, force=(0, 0, 0))
+    if name == "duct":
+        return dict(name="d3q19_mrt_sphere_duct_512x256x256", n=(512, 256, 256),
+                    lattice=lbm.LBM_D3Q19, model=lbm.LBM_MRT, tau=0.55, dtype=dmap[dtype],
+                    mask="duct", force=(1e-5, 0, 0))
+    if name == "elbm":
+        return dict(name="d3q19_elbm_decaying_turbulence_256^3", n=(256, 256, 256),
+                    lattice=lbm.LBM_D3Q19, model=lbm.LBM_ELBM, tau=0.5005, dtype=dmap[dtype],
+                    mask=None, force=(0, 0, 0))
+    raise ValueError(name)
+
+
+def workload_inputs(spec):
+    from paper_1311_2404_gb300 import workloads as wl
+    nx, ny, nz = spec["n"]
+    if spec["name"].startswith("d3q19_lbgk_taylor"):
+        rho, u = wl.taylor_green(nx, 0.05, nz=nz, D=3)
+        mask = None
+    elif "duct" in spec["name"]:
+        mask, _ = wl.duct_with_spheres(nx, ny, nz)
+        rho = np.ones((nz, ny, nx))
+        u = np.zeros((3, nz, ny, nx))
+    else:
+        rho, u = wl.turbulence(nx)
+        mask = None
+    return rho.astype(np.float32), u.astype(np.float32), mask
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1311_2404_gb300 import lbm
+
+    spec = workload_spec(args.workload, args.dtype, args.size)
+    nx, ny, nz = spec["n"]
+    nodes = nx * ny * nz
+    rho, u, mask = workload_inputs(spec)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = lbm.Simulation(nx, ny, nz, spec["lattice"], spec["model"], spec["tau"],
+                             spec["dtype"], stream=stream.cuda_stream)
+        if mask is not None:
+            sim.set_geometry(mask)
+        if any(spec["force"]):
+            sim.set_force(*spec["force"])
+        rho_d = torch.from_numpy(rho).cuda()
+        u_d = torch.from_numpy(u).cuda()
+        lbm.lbm_init_equilibrium(sim.h, rho_d, u_d)      # inputs resident in HBM
+        stream.synchronize()
+        for _ in range(max(args.warmup, 3)):
+            lbm.lbm_step(sim.h, 1)
+        stream.synchronize()
+
+        sampler = ClockSampler(local) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = lbm.lbm_launch_count(sim.h)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lbm.lbm_step(sim.h, args.steps)                   # K fused launches
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = lbm.lbm_launch_count(sim.h) - l0
+        clocks = sampler.stop() if sampler else None
+        lbm.lbm_sync(sim.h)
+
+        # end to end through the public API with host buffers
+        pin_r = torch.from_numpy(rho).pin_memory()
+        pin_u = torch.from_numpy(u).pin_memory()
+        out_r = torch.empty_like(pin_r).pin_memory()
+        out_u = torch.empty_like(pin_u).pin_memory()
+        lbm.lbm_init_equilibrium(sim.h, pin_r, pin_u)
+        lbm.lbm_step(sim.h, 1)
+        lbm.lbm_get_macro(sim.h, out_r, out_u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            lbm.lbm_init_equilibrium(sim.h, pin_r, pin_u)
+            lbm.lbm_step(sim.h, 1)
+            lbm.lbm_get_macro(sim.h, out_r, out_u)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        sim.close()
+
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    glups = nodes * args.steps * world / (ms_max * 1e-3) / 1e9
+    per_launch_s = ms / 1e3 / args.steps
+    bpn = B_PER_NODE[args.dtype] + (1 if mask is not None else 0)
+    achieved = bpn * nodes / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = traffic_for(args.workload, args.dtype)
+    line = {
+        "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
+        "value": round(glups, 4),
+        "unit": "GLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms_max / args.steps, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f32s": "f32", "f32": "f32", "f16s": "f32", "bf16s": "f32"}[args.dtype],
+        "data": "synthetic (seeded analytic/random initial fields; no dataset)",
+        "config": {"workload": spec["name"], "lattice": "D3Q19",
+                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
+                   "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
+                         % (B_PER_NODE[args.dtype] * nodes / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": peak_kind, "bytes_per_node": bpn},
+        "e2e": {"value": round(nodes * world / (e2e_ms * 1e-3) / 1e9, 4), "unit": "GLUPS",
+                "h2d_bytes_per_step": int(rho.nbytes + u.nbytes),
+                "d2h_bytes_per_step": int(rho.nbytes + u.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, budget_s=12.0)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def _oracle_sample(spec, nz_s, ny_s=None):
+    import oracle
+    from paper_1311_2404_gb300 import workloads as wl
+    nx, ny, nz = spec["n"]
+    ny_s = ny_s or ny
+    model = {0: oracle.BGK, 1: oracle.MRT, 2: oracle.ELBM}[spec["model"]]
+    p = oracle.make_params(nx, ny_s, nz_s, D=3, model=model, tau=spec["tau"],
+                           force=spec["force"])
+    if spec["name"].startswith("d3q19_lbgk_taylor"):
+        rho, u = wl.taylor_green(nx, 0.05, nz=nz_s, D=3)
+        rho, u = rho[:, :ny_s].copy(), u[:, :, :ny_s].copy()
+        mask = None
+    elif "duct" in spec["name"]:
+        m, _ = wl.duct_with_spheres(nx, ny, nz)
+        mask = np.ascontiguousarray(m[:nz_s, :ny_s])
+        rho = np.ones((nz_s, ny_s, nx))
+        u = np.zeros((3, nz_s, ny_s, nx))
+    else:
+        r, uu = wl.turbulence(nx)
+        rho = np.ascontiguousarray(r[:nz_s, :ny_s])
+        u = np.ascontiguousarray(uu[:, :nz_s, :ny_s])
+        mask = None
+    F = oracle.init(p, rho, u)
+    return p, F, mask, nx * ny_s * nz_s
+
+
+def cpu_baseline(spec, budget_s=12.0, steps=None):
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads(0)
+    p, F, mask, n = _oracle_sample(spec, 1)
+    t0 = time.perf_counter()
+    oracle.run(p, F, 1, mask)
+    dt1 = time.perf_counter() - t0
+    nz_s = max(1, min(spec["n"][2], int(budget_s / 4 / max(dt1, 1e-6))))
+    p, F, mask, n = _oracle_sample(spec, nz_s)
+    nsteps = max(1, min(50, int(budget_s / max(dt1 * nz_s, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(p, F, nsteps, mask)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * nsteps / dt / 1e9, 6), "unit": "GLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{spec['n'][0]}x{spec['n'][1]}x{nz_s} slab of the workload, "
+                      f"{nsteps} steps, FP64 C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload_spec(args.workload, args.dtype, args.size)
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads(0)
+    # per-step sample sized so warmup + steps finish in about two minutes
+    p1, F1, m1, n1 = _oracle_sample(spec, 1)
+    t0 = time.perf_counter()
+    oracle.run(p1, F1, 1, m1)
+    plane_s = time.perf_counter() - t0
+    total_steps = max(args.steps, 1) + max(args.warmup, 0)
+    per_step_budget = 120.0 / total_steps
+    if per_step_budget >= plane_s:
+        nz_s, ny_s = max(1, min(spec["n"][2], int(per_step_budget / plane_s))), None
+    else:
+        nz_s, ny_s = 1, max(2, int(spec["n"][1] * per_step_budget / plane_s))
+    p, F, mask, n = _oracle_sample(spec, nz_s, ny_s)
+    if args.warmup > 0:
+        oracle.run(p, F, args.warmup, mask)
+    t0 = time.perf_counter()
+    oracle.run(p, F, args.steps, mask)
+    dt = time.perf_counter() - t0
+    glups = n * args.steps / dt / 1e9
+    sample = (f"{spec['n'][0]}x{ny_s or spec['n'][1]}x{nz_s} slab of the workload per step, "
+              f"FP64 C oracle")
+    line = {
+        "impl": "reference",
+        "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
+        "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded analytic/random initial fields; no dataset)",
+        "config": {"workload": spec["name"], "lattice": "D3Q19",
+                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
+                   "storage": "f64 (oracle)", "tau": spec["tau"],
+                   "nodes": spec["n"][0] * spec["n"][1] * spec["n"][2]},
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

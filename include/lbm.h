@@ -1,0 +1,291 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) lattice Boltzmann stream-and-collide
+ * library.
+ *
+ * The library advances the particle distributions f_i of a lattice Boltzmann
+ * fluid (Januszewski & Kostur, "Sailfish: a flexible multi-GPU implementation
+ * of the lattice Boltzmann method", Sec. 2) on one GPU.  One call to
+ * lbm_step() performs, per time step and per lattice node, the fused update
+ * of Algorithm cnp (Sec. 3.3): pull streaming from the previous step's
+ * post-collision array (AB pattern, Sec. 3.3), half-way bounce-back at solid
+ * nodes (Sec. 2.3), the macroscopic moments (Eq. lb_macro), the collision
+ * (LBGK Eq. lbgk, MRT Eq. mrt_collision or entropic ELBM Eqs. elbm and
+ * alpha_cond), the body force (Guo Eq. guo_force or EDM Eq. edm_force) and,
+ * on the last step of the call, the output of rho and v (Eq. edm_momentum).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an int status (LBM_OK = 0 on success).  On error
+ *    lbm_last_error(h) returns a message; the handle stays usable unless the
+ *    error is LBM_ECUDA from a sticky CUDA fault.
+ *  - Arrays crossing the ABI are dense, C-ordered, x fastest: scalar fields
+ *    [nz][ny][nx], vector fields [D][nz][ny][nx] (D = 2 for D2Q9, 3 for
+ *    D3Q19).  nz = 1 for D2Q9.
+ *  - Pointers may be host or device memory unless stated otherwise; the
+ *    library detects which with cudaPointerGetAttributes.  Host pointers are
+ *    copied synchronously before the call returns.  The library never keeps
+ *    a caller pointer beyond the call, except the memory given to
+ *    lbm_bind_memory and the stream given to lbm_set_stream.
+ *  - Work is enqueued on the handle's stream (lbm_set_stream; default: the
+ *    legacy default stream).  Calls that return data to a host pointer or
+ *    report device status synchronise that stream.
+ *  - The domain is periodic along every axis; walls come only from the mask.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,   /* bad argument: size <= 0, tau <= 1/2, unsupported combination */
+    LBM_ESTATE = 2,   /* wrong call order, e.g. lbm_step before lbm_init_equilibrium */
+    LBM_ENOMEM = 3,   /* device memory exhausted or bound memory too small */
+    LBM_ECUDA = 4,    /* CUDA runtime error (message holds cudaGetErrorString) */
+    LBM_ENAN = 5,     /* a non-finite rho or v was produced on an output step */
+    LBM_ETIMEOUT = 6, /* a bounded device wait gave up (batched persistent kernel) */
+    LBM_ENOCONV = 7   /* ELBM strict mode: some alpha solve hit the iteration cap */
+};
+
+/* ---- lattices, collision models, storage types ------------------------ */
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };          /* Sec. 2, Fig. lattices, Table bgkweights */
+enum { LBM_BGK = 0, LBM_MRT = 1, LBM_ELBM = 2 }; /* Eqs. lbgk, mrt_collision, elbm */
+/* Storage of f_i in device memory.  *_S types store f_i - w_i (the
+ * round-off-minimising form of Sec. 3.7); arithmetic is FP64 for LBM_F64 and
+ * FP32 for all others. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32S = 2, LBM_F16S = 3, LBM_BF16S = 4 };
+/* Element type of macroscopic-field arrays crossing the ABI. */
+enum { LBM_FIELD_F64 = 0, LBM_FIELD_F32 = 1 };
+/* ELBM alpha modes (Eq. alpha_cond).  NEWTON: safeguarded FP64 Newton from
+ * alpha = 2.  SERIES_GUARDED: second-order small-deviation series guess,
+ * then at most guard_steps FP64 Newton steps, full Newton if the last
+ * correction exceeds guard_tol.  MLP_GUARDED: same with the learned guess
+ * (lbm_load_alpha_mlp).  FIXED2: alpha = 2 (the LBGK limit; tests only). */
+enum { LBM_ALPHA_NEWTON = 0, LBM_ALPHA_SERIES_GUARDED = 1, LBM_ALPHA_MLP_GUARDED = 2,
+       LBM_ALPHA_FIXED2 = 3 };
+
+typedef struct lbm_ctx* lbm_handle;
+
+/* ---- creation ---------------------------------------------------------- */
+
+/* Create a simulation of nx x ny x nz nodes (nz = 1 for D2Q9) with the given
+ * lattice, collision model and relaxation time tau (nu = (2 tau - 1) / 6,
+ * Sec. 2 after Eq. lbgk), storing f_i as dtype.  Supported: every lattice /
+ * model / dtype combination except MRT on D2Q9.  ELBM requires tau > 1/2 and
+ * is the only model that accepts tau arbitrarily close to 1/2.
+ * No device memory is touched until the first call that needs it.
+ * Errors: LBM_EINVAL (sizes < 1, nz != 1 with D2Q9, tau <= 1/2, unknown
+ * enum, node count beyond 2^31 - 1).  *out is NULL on error; the message is
+ * then available from lbm_last_error(NULL). */
+LBM_API int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
+               lbm_handle* out);
+
+/* Free the handle and any device memory the library allocated itself
+ * (memory given to lbm_bind_memory stays the caller's).  NULL is a no-op. */
+LBM_API int lbm_destroy(lbm_handle h);
+
+/* Message of the last error on h (thread-local message for h == NULL). */
+LBM_API const char* lbm_last_error(lbm_handle h);
+
+/* ---- memory and stream ------------------------------------------------- */
+
+/* Bytes of device memory the handle needs: two copies of the distributions
+ * (AB pattern), the node-type map, the macroscopic fields, and a staging
+ * area for host transfers.  Valid right after lbm_create. */
+LBM_API size_t lbm_required_bytes(lbm_handle h);
+
+/* Use caller-owned device memory (at least lbm_required_bytes, 256-byte
+ * aligned) instead of allocating.  Must precede lbm_set_geometry and
+ * lbm_init_equilibrium.  The caller keeps it alive until lbm_destroy.
+ * Errors: LBM_ESTATE (memory already in use), LBM_ENOMEM (too small),
+ * LBM_EINVAL (NULL, misaligned or not device memory). */
+LBM_API int lbm_bind_memory(lbm_handle h, void* dev_ptr, size_t bytes);
+
+/* Enqueue all work on this cudaStream_t (NULL = legacy default stream). */
+LBM_API int lbm_set_stream(lbm_handle h, void* cuda_stream);
+
+/* ---- geometry and parameters ------------------------------------------ */
+
+/* Node types (Sec. 3.4, simplified to one boundary kind): mask[n] = 0 fluid,
+ * nonzero solid, nx*ny*nz bytes, dense.  Solid nodes are walls for half-way
+ * bounce-back (Sec. 2.3): a population that would stream out of a solid node
+ * is replaced by the opposite population of the receiving node.  Solid nodes
+ * are not updated and report rho = 0, v = 0.  The data are copied.
+ * Must precede lbm_init_equilibrium.  Default: no solid nodes. */
+LBM_API int lbm_set_geometry(lbm_handle h, const uint8_t* mask);
+
+/* Uniform body force density F (lattice units), Sec. 2.4.  LBGK and MRT use
+ * Guo's term (Eq. guo_force; in moment space with (I - S/2) for MRT), ELBM
+ * uses the EDM term (Eq. edm_force).  Default 0. */
+LBM_API int lbm_set_force(lbm_handle h, double fx, double fy, double fz);
+
+/* MRT relaxation rates s_k (Eq. mrt_collision) for the 19 moments of the
+ * orthogonal D3Q19 basis of d'Humieres et al. (2002), in their order: rho,
+ * e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx,
+ * my, mz.  q must be 19.  Default: 0 for conserved moments, 1/tau for the
+ * five stress moments, 1.19, 1.4, 1.2, 1.4, 1.98 for the others. */
+LBM_API int lbm_set_mrt_rates(lbm_handle h, const double* s, int q);
+
+/* ELBM alpha solve (Eq. alpha_cond): mode (LBM_ALPHA_*), Newton relative
+ * step tolerance tol (default 1e-12), Newton evaluation cap max_iter
+ * (default 20), near-equilibrium skip threshold skip_eps on max_i |x_i| with
+ * x_i = (f_eq_i - f_i) / f_i (default 1e-3; alpha = 2 below it).
+ * guard_steps / guard_tol are set by lbm_set_elbm_guard. */
+LBM_API int lbm_set_elbm(lbm_handle h, int alpha_mode, double tol, int max_iter, double skip_eps);
+
+/* Guarded modes: take guard_steps (1..4, default 2) Newton steps from the
+ * guess and accept when the last correction <= guard_tol * alpha (default
+ * 1e-6); otherwise fall back to the full Newton solve. */
+LBM_API int lbm_set_elbm_guard(lbm_handle h, int guard_steps, double guard_tol);
+
+/* ELBM entropic equilibrium form: 0 = product form with mass/momentum
+ * restored (default; exact minimiser on D2Q9), 1 = polynomial Eq. equilibrium. */
+LBM_API int lbm_set_elbm_feq(lbm_handle h, int variant);
+
+/* Load the alpha surrogate's parameters (n = 1394 floats, host or device,
+ * layout: mean[8], inv_std[8], W1[32][8], b1[32], W2[32][32], b2[32],
+ * W3[32], b3, scale).  Weight matrices are rounded to BF16 on load;
+ * accumulation is FP32.  Guess: alpha = 2 + scale * out * eps. */
+LBM_API int lbm_load_alpha_mlp(lbm_handle h, const float* params, int n);
+
+/* Request per-node alpha output (FP64, [nz][ny][nx]) on output steps
+ * (ELBM only); read with lbm_get_alpha.  Costs 8 B/node on output steps. */
+LBM_API int lbm_set_alpha_output(lbm_handle h, int on);
+
+/* Capture the n launches of lbm_step(h, n) in a CUDA graph and replay it on
+ * later calls with the same n (useful for small, launch-bound domains). */
+LBM_API int lbm_set_graph(lbm_handle h, int on);
+
+/* ---- initialisation and stepping -------------------------------------- */
+
+/* F = f_eq(rho, u) at every node (polynomial Eq. equilibrium for LBGK/MRT,
+ * the model's own equilibrium for ELBM) and t = 0.  rho [nz][ny][nx], u
+ * [D][nz][ny][nx], element type field_dtype.  Errors: LBM_EINVAL,
+ * LBM_ENOMEM, LBM_ECUDA. */
+LBM_API int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field_dtype);
+
+/* Advance n >= 1 time steps (asynchronous on the stream).  The last step
+ * writes rho and v (the force-shifted velocity of Eq. edm_momentum) of every
+ * node, computed from the post-streaming distributions of that step.
+ * In-kernel errors are reported by the next synchronising call. */
+LBM_API int lbm_step(lbm_handle h, int n);
+
+/* Steps taken since lbm_init_equilibrium / lbm_set_state. */
+LBM_API int lbm_get_time(lbm_handle h, long long* t);
+
+/* ---- readback ---------------------------------------------------------- */
+
+/* rho [nz][ny][nx] and v [D][nz][ny][nx] of the last step (either pointer
+ * may be NULL).  Solid nodes give 0.  Synchronises the stream; returns
+ * LBM_ENAN if a non-finite value was found, LBM_ESTATE before any step. */
+LBM_API int lbm_get_macro(lbm_handle h, void* rho, void* u, int field_dtype);
+
+/* Per-node alpha of the last output step (FP64, [nz][ny][nx]); requires
+ * lbm_set_alpha_output(h, 1) before the step. */
+LBM_API int lbm_get_alpha(lbm_handle h, double* alpha);
+
+/* FP64 sums over fluid nodes of the last step's fields, reduced on the GPU
+ * in a fixed order (bitwise reproducible): out[0] = sum rho,
+ * out[1..D] = sum rho v_a, out[D+1] = sum rho |v|^2 / 2.  out is host
+ * memory of D + 2 doubles.  Synchronises. */
+LBM_API int lbm_reduce(lbm_handle h, double* out);
+
+/* ELBM counters accumulated since init (host, 6 values): g evaluations,
+ * skipped nodes, clamped nodes, nodes at the iteration cap, nodes accepted
+ * from a guess, node updates.  Synchronises. */
+LBM_API int lbm_get_elbm_stats(lbm_handle h, double* out);
+
+/* Size in bytes of the raw state (the current distribution array). */
+LBM_API size_t lbm_state_bytes(lbm_handle h);
+
+/* Copy the raw state out / in (host or device pointer, lbm_state_bytes).
+ * The layout is internal; a state is only meaningful for a handle created
+ * with the same arguments.  set_state also sets the step counter to t. */
+LBM_API int lbm_get_state(lbm_handle h, void* dst, long long* t);
+LBM_API int lbm_set_state(lbm_handle h, const void* src, long long t);
+
+/* Synchronise the stream and return any pending device status. */
+LBM_API int lbm_sync(lbm_handle h);
+
+/* Number of kernels the handle has launched (for launch accounting). */
+LBM_API long long lbm_launch_count(lbm_handle h);
+
+/* ---- batched ensemble of independent D2Q9 domains ---------------------- */
+
+typedef struct lbm_batch_ctx* lbm_batch;
+
+/* ndom independent periodic D2Q9 LBGK domains of sizes nx[d] x ny[d] with
+ * relaxation times tau[d], storage dtype LBM_F32S or LBM_F16S.  All domains
+ * advance together in one persistent cooperative launch per lbm_batch_step
+ * call; that launch is captured in a CUDA graph and replayed. */
+LBM_API int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, int dtype,
+                     lbm_batch* out);
+LBM_API int lbm_batch_destroy(lbm_batch b);
+LBM_API const char* lbm_batch_last_error(lbm_batch b);
+LBM_API int lbm_batch_set_stream(lbm_batch b, void* cuda_stream);
+/* Mask of domain d (host or device, ny[d]*nx[d] bytes, 0 fluid). */
+LBM_API int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask);
+/* Guo body force of domain d. */
+LBM_API int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy);
+/* f = f_eq(rho, u) for domain d; rho [ny][nx], u [2][ny][nx]. */
+LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
+                               int field_dtype);
+/* Choose block size, tile shape and CTAs per SM by timing a few steps of
+ * each candidate (CUDA events); restores the state afterwards. */
+LBM_API int lbm_batch_autotune(lbm_batch b);
+/* Current launch configuration: threads per CTA, CTAs, tile width, tile rows. */
+LBM_API int lbm_batch_get_config(lbm_batch b, int* out4);
+/* Advance every domain n steps in one persistent launch.  The per-step
+ * grid barrier spins a bounded number of times; if it gives up, the kernel
+ * exits and the next synchronising call returns LBM_ETIMEOUT. */
+LBM_API int lbm_batch_step(lbm_batch b, int n);
+LBM_API int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype);
+LBM_API int lbm_batch_sync(lbm_batch b);
+LBM_API long long lbm_batch_launch_count(lbm_batch b);
+LBM_API size_t lbm_batch_nodes(lbm_batch b);
+
+/* ---- training the alpha surrogate --------------------------------------- */
+
+/* Collect (features, alpha) pairs from the handle's next output step: for
+ * every fluid node whose alpha was solved by full Newton (not skipped, not
+ * clamped), the 8 invariant features (FP32) and the converged alpha (FP64).
+ * Requires an ELBM handle.  Writes at most cap pairs to device buffers X
+ * [cap][8] and y [cap]; *count receives the number written.  The sampling is
+ * deterministic (every stride-th eligible node). */
+LBM_API int lbm_elbm_collect_pairs(lbm_handle h, int stride, float* X_dev, double* y_dev, int cap,
+                           int* count);
+
+/* Train the surrogate on n pairs (device X [n][8] FP32, alpha [n] FP64) with
+ * minibatch Adam entirely on the GPU (forward, backward and update kernels).
+ * params (host, 1394 floats) holds the initial parameters (mean, inv_std and
+ * scale are kept fixed) and receives the trained ones.  cfg = {epochs,
+ * batch, lr, seed}; loss_out (host, epochs floats) receives the mean loss
+ * per epoch.  Synchronises. */
+LBM_API int lbm_mlp_train(const float* X_dev, const double* alpha_dev, int n, const double* cfg,
+                  float* params, float* loss_out, void* cuda_stream);
+
+/* One forward+backward pass on a batch (device X [n][8], device targets
+ * t [n]), for checking gradients: writes the loss and the gradient of every
+ * parameter (host, 1394 floats; zeros for fixed entries).  Synchronises. */
+LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const float* params,
+                 float* loss, float* grad, void* cuda_stream);
+
+/* Forward pass only: alpha guesses for n feature rows (device in and out). */
+LBM_API int lbm_mlp_forward(const float* X_dev, int n, const float* params, float* alpha_dev,
+                    void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,9 @@
+// Instantiations of the stream-and-collide kernel for the ELBM collision model.
+#include "step_kernel.cuh"
+
+namespace lbm {
+cudaError_t launch_step_elbm(int lattice, int store, const StepParams& p, bool mask, cudaStream_t s)
+{
+    return launch_step_model<MODEL_ELBM>(lattice, store, p, mask, s);
+}
+}  // namespace lbm

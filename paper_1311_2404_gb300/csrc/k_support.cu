@@ -1,0 +1,260 @@
+// Support kernels around the step: node-type map, equilibrium initialisation,
+// field packing to dense caller layout, and deterministic FP64 reductions.
+#include "collide.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Node-type map (Sec. 3.4, reduced to fluid / solid): bit 0 solid, bit 1 a
+// fluid node with at least one solid upstream neighbour (the only nodes that
+// need the bounce-back check).  dense: [nz][ny][nx]; flags: padded rows.
+// ---------------------------------------------------------------------------
+template <class L>
+__global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__ flags, int nx,
+                        int ny, int nz, int nxp)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nxp) return;
+    const size_t out = ((size_t)z * ny + y) * nxp + x;
+    if (x >= nx) {
+        flags[out] = FLAG_SOLID;  // padding never updates
+        return;
+    }
+    auto at = [&](int xx, int yy, int zz) {
+        xx = (xx + nx) % nx;
+        yy = (yy + ny) % ny;
+        zz = (zz + nz) % nz;
+        return dense[((size_t)zz * ny + yy) * nx + xx] != 0;
+    };
+    const bool solid = at(x, y, z);
+    bool near = false;
+    if (!solid)
+        for (int i = 1; i < L::Q; ++i) near |= at(x - L::ex(i), y - L::ey(i), z - L::ez(i));
+    flags[out] = (solid ? FLAG_SOLID : 0) | (near ? FLAG_NEAR_WALL : 0);
+}
+
+cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, int nx, int ny,
+                         int nz, int nxp, cudaStream_t s)
+{
+    dim3 block(128), grid((nxp + 127) / 128, ny, nz);
+    if (lattice == 0)
+        k_flags<D2Q9><<<grid, block, 0, s>>>(dense, flags, nx, ny, nz, nxp);
+    else
+        k_flags<D3Q19><<<grid, block, 0, s>>>(dense, flags, nx, ny, nz, nxp);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// F = f_eq(rho, u) (polynomial, or the entropic form for ELBM) at every node.
+// rho [nz][ny][nx], u [D][nz][ny][nx] dense, element type FT.
+// ---------------------------------------------------------------------------
+template <class L, class S, class FT>
+__global__ void k_init(const FT* __restrict__ rho, const FT* __restrict__ u, void* Aout, int nx,
+                       int ny, int nz, int nxp, long long sq, int entropic, int feq_variant)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nxp) return;
+    typename S::T* A = static_cast<typename S::T*>(Aout);
+    const size_t n = ((size_t)z * ny + y) * nxp + x;
+    double r = 1.0, uu[3] = {0, 0, 0};
+    if (x < nx) {
+        const size_t nd = ((size_t)z * ny + y) * nx + x;
+        const size_t N = (size_t)nx * ny * nz;
+        r = (double)rho[nd];
+        for (int a = 0; a < L::D; ++a) uu[a] = (double)u[a * N + nd];
+    }
+    double dev[L::Q];   // f_eq - w
+    if (entropic) {
+        elbm_feq<L>(r, uu, feq_variant, dev);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) dev[i] -= L::w(i);
+    } else {
+        // Eq. equilibrium in deviation form: w (rho - 1 + rho (3 eu + 9/2 eu^2 - 3/2 u^2))
+        const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double eu = L::ex(i) * uu[0] + L::ey(i) * uu[1] + L::ez(i) * uu[2];
+            dev[i] = L::w(i) * ((r - 1.0) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        A[(size_t)i * sq + n] = S::encode((typename S::R)dev[i], L::w(i));
+}
+
+template <class L, class S>
+static cudaError_t init_t(const void* rho, const void* u, int field_f32, void* A, int nx, int ny,
+                          int nz, int nxp, long long sq, int entropic, int feq_variant,
+                          cudaStream_t s)
+{
+    dim3 block(128), grid((nxp + 127) / 128, ny, nz);
+    if (field_f32)
+        k_init<L, S, float><<<grid, block, 0, s>>>((const float*)rho, (const float*)u, A, nx, ny,
+                                                   nz, nxp, sq, entropic, feq_variant);
+    else
+        k_init<L, S, double><<<grid, block, 0, s>>>((const double*)rho, (const double*)u, A, nx,
+                                                    ny, nz, nxp, sq, entropic, feq_variant);
+    return cudaGetLastError();
+}
+
+template <class L>
+static cudaError_t init_l(int store, const void* rho, const void* u, int field_f32, void* A,
+                          int nx, int ny, int nz, int nxp, long long sq, int entropic,
+                          int feq_variant, cudaStream_t s)
+{
+    switch (store) {
+    case 0: return init_t<L, StoreF64>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    case 1: return init_t<L, StoreF32>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    case 2: return init_t<L, StoreF32S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    case 3: return init_t<L, StoreF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    case 4: return init_t<L, StoreBF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
+                        void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
+                        int feq_variant, cudaStream_t s)
+{
+    if (lattice == 0)
+        return init_l<D2Q9>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
+                            feq_variant, s);
+    return init_l<D3Q19>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant,
+                         s);
+}
+
+// ---------------------------------------------------------------------------
+// Padded compute-type field -> dense caller field (F32 or F64).
+// nfields consecutive planes spaced sq apart in src, N apart in dst.
+// ---------------------------------------------------------------------------
+template <class RT, class OT>
+__global__ void k_pack(const RT* __restrict__ src, OT* __restrict__ dst, int nfields, int nx,
+                       int ny, int nz, int nxp, long long sq)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= nx) return;
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t nd = ((size_t)z * ny + y) * nx + x;
+    const size_t n = ((size_t)z * ny + y) * nxp + x;
+    for (int f = 0; f < nfields; ++f) dst[f * N + nd] = (OT)src[f * sq + n];
+}
+
+cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, int nfields, int nx,
+                        int ny, int nz, int nxp, long long sq, cudaStream_t s)
+{
+    dim3 block(128), grid((nx + 127) / 128, ny, nz);
+    if (src_f64) {
+        if (dst_f32)
+            k_pack<double, float><<<grid, block, 0, s>>>((const double*)src, (float*)dst, nfields,
+                                                         nx, ny, nz, nxp, sq);
+        else
+            k_pack<double, double><<<grid, block, 0, s>>>((const double*)src, (double*)dst,
+                                                          nfields, nx, ny, nz, nxp, sq);
+    } else {
+        if (dst_f32)
+            k_pack<float, float><<<grid, block, 0, s>>>((const float*)src, (float*)dst, nfields,
+                                                        nx, ny, nz, nxp, sq);
+        else
+            k_pack<float, double><<<grid, block, 0, s>>>((const float*)src, (double*)dst,
+                                                         nfields, nx, ny, nz, nxp, sq);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 sums over fluid nodes: mass, momentum (D), kinetic
+// energy.  Pass 1: a fixed grid of kReduceBlocks CTAs, each striding over
+// rows in a fixed order and reducing in a fixed tree -> partials.  Pass 2:
+// one CTA sums the partials in a fixed tree.  Bitwise reproducible.
+// ---------------------------------------------------------------------------
+template <class RT>
+__global__ void __launch_bounds__(256) k_reduce_partial(const RT* __restrict__ rho,
+                                                        const RT* __restrict__ u,
+                                                        const uint8_t* __restrict__ flags, int D,
+                                                        int nx, int ny, int nz, int nxp,
+                                                        long long sq, double* __restrict__ part)
+{
+    __shared__ double sh[256][5];
+    double acc[5] = {0, 0, 0, 0, 0};
+    const long long rows = (long long)ny * nz;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const long long base = r * nxp;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long n = base + x;
+            if (flags && (flags[n] & FLAG_SOLID)) continue;
+            const double rr = (double)rho[n];
+            double ke = 0;
+            acc[0] += rr;
+            for (int a = 0; a < D; ++a) {
+                const double va = (double)u[a * sq + n];
+                acc[1 + a] += rr * va;
+                ke += va * va;
+            }
+            acc[1 + D] += 0.5 * rr * ke;
+        }
+    }
+    for (int k = 0; k < 5; ++k) sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 5; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ part,
+                                                      int nblocks, double* __restrict__ out)
+{
+    __shared__ double sh[256][5];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 5; ++k) acc[k] += part[b * 5 + k];
+    for (int k = 0; k < 5; ++k) sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 5; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint8_t* flags, int D,
+                          int nx, int ny, int nz, int nxp, long long sq, double* partials,
+                          double* out, cudaStream_t s)
+{
+    if (f64)
+        k_reduce_partial<double><<<kReduceBlocks, 256, 0, s>>>(
+            (const double*)rho, (const double*)u, flags, D, nx, ny, nz, nxp, sq, partials);
+    else
+        k_reduce_partial<float><<<kReduceBlocks, 256, 0, s>>>(
+            (const float*)rho, (const float*)u, flags, D, nx, ny, nz, nxp, sq, partials);
+    k_reduce_final<<<1, 256, 0, s>>>(partials, kReduceBlocks, out);
+    return cudaGetLastError();
+}
+
+// Sum the 64 replicas of the ELBM counters into 6 values.
+__global__ void k_sum_ctr(const unsigned long long* __restrict__ rep, double* __restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= 6) return;
+    unsigned long long s = 0;
+    for (int r = 0; r < 64; ++r) s += rep[r * 8 + k];
+    out[k] = (double)s;
+}
+
+cudaError_t launch_sum_ctr(const unsigned long long* rep, double* out, cudaStream_t s)
+{
+    k_sum_ctr<<<1, 32, 0, s>>>(rep, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

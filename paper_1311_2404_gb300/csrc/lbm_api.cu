@@ -1,0 +1,665 @@
+// Host runtime and C ABI of the single-domain simulation (include/lbm.h).
+//
+// A handle owns one device arena (allocated here, or bound by the caller):
+//   A, B      two copies of the distributions (AB pattern, Sec. 3.3),
+//             [q][z][y][x] structure of arrays, x padded to a multiple of 32
+//             elements and direction planes padded to 128 elements
+//   flags     node-type map, one byte per (padded) node
+//   rho, u    macroscopic output fields in the compute type, padded layout
+//   alpha     ELBM per-node alpha (FP64), ELBM handles only
+//   misc      status word, ELBM counters, reduction scratch, MLP parameters
+//   stage     dense staging for host transfers and dtype conversion
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+
+#include "../../include/lbm.h"
+#include "collide.cuh"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0, lattice = 0, model = 0, dtype = 0, D = 0, Q = 0;
+    double tau = 1.0;
+    int nxp = 0;
+    long long sq = 0;       // elements per direction plane (padded)
+    long long N = 0;        // dense node count
+    size_t esize = 0;       // storage element size
+    size_t rsize = 0;       // compute (output field) element size
+    // arena
+    char* base = nullptr;
+    size_t bytes = 0;
+    bool owned = false;
+    size_t off_A = 0, off_B = 0, off_flags = 0, off_rho = 0, off_u = 0, off_alpha = 0,
+           off_misc = 0, off_part = 0, off_mlp = 0, off_stage = 0, stage_bytes = 0;
+    int cur = 0;            // 0: state in A, 1: state in B
+    bool has_mask = false, inited = false, have_out = false;
+    cudaStream_t stream = nullptr;
+    double F[3] = {0, 0, 0};
+    double s[19];
+    int alpha_mode = LBM_ALPHA_NEWTON, max_iter = 20, guard_steps = 2, feq_variant = 0;
+    double tol = 1e-12, skip_eps = 1e-3, guard_tol = 1e-6;
+    bool mlp_loaded = false, alpha_out = false, use_graph = false;
+    long long t = 0, launches = 0;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+// misc block layout (bytes from off_misc)
+enum : size_t {
+    MISC_STATUS = 0,        // uint32 status bits
+    MISC_PAIRS = 8,         // int pairs counter
+    MISC_RED = 64,          // 5 doubles reduction result
+    MISC_CTR_OUT = 128,     // 6 doubles summed counters
+    MISC_CTR = 256,         // 64 x 8 unsigned long long counter replicas
+    MISC_BYTES = 256 + 64 * 8 * 8
+};
+
+static thread_local std::string g_err;
+
+static void drop_graphs(lbm_ctx* h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+static int fail(lbm_ctx* h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_err = buf;
+    return code;
+}
+
+static int cuda_fail(lbm_ctx* h, cudaError_t e, const char* what)
+{
+    return fail(h, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                                      \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, (what)); \
+    } while (0)
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void default_rates(double tau, double* s)
+{
+    for (int k = 0; k < 19; ++k) s[k] = 0.0;
+    const double w = 1.0 / tau;
+    s[1] = 1.19;
+    s[2] = 1.4;
+    s[4] = s[6] = s[8] = 1.2;
+    s[9] = s[11] = s[13] = s[14] = s[15] = w;
+    s[10] = s[12] = 1.4;
+    s[16] = s[17] = s[18] = 1.98;
+}
+
+static void layout(lbm_ctx* h)
+{
+    size_t o = 0;
+    const size_t dist = (size_t)h->Q * h->sq * h->esize;
+    h->off_A = o; o = align256(o + dist);
+    h->off_B = o; o = align256(o + dist);
+    h->off_flags = o; o = align256(o + (size_t)h->sq);
+    h->off_rho = o; o = align256(o + (size_t)h->sq * h->rsize);
+    h->off_u = o; o = align256(o + (size_t)h->D * h->sq * h->rsize);
+    h->off_alpha = o;
+    if (h->model == LBM_ELBM) o = align256(o + (size_t)h->sq * 8);
+    h->off_misc = o; o = align256(o + MISC_BYTES);
+    h->off_part = o; o = align256(o + (size_t)kReduceBlocks * 5 * 8);
+    h->off_mlp = o; o = align256(o + MLP_NPARAM * 4);
+    h->off_stage = o;
+    h->stage_bytes = align256((size_t)h->N * (1 + h->D) * 8);
+    o = align256(o + h->stage_bytes);
+    h->bytes = o;
+}
+
+template <class T>
+static T* at(lbm_ctx* h, size_t off) { return reinterpret_cast<T*>(h->base + off); }
+
+static int ensure_memory(lbm_ctx* h)
+{
+    if (h->base) return LBM_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, h->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LBM_ENOMEM, "cudaMalloc(%zu bytes): %s", h->bytes, cudaGetErrorString(e));
+    }
+    h->base = static_cast<char*>(p);
+    h->owned = true;
+    CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
+    CK(h, cudaMemsetAsync(h->base + h->off_flags, 0, (size_t)h->sq, h->stream), "clear flags");
+    return LBM_OK;
+}
+
+static int read_status(lbm_ctx* h, unsigned* st)
+{
+    CK(h, cudaMemcpyAsync(st, h->base + h->off_misc + MISC_STATUS, 4, cudaMemcpyDeviceToHost,
+                          h->stream),
+       "read status");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    return LBM_OK;
+}
+
+static int sync_status(lbm_ctx* h)
+{
+    if (!h->base) {
+        CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+        return LBM_OK;
+    }
+    unsigned st = 0;
+    int r = read_status(h, &st);
+    if (r) return r;
+    if (st & STATUS_NAN) return fail(h, LBM_ENAN, "non-finite rho or v on an output step");
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
+               lbm_handle* out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1)
+        return fail(nullptr, LBM_EINVAL, "sizes must be >= 1 (got %d x %d x %d)", nx, ny, nz);
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+        return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lattice);
+    if (lattice == LBM_D2Q9 && nz != 1)
+        return fail(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1 (got %d)", nz);
+    if (model != LBM_BGK && model != LBM_MRT && model != LBM_ELBM)
+        return fail(nullptr, LBM_EINVAL, "unknown model %d", model);
+    if (model == LBM_MRT && lattice != LBM_D3Q19)
+        return fail(nullptr, LBM_EINVAL, "MRT is implemented for D3Q19 only");
+    if (dtype < LBM_F64 || dtype > LBM_BF16S)
+        return fail(nullptr, LBM_EINVAL, "unknown dtype %d", dtype);
+    if (!(tau > 0.5) || !(tau < 1e6))
+        return fail(nullptr, LBM_EINVAL, "tau must be > 1/2 (got %g)", tau);
+    const long long nxp = ((long long)nx + 31) / 32 * 32;
+    long long sq = nxp * ny * nz;
+    sq = (sq + 127) / 128 * 128;
+    if (sq > 0x7fffffffLL - 1024)
+        return fail(nullptr, LBM_EINVAL, "domain too large: %lld padded nodes > 2^31", sq);
+    lbm_ctx* h = new lbm_ctx();
+    h->nx = nx; h->ny = ny; h->nz = nz;
+    h->lattice = lattice; h->model = model; h->dtype = dtype; h->tau = tau;
+    h->D = lattice == LBM_D2Q9 ? 2 : 3;
+    h->Q = lattice == LBM_D2Q9 ? 9 : 19;
+    h->nxp = (int)nxp;
+    h->sq = sq;
+    h->N = (long long)nx * ny * nz;
+    h->esize = dtype == LBM_F64 ? 8 : (dtype == LBM_F32 || dtype == LBM_F32S) ? 4 : 2;
+    h->rsize = dtype == LBM_F64 ? 8 : 4;
+    default_rates(tau, h->s);
+    layout(h);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h)
+{
+    if (!h) return LBM_OK;
+    drop_graphs(h);
+    if (h->owned && h->base) cudaFree(h->base);
+    delete h;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+size_t lbm_required_bytes(lbm_handle h) { return h ? h->bytes : 0; }
+
+int lbm_bind_memory(lbm_handle h, void* dev_ptr, size_t bytes)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->base) return fail(h, LBM_ESTATE, "memory already in use");
+    if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255))
+        return fail(h, LBM_EINVAL, "bound memory must be non-NULL and 256-byte aligned");
+    if (bytes < h->bytes)
+        return fail(h, LBM_ENOMEM, "bound memory too small: %zu < %zu bytes", bytes, h->bytes);
+    if (!is_device_ptr(dev_ptr)) return fail(h, LBM_EINVAL, "bound memory is not device memory");
+    h->base = static_cast<char*>(dev_ptr);
+    h->owned = false;
+    CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
+    CK(h, cudaMemsetAsync(h->base + h->off_flags, 0, (size_t)h->sq, h->stream), "clear flags");
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->stream != static_cast<cudaStream_t>(stream)) drop_graphs(h);
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_handle h, const uint8_t* mask)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!mask) return fail(h, LBM_EINVAL, "mask is NULL");
+    if (h->inited) return fail(h, LBM_ESTATE, "set the geometry before lbm_init_equilibrium");
+    int r = ensure_memory(h);
+    if (r) return r;
+    uint8_t* stage = at<uint8_t>(h, h->off_stage);
+    const bool dev = is_device_ptr(mask);
+    CK(h, cudaMemcpyAsync(stage, mask, (size_t)h->N,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
+       "copy mask");
+    CK(h, launch_flags(h->lattice, stage, at<uint8_t>(h, h->off_flags), h->nx, h->ny, h->nz,
+                       h->nxp, h->stream),
+       "node-type map kernel");
+    h->launches += 1;
+    CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    h->has_mask = true;
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_handle h, double fx, double fy, double fz)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz))
+        return fail(h, LBM_EINVAL, "force must be finite");
+    if (h->D == 2 && fz != 0.0) return fail(h, LBM_EINVAL, "D2Q9 force has no z component");
+    h->F[0] = fx; h->F[1] = fy; h->F[2] = fz;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_mrt_rates(lbm_handle h, const double* s, int q)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_MRT) return fail(h, LBM_EINVAL, "not an MRT handle");
+    if (!s || q != 19) return fail(h, LBM_EINVAL, "need 19 rates");
+    for (int k = 0; k < 19; ++k) {
+        if (!std::isfinite(s[k])) return fail(h, LBM_EINVAL, "rate %d not finite", k);
+        h->s[k] = s[k];
+    }
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_elbm(lbm_handle h, int alpha_mode, double tol, int max_iter, double skip_eps)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
+    if (alpha_mode < 0 || alpha_mode > 3) return fail(h, LBM_EINVAL, "bad alpha mode");
+    if (!(tol > 0) || max_iter < 1 || max_iter > 200 || !(skip_eps >= 0))
+        return fail(h, LBM_EINVAL, "bad tolerance / iteration cap / skip threshold");
+    h->alpha_mode = alpha_mode; h->tol = tol; h->max_iter = max_iter; h->skip_eps = skip_eps;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_elbm_guard(lbm_handle h, int guard_steps, double guard_tol)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (guard_steps < 1 || guard_steps > 4 || !(guard_tol > 0))
+        return fail(h, LBM_EINVAL, "guard_steps must be 1..4 and guard_tol > 0");
+    h->guard_steps = guard_steps; h->guard_tol = guard_tol;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_elbm_feq(lbm_handle h, int variant)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (variant != 0 && variant != 1) return fail(h, LBM_EINVAL, "variant must be 0 or 1");
+    if (h->inited) return fail(h, LBM_ESTATE, "choose the equilibrium before initialising");
+    h->feq_variant = variant;
+    return LBM_OK;
+}
+
+int lbm_load_alpha_mlp(lbm_handle h, const float* params, int n)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!params || n != MLP_NPARAM) return fail(h, LBM_EINVAL, "need %d parameters", MLP_NPARAM);
+    int r = ensure_memory(h);
+    if (r) return r;
+    float host[MLP_NPARAM];
+    if (is_device_ptr(params)) {
+        CK(h, cudaMemcpy(host, params, sizeof host, cudaMemcpyDeviceToHost), "copy parameters");
+    } else {
+        std::memcpy(host, params, sizeof host);
+    }
+    // weight matrices and biases (entries 16 .. 1392) rounded to BF16
+    for (int k = 16; k < MLP_NPARAM - 1; ++k)
+        host[k] = __bfloat162float(__float2bfloat16_rn(host[k]));
+    CK(h, cudaMemcpy(h->base + h->off_mlp, host, sizeof host, cudaMemcpyHostToDevice),
+       "upload parameters");
+    h->mlp_loaded = true;
+    return LBM_OK;
+}
+
+int lbm_set_alpha_output(lbm_handle h, int on)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "alpha output needs an ELBM handle");
+    h->alpha_out = on != 0;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_graph(lbm_handle h, int on)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    h->use_graph = on != 0;
+    return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field_dtype)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u must be non-NULL");
+    if (field_dtype != LBM_FIELD_F64 && field_dtype != LBM_FIELD_F32)
+        return fail(h, LBM_EINVAL, "unknown field dtype %d", field_dtype);
+    int r = ensure_memory(h);
+    if (r) return r;
+    const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
+    const size_t nb = (size_t)h->N * fs;
+    const void* drho = rho;
+    const void* du = u;
+    char* stage = at<char>(h, h->off_stage);
+    bool host_in = false;
+    if (!is_device_ptr(rho)) {
+        CK(h, cudaMemcpyAsync(stage, rho, nb, cudaMemcpyHostToDevice, h->stream), "copy rho");
+        drho = stage;
+        host_in = true;
+    }
+    if (!is_device_ptr(u)) {
+        CK(h, cudaMemcpyAsync(stage + nb, u, nb * h->D, cudaMemcpyHostToDevice, h->stream),
+           "copy u");
+        du = stage + nb;
+        host_in = true;
+    }
+    CK(h, launch_init(h->lattice, h->dtype, drho, du, field_dtype == LBM_FIELD_F32,
+                      h->base + h->off_A, h->nx, h->ny, h->nz, h->nxp, h->sq,
+                      h->model == LBM_ELBM, h->feq_variant, h->stream),
+       "init kernel");
+    h->launches += 1;
+    CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
+    if (host_in) CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    h->cur = 0;
+    h->t = 0;
+    h->inited = true;
+    h->have_out = false;
+    return LBM_OK;
+}
+
+static StepParams make_params(lbm_ctx* h)
+{
+    StepParams p;
+    std::memset(&p, 0, sizeof p);
+    p.flags = h->has_mask ? at<uint8_t>(h, h->off_flags) : nullptr;
+    p.rho = h->base + h->off_rho;
+    p.u = h->base + h->off_u;
+    p.alpha_out = (h->model == LBM_ELBM && h->alpha_out) ? at<double>(h, h->off_alpha) : nullptr;
+    p.status = at<unsigned>(h, h->off_misc + MISC_STATUS);
+    p.elbm_ctr = h->model == LBM_ELBM ? at<unsigned long long>(h, h->off_misc + MISC_CTR)
+                                      : nullptr;
+    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz; p.nxp = h->nxp;
+    p.sq = h->sq;
+    p.omega = 1.0 / h->tau;
+    p.F[0] = h->F[0]; p.F[1] = h->F[1]; p.F[2] = h->F[2];
+    p.has_force = (h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0);
+    for (int k = 0; k < 19; ++k) {
+        const double n2 = h->lattice == LBM_D3Q19 ? (double)mrt_norm2(k) : 1.0;
+        p.mrt_c[k] = (float)(h->s[k] / n2);
+        p.mrt_cf[k] = (float)((1.0 - 0.5 * h->s[k]) / n2);
+    }
+    p.alpha_mode = h->alpha_mode; p.max_iter = h->max_iter;
+    p.guard_steps = h->guard_steps; p.feq_variant = h->feq_variant;
+    p.tol = h->tol; p.skip_eps = h->skip_eps; p.guard_tol = h->guard_tol;
+    p.mlp = at<float>(h, h->off_mlp);
+    p.pairs_stride = 1;
+    return p;
+}
+
+static cudaError_t launch_one(lbm_ctx* h, StepParams& p, int from, bool out)
+{
+    p.A = h->base + (from == 0 ? h->off_A : h->off_B);
+    p.B = h->base + (from == 0 ? h->off_B : h->off_A);
+    p.out = out ? 1 : 0;
+    const bool mask = h->has_mask;
+    if (h->model == LBM_BGK) return launch_step_bgk(h->lattice, h->dtype, p, mask, h->stream);
+    if (h->model == LBM_MRT) return launch_step_mrt(h->lattice, h->dtype, p, mask, h->stream);
+    return launch_step_elbm(h->lattice, h->dtype, p, mask, h->stream);
+}
+
+static int check_step_ready(lbm_ctx* h)
+{
+    if (!h->inited) return fail(h, LBM_ESTATE, "lbm_init_equilibrium must precede lbm_step");
+    if (h->model == LBM_ELBM && h->alpha_mode == LBM_ALPHA_MLP_GUARDED && !h->mlp_loaded)
+        return fail(h, LBM_ESTATE, "MLP alpha mode needs lbm_load_alpha_mlp");
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int n)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 1) return fail(h, LBM_EINVAL, "n must be >= 1 (got %d)", n);
+    int r = check_step_ready(h);
+    if (r) return r;
+    StepParams p = make_params(h);
+    if (h->use_graph && h->stream != nullptr) {
+        auto key = std::make_pair(n, h->cur);
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            cudaGraph_t g;
+            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+               "begin capture");
+            int from = h->cur;
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < n && le == cudaSuccess; ++k) {
+                le = launch_one(h, p, from, k == n - 1);
+                from ^= 1;
+            }
+            cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+            if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
+            CK(h, ce, "end capture");
+            cudaGraphExec_t ge;
+            cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            CK(h, ie, "instantiate graph");
+            it = h->graphs.emplace(key, ge).first;
+        }
+        CK(h, cudaGraphLaunch(it->second, h->stream), "graph launch");
+        h->cur ^= (n & 1);
+    } else {
+        for (int k = 0; k < n; ++k) {
+            CK(h, launch_one(h, p, h->cur, k == n - 1), "stream-collide kernel");
+            h->cur ^= 1;
+        }
+    }
+    h->launches += n;
+    h->t += n;
+    h->have_out = true;
+    return LBM_OK;
+}
+
+int lbm_get_time(lbm_handle h, long long* t)
+{
+    if (!h || !t) return fail(h, LBM_EINVAL, "NULL argument");
+    *t = h->t;
+    return LBM_OK;
+}
+
+static int get_field(lbm_ctx* h, size_t src_off, int nfields, void* dst, int field_dtype)
+{
+    const int dst_f32 = field_dtype == LBM_FIELD_F32;
+    const size_t fs = dst_f32 ? 4 : 8;
+    const size_t nb = (size_t)h->N * fs * nfields;
+    const bool dev = is_device_ptr(dst);
+    void* out = dev ? dst : h->base + h->off_stage;
+    CK(h, launch_pack(h->rsize == 8, h->base + src_off, dst_f32, out, nfields, h->nx, h->ny,
+                      h->nz, h->nxp, h->sq, h->stream),
+       "pack kernel");
+    h->launches += 1;
+    if (!dev)
+        CK(h, cudaMemcpyAsync(dst, out, nb, cudaMemcpyDeviceToHost, h->stream), "copy out");
+    return LBM_OK;
+}
+
+int lbm_get_macro(lbm_handle h, void* rho, void* u, int field_dtype)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (field_dtype != LBM_FIELD_F64 && field_dtype != LBM_FIELD_F32)
+        return fail(h, LBM_EINVAL, "unknown field dtype %d", field_dtype);
+    if (!h->have_out) return fail(h, LBM_ESTATE, "no step has produced output yet");
+    int r;
+    if (rho && (r = get_field(h, h->off_rho, 1, rho, field_dtype))) return r;
+    if (u && (r = get_field(h, h->off_u, h->D, u, field_dtype))) return r;
+    return sync_status(h);
+}
+
+int lbm_get_alpha(lbm_handle h, double* alpha)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!alpha) return fail(h, LBM_EINVAL, "alpha is NULL");
+    if (h->model != LBM_ELBM || !h->alpha_out || !h->have_out)
+        return fail(h, LBM_ESTATE, "alpha output needs ELBM, lbm_set_alpha_output and a step");
+    const bool dev = is_device_ptr(alpha);
+    void* out = dev ? (void*)alpha : h->base + h->off_stage;
+    CK(h, launch_pack(1, h->base + h->off_alpha, 0, out, 1, h->nx, h->ny, h->nz, h->nxp, h->sq,
+                      h->stream),
+       "pack kernel");
+    h->launches += 1;
+    if (!dev)
+        CK(h, cudaMemcpyAsync(alpha, out, (size_t)h->N * 8, cudaMemcpyDeviceToHost, h->stream),
+           "copy alpha");
+    return sync_status(h);
+}
+
+int lbm_reduce(lbm_handle h, double* out)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (!h->have_out) return fail(h, LBM_ESTATE, "no step has produced output yet");
+    double* dres = at<double>(h, h->off_misc + MISC_RED);
+    CK(h, launch_reduce(h->rsize == 8, h->base + h->off_rho, h->base + h->off_u,
+                        h->has_mask ? at<uint8_t>(h, h->off_flags) : nullptr, h->D, h->nx, h->ny,
+                        h->nz, h->nxp, h->sq, at<double>(h, h->off_part), dres, h->stream),
+       "reduce kernels");
+    h->launches += 2;
+    double tmp[5];
+    CK(h, cudaMemcpyAsync(tmp, dres, sizeof tmp, cudaMemcpyDeviceToHost, h->stream), "copy sums");
+    int r = sync_status(h);
+    for (int k = 0; k < h->D + 2; ++k) out[k] = tmp[k];
+    return r;
+}
+
+int lbm_get_elbm_stats(lbm_handle h, double* out)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
+    int r = ensure_memory(h);
+    if (r) return r;
+    double* d = at<double>(h, h->off_misc + MISC_CTR_OUT);
+    CK(h, launch_sum_ctr(at<unsigned long long>(h, h->off_misc + MISC_CTR), d, h->stream),
+       "counter kernel");
+    h->launches += 1;
+    CK(h, cudaMemcpyAsync(out, d, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "copy counters");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(lbm_handle h) { return h ? (size_t)h->Q * h->sq * h->esize : 0; }
+
+int lbm_get_state(lbm_handle h, void* dst, long long* t)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!dst) return fail(h, LBM_EINVAL, "dst is NULL");
+    if (!h->inited) return fail(h, LBM_ESTATE, "no state yet");
+    const size_t nb = lbm_state_bytes(h);
+    CK(h, cudaMemcpyAsync(dst, h->base + (h->cur == 0 ? h->off_A : h->off_B), nb,
+                          cudaMemcpyDefault, h->stream),
+       "copy state");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    if (t) *t = h->t;
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle h, const void* src, long long t)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!src) return fail(h, LBM_EINVAL, "src is NULL");
+    int r = ensure_memory(h);
+    if (r) return r;
+    const size_t nb = lbm_state_bytes(h);
+    CK(h, cudaMemcpyAsync(h->base + h->off_A, src, nb, cudaMemcpyDefault, h->stream),
+       "copy state");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    h->cur = 0;
+    h->t = t;
+    h->inited = true;
+    h->have_out = false;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    return sync_status(h);
+}
+
+long long lbm_launch_count(lbm_handle h) { return h ? h->launches : 0; }
+
+int lbm_elbm_collect_pairs(lbm_handle h, int stride, float* X_dev, double* y_dev, int cap,
+                           int* count)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
+    if (stride < 1 || cap < 1 || !X_dev || !y_dev || !count)
+        return fail(h, LBM_EINVAL, "bad pair-capture arguments");
+    if (!is_device_ptr(X_dev) || !is_device_ptr(y_dev))
+        return fail(h, LBM_EINVAL, "pair buffers must be device memory");
+    int r = check_step_ready(h);
+    if (r) return r;
+    StepParams p = make_params(h);
+    int* cnt = at<int>(h, h->off_misc + MISC_PAIRS);
+    CK(h, cudaMemsetAsync(cnt, 0, sizeof(int), h->stream), "clear pair count");
+    p.pairs_X = X_dev;
+    p.pairs_y = y_dev;
+    p.pairs_count = cnt;
+    p.pairs_cap = cap;
+    p.pairs_stride = stride;
+    CK(h, launch_one(h, p, h->cur, true), "stream-collide kernel (pair capture)");
+    h->cur ^= 1;
+    h->launches += 1;
+    h->t += 1;
+    h->have_out = true;
+    int hc = 0;
+    CK(h, cudaMemcpyAsync(&hc, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "count");
+    r = sync_status(h);
+    *count = hc < cap ? hc : cap;
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Device-side building blocks of the stream-and-collide kernels: lattice
+// tables, storage codecs and the per-node collision operators.
+//
+// Every operator works on deviations d_i = f_i - w_i held in registers (the
+// round-off-minimising formulation the paper studies in Sec. 3.7): mass is
+// rho = 1 + sum d_i and momentum j = sum e_i d_i since sum w_i = 1 and
+// sum w_i e_i = 0.  Storage types that keep f_i itself convert on load/store.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattices (Sec. 2, Fig. lattices, Table bgkweights).  Own ordering: rest
+// first, then opposite pairs (2k-1, 2k), so opp(i) = i + 1 for odd i and
+// i - 1 for even i > 0.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int D = 2, Q = 9;
+    __host__ __device__ static constexpr int ex(int i) {
+        constexpr int t[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        constexpr int t[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int D = 3, Q = 19;
+    __host__ __device__ static constexpr int ex(int i) {
+        constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Storage codecs.  load() returns the deviation d = f - w in the compute type
+// R; store() takes it back.  *_S codecs keep d itself (Sec. 3.7 round-off
+// minimisation; FP16/BF16 extend it to half-width storage).
+// ---------------------------------------------------------------------------
+struct StoreF64 {
+    using T = double;
+    using R = double;
+    __device__ static R load(const T* p, double w) { return __ldg(p) - w; }
+    __device__ static void store(T* p, R d, double w) { *p = d + w; }
+    __device__ static T encode(R d, double w) { return d + w; }
+};
+struct StoreF32 {
+    using T = float;
+    using R = float;
+    __device__ static R load(const T* p, double w) { return __ldg(p) - (float)w; }
+    __device__ static void store(T* p, R d, double w) { *p = d + (float)w; }
+    __device__ static T encode(R d, double w) { return d + (float)w; }
+};
+struct StoreF32S {
+    using T = float;
+    using R = float;
+    __device__ static R load(const T* p, double) { return __ldg(p); }
+    __device__ static void store(T* p, R d, double) { *p = d; }
+    __device__ static T encode(R d, double) { return d; }
+};
+struct StoreF16S {
+    using T = __half;
+    using R = float;
+    __device__ static R load(const T* p, double) { return __half2float(__ldg(p)); }
+    __device__ static void store(T* p, R d, double) { *p = __float2half_rn(d); }
+    __device__ static T encode(R d, double) { return __float2half_rn(d); }
+};
+struct StoreBF16S {
+    using T = __nv_bfloat16;
+    using R = float;
+    __device__ static R load(const T* p, double) { return __bfloat162float(__ldg(p)); }
+    __device__ static void store(T* p, R d, double) { *p = __float2bfloat16_rn(d); }
+    __device__ static T encode(R d, double) { return __float2bfloat16_rn(d); }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel parameters (passed by value).
+// ---------------------------------------------------------------------------
+enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2 };
+enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2 };
+enum { STATUS_NAN = 1u, STATUS_NOCONV = 2u, STATUS_TIMEOUT = 4u };
+// ELBM per-node outcome, shared meaning with the counters of the ABI
+enum { ALPHA_CONV = 0, ALPHA_SKIP = 1, ALPHA_CLAMP = 2, ALPHA_NOCONV = 3, ALPHA_GUARDED = 5 };
+enum { MLP_NPARAM = 1394 };
+
+struct StepParams {
+    const void* A;             // post-collision distributions at t (read)
+    void* B;                   // post-collision distributions at t+1 (written)
+    const uint8_t* flags;      // node-type map (FLAG_*) or nullptr
+    void* rho;                 // output fields (compute type), padded layout
+    void* u;                   // [D][sq]
+    double* alpha_out;         // ELBM per-node alpha or nullptr
+    unsigned int* status;      // STATUS_* bits
+    unsigned long long* elbm_ctr;  // 6 counters or nullptr
+    float* pairs_X;            // ELBM training-pair capture (nullptr = off)
+    double* pairs_y;
+    int* pairs_count;
+    int pairs_cap, pairs_stride;
+    int nx, ny, nz, nxp;       // logical sizes, padded row length
+    long long sq;              // elements between direction planes
+    int out;                   // write rho/u (and alpha) this step
+    int has_force;
+    double omega;              // 1/tau
+    double F[3];               // body force
+    float mrt_c[19];           // s_k / |M_k|^2
+    float mrt_cf[19];          // (1 - s_k/2) / |M_k|^2
+    // ELBM
+    int alpha_mode, max_iter, guard_steps, feq_variant;
+    double tol, skip_eps, guard_tol;
+    const float* mlp;          // MLP_NPARAM floats (BF16-rounded weights)
+};
+
+}  // namespace lbm

@@ -108,7 +108,8 @@ def duct_with_spheres(nx: int = 512, ny: int = 256, nz: int = 256,
 def turbulence(n: int = 256, k0: float = 4.0, u_rms: float = 0.04, seed: int = 2404):
     """Random-phase solenoidal velocity on a periodic n^3 box with energy
     spectrum E(k) ~ k^4 exp(-2 (k/k0)^2): white noise filtered by
-    sqrt(E(k) / (4 pi k^2)), projected onto divergence-free fields, scaled so
+    sqrt(E(k) / (4 pi k^2)) (Nyquist modes dropped), projected onto
+    divergence-free fields, scaled so
     that the per-component rms sqrt(<|u|^2>/3) equals u_rms.  rho = 1.
     Returns (rho, u) in float64."""
     rng = _rng(seed)
@@ -119,6 +120,10 @@ def turbulence(n: int = 256, k0: float = 4.0, u_rms: float = 0.04, seed: int = 2
     with np.errstate(divide="ignore", invalid="ignore"):
         amp = np.where(k2 > 0, np.sqrt(kmag ** 4 * np.exp(-2.0 * (kmag / k0) ** 2)
                                        / (4 * np.pi * k2)), 0.0)
+    # drop the Nyquist planes, whose real-valued modes cannot hold a projected
+    # (complex) solenoidal component
+    half = n // 2
+    amp[(np.abs(kx) == half) | (np.abs(ky) == half) | (np.abs(kz) == half)] = 0.0
     uh = []
     for _ in range(3):
         w = rng.standard_normal((n, n, n))

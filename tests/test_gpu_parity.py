@@ -1,0 +1,290 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a GB300).
+
+Tolerances (relative L2 over all nodes, rho and v):
+  LBM_F64                      1e-12 (same arithmetic up to rounding order)
+  LBM_F32 / LBM_F32S           1e-5  (the stated FP32 parity bar)
+  LBM_F16S / LBM_BF16S         reported, bounded loosely (storage-limited)
+Every call goes through the C ABI (paper_1311_2404_gb300.lbm).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import analytic as an
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1311_2404_gb300 import lbm  # noqa: E402
+from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
+
+TOL = {lbm.LBM_F64: 1e-12, lbm.LBM_F32: 1e-5, lbm.LBM_F32S: 1e-5,
+       lbm.LBM_F16S: 2e-2, lbm.LBM_BF16S: 2e-1}
+OMODEL = {lbm.LBM_BGK: oracle.BGK, lbm.LBM_MRT: oracle.MRT, lbm.LBM_ELBM: oracle.ELBM}
+
+
+def _dev_err(a, b):
+    """Relative L2 of the deviation from rest (rho - 1 for densities)."""
+    return an.rel_l2(a, b)
+
+
+def run_pair(D, model, dtype, shape, steps, tau=0.6, force=(0.0, 0.0, 0.0), mask=None,
+             rho=None, u=None, elbm=None, seed=3):
+    nz, ny, nx = shape
+    if rho is None:
+        rho, u = wl.random_state(nx, ny, nz, D, seed=seed, u_amp=0.04, rho_amp=0.01)
+    lat = lbm.LBM_D2Q9 if D == 2 else lbm.LBM_D3Q19
+    sim = lbm.Simulation(nx, ny, nz, lat, model, tau, dtype)
+    if mask is not None:
+        sim.set_geometry(mask)
+    if any(force):
+        sim.set_force(*force[:3])
+    okw = {}
+    if elbm:
+        lbm.lbm_set_elbm(sim.h, elbm.get("mode", 0), 1e-12, 20, elbm.get("skip", 1e-3))
+        okw = dict(alpha_mode=elbm.get("mode", 0), skip_eps=elbm.get("skip", 1e-3))
+    sim.init(rho, u)
+    sim.step(steps)
+    rg, ug = sim.macro()
+    sim.close()
+    p = oracle.make_params(nx, ny, nz, D=D, model=OMODEL[model], tau=tau, force=force, **okw)
+    F = oracle.init(p, rho, u)
+    ro, uo, _, _ = oracle.run(p, F, steps, mask)
+    return rg, ug, ro, uo
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32, lbm.LBM_F32S, lbm.LBM_F16S,
+                                   lbm.LBM_BF16S])
+@pytest.mark.parametrize("D,model", [(2, lbm.LBM_BGK), (3, lbm.LBM_BGK), (3, lbm.LBM_MRT)])
+def test_parity_ragged_grid_with_walls_and_force(D, model, dtype):
+    """A ragged grid (x not a multiple of the 32-wide row tile, several tiles,
+    a partial block in y), random spheres + walls, body force."""
+    shape = (1, 45, 77) if D == 2 else (12, 21, 37)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(8)
+    mask = (rng.random(shape) < 0.08).astype(np.uint8)
+    mask[:, 0, :] = 1
+    force = (2e-5, -1e-5, 0.0) if D == 2 else (1e-5, 5e-6, -3e-6)
+    rg, ug, ro, uo = run_pair(D, model, dtype, shape, 40, tau=0.7, force=force, mask=mask)
+    fl = mask == 0
+    assert np.all(rg[~fl] == 0) and np.all(ug[:, ~fl] == 0)
+    e_u, e_r = an.rel_l2(ug, uo), an.rel_l2(rg - 1 * fl, ro - 1 * fl)
+    tol = TOL[dtype]
+    assert e_u < tol, (e_u, e_r)
+    assert an.rel_l2(rg, ro) < tol
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32S])
+@pytest.mark.parametrize("D", [2, 3])
+def test_parity_elbm(D, dtype):
+    """ELBM with the FP64 Newton solve, random near-equilibrium state with a
+    non-equilibrium start (skip threshold 0: every node solves)."""
+    shape = (1, 40, 52) if D == 2 else (10, 14, 18)
+    rg, ug, ro, uo = run_pair(D, lbm.LBM_ELBM, dtype, shape, 12, tau=0.505,
+                              force=(1e-5, 0.0, 0.0), elbm=dict(mode=0, skip=0.0))
+    tol = TOL[dtype]
+    assert an.rel_l2(ug, uo) < tol and an.rel_l2(rg, ro) < tol
+
+
+def test_elbm_alpha_field_parity():
+    """Per-node alpha (FP64 output) against the oracle's alpha: 1e-8 absolute."""
+    D, nx, ny, nz, tau = 3, 20, 12, 10, 0.5005
+    rho, u = wl.turbulence(20)
+    rho, u = rho[:nz, :ny, :nx].copy(), u[:, :nz, :ny, :nx].copy()
+    sim = lbm.Simulation(nx, ny, nz, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F64)
+    lbm.lbm_set_elbm(sim.h, lbm.LBM_ALPHA_NEWTON, 1e-12, 20, 1e-4)
+    lbm.lbm_set_alpha_output(sim.h, 1)
+    sim.init(rho, u)
+    sim.step(6)
+    ag = np.empty((nz, ny, nx))
+    lbm.lbm_get_alpha(sim.h, ag)
+    st = lbm.lbm_get_elbm_stats(sim.h)
+    sim.close()
+    p = oracle.make_params(nx, ny, nz, D=3, model=oracle.ELBM, tau=tau, skip_eps=1e-4)
+    F = oracle.init(p, rho, u)
+    _, _, ao, sto = oracle.run(p, F, 6, want_alpha=True)
+    assert np.abs(ag - ao).max() < 1e-8
+    assert st[5] == nx * ny * nz * 6                    # node updates
+    assert abs(st[1] - sto[1]) <= 0.01 * st[5]          # skipped counts agree
+
+
+def test_poiseuille_c1_fp64():
+    """64 x 32 D2Q9 LBGK FP64 channel, tau 0.8, g 1e-6, 5000 steps: equals the
+    oracle to 1e-13 and the start-up series to 1e-3."""
+    nx, ny, tau, g, T = 64, 32, 0.8, 1e-6, 5000
+    mask = wl.channel_mask(nx, ny)
+    rho = np.ones((1, ny, nx))
+    u = np.zeros((2, 1, ny, nx))
+    rg, ug, ro, uo = run_pair(2, lbm.LBM_BGK, lbm.LBM_F64, (1, ny, nx), T, tau=tau,
+                              force=(g, 0.0, 0.0), mask=mask, rho=rho, u=u)
+    assert np.abs(ug - uo).max() < 1e-13 * np.abs(uo).max() + 1e-18
+    y = np.arange(1, ny - 1, dtype=np.float64)
+    ref = an.poiseuille_startup(y, g, an.nu_of_tau(tau), 0.5, ny - 2, T)
+    assert an.rel_l2(ug[0, 0, 1:ny - 1, 7], ref) < 1e-3
+
+
+@pytest.fixture(scope="module")
+def tg256_oracle():
+    """The 256^3 extruded Taylor-Green vortex after 1000 steps computed by the
+    oracle on one z plane (the field is z-independent, so every plane of the
+    full box equals it exactly)."""
+    n, tau, u0, T = 256, 0.6, 0.05, 1000
+    rho, u = wl.taylor_green(n, u0, nz=1, D=3)
+    p = oracle.make_params(n, n, 1, D=3, model=oracle.BGK, tau=tau)
+    F = oracle.init(p, rho, u)
+    ro, uo, _, _ = oracle.run(p, F, T)
+    return ro, uo
+
+
+def test_taylor_green_256_full_size(tg256_oracle):
+    """The bench workload: D3Q19 LBGK FP32S, 256^3, tau 0.6, u0 0.05, 1000
+    steps.  Every z plane equals the oracle within 1e-5 (rho, u), planes are
+    bitwise identical, mass is conserved, kinetic energy decays as
+    exp(-4 nu k^2 t) within 1e-4."""
+    n, tau, u0, T = 256, 0.6, 0.05, 1000
+    ro, uo = tg256_oracle
+    rho, u = wl.taylor_green(n, u0, nz=n, D=3)
+    sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_BGK, tau, lbm.LBM_F32S)
+    sim.init(rho.astype(np.float32), u.astype(np.float32))
+    sim.step(T)
+    sums = sim.reduce()
+    rg = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    ug = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+    lbm.lbm_get_macro(sim.h, rg, ug)
+    sim.close()
+    # all planes identical
+    assert torch.equal(rg, rg[:1].expand_as(rg)) and torch.equal(ug, ug[:, :1].expand_as(ug))
+    r0 = rg[0:1].double().cpu().numpy()
+    u0g = ug[:, 0:1].double().cpu().numpy()
+    assert an.rel_l2(u0g, uo) < 1e-5
+    assert an.rel_l2(r0, ro) < 1e-5
+    assert an.rel_l2(r0 - 1, ro - 1) < 1e-3       # the deviation from rest, too
+    # FP64 reductions: mass, KE decay
+    nu = an.nu_of_tau(tau)
+    k = 2 * math.pi / n
+    assert abs(sums[0] - rho.sum()) < 1e-6 * rho.sum()
+    E0 = 0.5 * (rho * (u * u).sum(0)).sum()
+    assert abs(sums[4] / E0 / math.exp(-4 * nu * k * k * T) - 1) < 1e-4
+
+
+def test_checkpoint_resume_bitwise():
+    nx, ny, nz = 40, 24, 16
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=21)
+    sim = lbm.Simulation(nx, ny, nz, lbm.LBM_D3Q19, lbm.LBM_MRT, 0.55, lbm.LBM_F16S)
+    sim.set_force(1e-5, 0, 0)
+    sim.init(rho, u)
+    sim.step(7)
+    buf, t = sim.state()
+    sim.step(9)
+    r1, u1 = sim.macro()
+    sim.set_state(buf, t)
+    assert lbm.lbm_get_time(sim.h) == 7
+    sim.step(9)
+    r2, u2 = sim.macro()
+    sim.close()
+    assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
+
+
+def test_graph_replay_equals_plain_launches():
+    n = 48
+    rho, u = wl.random_state(n, n, n // 2, 3, seed=22)
+    out = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            sim = lbm.Simulation(n, n, n // 2, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+            lbm.lbm_set_graph(sim.h, graph)
+            sim.init(rho, u)
+            for _ in range(3):
+                sim.step(5)
+            out.append(sim.macro())
+            assert lbm.lbm_get_time(sim.h) == 15
+            sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_translation_covariance_bitwise_gpu():
+    nx, ny, nz = 35, 19, 11
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=23)
+    sh = (3, 5, 7)
+    res = []
+    for r_, u_ in ((rho, u), (np.roll(rho, sh, (0, 1, 2)), np.roll(u, sh, (1, 2, 3)))):
+        sim = lbm.Simulation(nx, ny, nz, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+        sim.init(np.ascontiguousarray(r_), np.ascontiguousarray(u_))
+        sim.step(10)
+        res.append(sim.macro())
+        sim.close()
+    assert np.array_equal(np.roll(res[0][0], sh, (0, 1, 2)), res[1][0])
+    assert np.array_equal(np.roll(res[0][1], sh, (1, 2, 3)), res[1][1])
+
+
+def test_reduce_matches_fields_and_is_reproducible():
+    nx, ny, nz = 64, 33, 9
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=24)
+    mask = wl.channel_mask(nx, ny, nz)
+    sim = lbm.Simulation(nx, ny, nz, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F64)
+    sim.set_geometry(mask)
+    sim.init(rho, u)
+    sim.step(3)
+    a = sim.reduce()
+    b = sim.reduce()
+    r, v = sim.macro()
+    sim.close()
+    assert np.array_equal(a, b)
+    fl = mask == 0
+    ref = [r[fl].sum()] + [(r * v[k])[fl].sum() for k in range(3)] + \
+        [0.5 * (r * (v * v).sum(0))[fl].sum()]
+    assert np.allclose(a, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_errors_and_nan_detection():
+    with pytest.raises(lbm.LBMError) as ei:
+        sim = lbm.Simulation(8, 8, 8, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+        sim.step(1)
+    assert ei.value.code == lbm.LBM_ESTATE
+    h = lbm.lbm_create(16, 16, 16, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+    try:
+        small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_bind_memory(h, small, 1024)
+        assert ei.value.code == lbm.LBM_ENOMEM
+        host = np.zeros(lbm.lbm_required_bytes(h), dtype=np.uint8)
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_bind_memory(h, host.ctypes.data // 256 * 256 + 256, host.size - 256)
+        assert ei.value.code in (lbm.LBM_EINVAL, lbm.LBM_ENOMEM)
+    finally:
+        lbm.lbm_destroy(h)
+    sim = lbm.Simulation(8, 8, 8, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+    rho = np.ones((8, 8, 8))
+    rho[3, 4, 5] = np.nan
+    sim.init(rho, np.zeros((3, 8, 8, 8)))
+    sim.step(2)
+    with pytest.raises(lbm.LBMError) as ei:
+        sim.macro()
+    assert ei.value.code == lbm.LBM_ENAN
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 5), (1, 3, 1), (2, 2, 2)])
+def test_degenerate_tiny_grids(shape):
+    """Single-node and single-row periodic grids wrap onto themselves."""
+    nz, ny, nx = shape
+    D = 2 if nz == 1 and shape != (2, 2, 2) else 3
+    rho, u = wl.random_state(nx, ny, nz, D, seed=25)
+    rg, ug, ro, uo = run_pair(D, lbm.LBM_BGK, lbm.LBM_F64, shape, 5, force=(1e-4, 0, 0))
+    assert np.abs(ug - uo).max() < 1e-14 and np.abs(rg - ro).max() < 1e-14
+
+
+def test_launch_accounting():
+    sim = lbm.Simulation(32, 32, 8, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+    rho, u = wl.random_state(32, 32, 8, 3, seed=26)
+    sim.init(rho, u)
+    c0 = lbm.lbm_launch_count(sim.h)
+    sim.step(17)
+    assert lbm.lbm_launch_count(sim.h) - c0 == 17
+    sim.close()
