@@ -238,7 +238,8 @@ LBM_API int lbm_batch_set_stream(lbm_batch b, void* cuda_stream);
 LBM_API int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask);
 /* Guo body force of domain d. */
 LBM_API int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy);
-/* f = f_eq(rho, u) for domain d; rho [ny][nx], u [2][ny][nx]. */
+/* f = f_eq(rho, u) for domain d; rho [ny][nx], u [2][ny][nx].  Every domain
+ * must be initialised before the first lbm_batch_step; afterwards LBM_ESTATE. */
 LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
                                int field_dtype);
 /* Choose block size, tile shape and CTAs per SM by timing a few steps of
@@ -251,6 +252,14 @@ LBM_API int lbm_batch_get_config(lbm_batch b, int* out4);
  * exits and the next synchronising call returns LBM_ETIMEOUT. */
 LBM_API int lbm_batch_step(lbm_batch b, int n);
 LBM_API int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype);
+/* Spin limit of the per-step grid barrier (default 2e7 spins of ~0.1 us,
+ * about two seconds).  A wait that exceeds it ends the launch early and the
+ * next synchronising call returns LBM_ETIMEOUT. */
+LBM_API int lbm_batch_set_wait_limit(lbm_batch b, long long spins);
+/* Fault-injection hook for testing the timeout path: when on, CTA 0 leaves
+ * the first grid barrier of the next launch without arriving, so every other
+ * CTA's bounded wait runs out.  The state after such a launch is incomplete. */
+LBM_API int lbm_batch_inject_missing_arrival(lbm_batch b, int on);
 LBM_API int lbm_batch_sync(lbm_batch b);
 LBM_API long long lbm_batch_launch_count(lbm_batch b);
 LBM_API size_t lbm_batch_nodes(lbm_batch b);
@@ -280,6 +289,9 @@ LBM_API int lbm_mlp_train(const float* X_dev, const double* alpha_dev, int n, co
  * parameter (host, 1394 floats; zeros for fixed entries).  Synchronises. */
 LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const float* params,
                  float* loss, float* grad, void* cuda_stream);
+
+/* Message of the last failed lbm_mlp_* call on this thread. */
+LBM_API const char* lbm_mlp_last_error(void);
 
 /* Forward pass only: alpha guesses for n feature rows (device in and out). */
 LBM_API int lbm_mlp_forward(const float* X_dev, int n, const float* params, float* alpha_dev,

@@ -438,6 +438,9 @@ static void elbm_alpha(const olat* L, const oracle_params* p, const double* f,
         if (g < 0.0) lo = alpha;
         else { hi = alpha; hi_known = 1; }
         double an = (gp > 0.0) ? alpha - g / gp : NAN;
+        /* a step already below the tolerance ends the solve; testing the
+         * bracket first would reject a sub-ulp step at the root itself */
+        if (fabs(an - alpha) <= p->tol * alpha) { alpha = an; status = AL_CONV; break; }
         if (!(an > lo && an < hi)) {
             if (!hi_known && !(an < hi)) {
                 /* Newton points past the positivity limit: is there a root? */

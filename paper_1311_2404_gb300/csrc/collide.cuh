@@ -20,8 +20,8 @@ namespace lbm {
 // LBGK
 // ---------------------------------------------------------------------------
 template <class L, class R>
-__device__ __forceinline__ void bgk_collide(R (&d)[L::Q], const StepParams& p, R& rho_out,
-                                            R (&v)[3])
+__host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R F1, R F2, bool has_force,
+                                            R& rho_out, R (&v)[3])
 {
     R drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
@@ -33,12 +33,10 @@ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], const StepParams& p, R
     }
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
-    const R F0 = (R)p.F[0], F1 = (R)p.F[1], F2 = (R)p.F[2];
     v[0] = (j[0] + R(0.5) * F0) * irho;
     v[1] = (j[1] + R(0.5) * F1) * irho;
     v[2] = (L::D == 3) ? (j[2] + R(0.5) * F2) * irho : R(0);
     const R usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const R om = (R)p.omega;
     const R cf = R(1) - R(0.5) * om;
     const R vF = v[0] * F0 + v[1] * F1 + v[2] * F2;
 #pragma unroll
@@ -47,7 +45,7 @@ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], const StepParams& p, R
         const R eu = L::ex(i) * v[0] + L::ey(i) * v[1] + L::ez(i) * v[2];
         const R feq = wi * (drho + rho * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq));
         R di = d[i] + om * (feq - d[i]);
-        if (p.has_force) {
+        if (has_force) {
             const R eF = L::ex(i) * F0 + L::ey(i) * F1 + L::ez(i) * F2;
             di += cf * wi * (R(3) * (eF - vF) + R(9) * eu * eF);
         }
@@ -97,7 +95,7 @@ __host__ __device__ constexpr int mrt_norm2(int k)
 }
 
 template <class R>
-__device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& rho_out,
+__host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& rho_out,
                                             R (&v)[3])
 {
     using L = D3Q19;
@@ -155,11 +153,11 @@ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& 
 // ELBM
 // ---------------------------------------------------------------------------
 // Entropic equilibrium, Sec. 2.1.3, with the first factor read as
-// 2 - sqrt(1 + 3 u^2) and, on D3Q19, mass and momentum put back along the
-// zeroth and first Hermite directions (variant 0); or the polynomial
-// equilibrium (variant 1).  FP64.
+// 2 - sqrt(1 + 3 u^2) and mass and momentum put back along the zeroth and
+// first Hermite directions (variant 0); or the polynomial equilibrium
+// (variant 1).  FP64.
 template <class L>
-__device__ __forceinline__ void elbm_feq(double rho, const double (&u)[3], int variant,
+__host__ __device__ __forceinline__ void elbm_feq(double rho, const double (&u)[3], int variant,
                                          double (&fe)[L::Q])
 {
     if (variant == 1) {
@@ -193,7 +191,9 @@ __device__ __forceinline__ void elbm_feq(double rho, const double (&u)[3], int v
         }
         fe[i] = q;
     }
-    if (L::D == 3) {
+    {
+        // put the residual mass and momentum back (zero up to rounding on
+        // D2Q9, O(u^3) on D3Q19): the root of g shifts with f_eq's mass defect
         double m0 = 0, m1[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
@@ -217,7 +217,7 @@ __device__ __forceinline__ void elbm_feq(double rho, const double (&u)[3], int v
 // (the termwise form of the H difference; sum Delta_i = 0 removes the
 // constant of dH/df).
 template <class L>
-__device__ __forceinline__ void elbm_g(const double (&f)[L::Q], const double (&x)[L::Q],
+__host__ __device__ __forceinline__ void elbm_g(const double (&f)[L::Q], const double (&x)[L::Q],
                                        double A, double a, double& g, double& gp)
 {
     double s = 0, sp = 0;
@@ -236,7 +236,7 @@ __device__ __forceinline__ void elbm_g(const double (&f)[L::Q], const double (&x
 // FP32 out): t3..t6 = (a_k / rho) / eps^k with a_k = sum f x^k and
 // eps = sqrt(a2 / rho), eps, max x / eps, min x / eps, A / a2.
 template <class L>
-__device__ __forceinline__ void elbm_features(const double (&f)[L::Q], const double (&x)[L::Q],
+__host__ __device__ __forceinline__ void elbm_features(const double (&f)[L::Q], const double (&x)[L::Q],
                                               double rho, double A, double (&feat)[8],
                                               double (&ak)[7])
 {
@@ -271,7 +271,7 @@ __device__ __forceinline__ void elbm_features(const double (&f)[L::Q], const dou
 
 // MLP 8 -> 32 -> 32 -> 1 (tanh), parameters in shared memory (FP32 holding
 // BF16-rounded weights), FP32 accumulation.  Returns the raw output.
-__device__ __forceinline__ float mlp_eval(const float* __restrict__ P, const double (&feat)[8])
+__host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, const double (&feat)[8])
 {
     const float* mean = P;
     const float* istd = P + 8;
@@ -314,7 +314,7 @@ struct AlphaResult {
 // with g(0) = 0).  If the positivity limit hi is reached with g(hi) < 0 there
 // is no root below it and alpha = hi = alpha_max (1 - 1e-10).
 template <class L>
-__device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double (&x)[L::Q], double A,
+__host__ __device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double (&x)[L::Q], double A,
                                   double rho, const StepParams& p, const float* smlp,
                                   double (&feat)[8], bool& have_feat)
 {
@@ -372,6 +372,9 @@ __device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double (&x)[L::
         if (g < 0) lo = a;
         else { hi = a; hi_known = true; }
         double an = (gp > 0) ? a - g / gp : -1.0;
+        // a step below the tolerance is the answer, even when rounding has
+        // collapsed the bracket onto the root
+        if (gp > 0 && fabs(an - a) <= p.tol * a) { a = an; status = ALPHA_CONV; break; }
         if (!(an > lo && an < hi)) {
             if (!hi_known && !(an < hi)) {
                 double gh, gph;
@@ -394,7 +397,7 @@ __device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double (&x)[L::
 // ELBM collision of one node.  d (deviations, compute type R) in/out.
 // Returns the per-node outcome for the counters.
 template <class L, class R>
-__device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const StepParams& p,
+__host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const StepParams& p,
                                                     const float* smlp, R& rho_out, R (&vout)[3],
                                                     double (&feat)[8], bool& have_feat)
 {

@@ -1,0 +1,661 @@
+// Batched ensemble of independent D2Q9 LBGK domains of uneven sizes, advanced
+// by one persistent cooperative launch per lbm_batch_step call.
+//
+// Layout: every domain d owns, inside one arena, its own AB pair of SoA
+// distribution arrays [9][ny][nxp] (x padded to 32), a node-type map and
+// output fields rho, ux, uy.  The work list is the set of tiles (domain,
+// x0, y0) of tw x th nodes over all domains; persistent CTA g owns the
+// contiguous tile range [g T / G, (g+1) T / G).  After each time step all
+// CTAs meet at a grid barrier whose spin is bounded: if it gives up, the CTA
+// records STATUS_TIMEOUT and returns, so a lost arrival ends the launch with
+// an error status instead of a hang.  The per-node update is the same code as
+// the single-domain kernel (pull streaming, half-way bounce-back, LBGK with
+// Guo forcing), so every domain evolves exactly as it would alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "collide.cuh"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+struct DomDev {
+    long long offA, offB, offF, offO;   // byte offsets in the arena
+    long long sq;                       // elements per direction plane
+    int nx, ny, nxp, has_force;
+    float omega, gx, gy, pad;
+};
+
+struct BatchParams {
+    char* base;
+    const DomDev* dom;
+    const int4* tiles;                  // (domain, x0, y0, 0)
+    int ntiles;
+    int nsteps;
+    int cur;                            // 0: state in A regions
+    int th;                             // tile rows
+    unsigned* bar;                      // [0] arrivals, [1] generation
+    unsigned* status;
+    long long wait_limit;               // spins before giving up
+    int withhold;                       // test hook: CTA 0 skips its first arrival
+};
+
+// Bounded grid barrier (generation counter).  Returns false when this CTA
+// must stop (its wait ran out, or it withheld its arrival).
+__device__ bool grid_barrier(const BatchParams& bp, bool skip_arrive)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        ok = 1;
+        volatile unsigned* vgen = bp.bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        if (skip_arrive) {
+            ok = 0;
+        } else {
+            const unsigned prev = atomicAdd(bp.bar, 1u);
+            if (prev == gridDim.x - 1) {
+                atomicExch(bp.bar, 0u);
+                __threadfence();
+                atomicAdd(bp.bar + 1, 1u);
+            } else {
+                long long spins = 0;
+                while (*vgen == gen) {
+                    if (++spins > bp.wait_limit) {
+                        atomicOr(bp.status, STATUS_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <class S>
+__global__ void k_batch(const BatchParams bp)
+{
+    using T = typename S::T;
+    using L = D2Q9;
+    const int G = gridDim.x;
+    const long long t0 = (long long)bp.ntiles * blockIdx.x / G;
+    const long long t1 = (long long)bp.ntiles * (blockIdx.x + 1) / G;
+    int cur = bp.cur;
+    for (int step = 0; step < bp.nsteps; ++step) {
+        const bool out = (step == bp.nsteps - 1);
+        for (long long t = t0; t < t1; ++t) {
+            const int4 tile = bp.tiles[t];
+            const DomDev D = bp.dom[tile.x];
+            const T* __restrict__ A =
+                reinterpret_cast<const T*>(bp.base + (cur == 0 ? D.offA : D.offB));
+            T* __restrict__ B = reinterpret_cast<T*>(bp.base + (cur == 0 ? D.offB : D.offA));
+            const uint8_t* __restrict__ flags = reinterpret_cast<const uint8_t*>(bp.base + D.offF);
+            float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
+            const int x = tile.y + threadIdx.x;
+            if (x >= D.nx) continue;
+            for (int r = threadIdx.y; r < bp.th; r += blockDim.y) {
+                const int y = tile.z + r;
+                if (y >= D.ny) break;
+                const int n = y * D.nxp + x;
+                const unsigned fl = flags[n];
+                if (fl & FLAG_SOLID) {
+                    if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+                    continue;
+                }
+                const int cx[3] = {x == 0 ? D.nx - 1 : x - 1, x, x == D.nx - 1 ? 0 : x + 1};
+                const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
+                                   (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
+                float d[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    d[i] = S::load(A + (size_t)i * D.sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)],
+                                   L::w(i));
+                if (fl & FLAG_NEAR_WALL) {
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+                        if (flags[src] & FLAG_SOLID)
+                            d[i] = S::load(A + (size_t)L::opp(i) * D.sq + n, L::w(L::opp(i)));
+                    }
+                }
+                float rho, v[3];
+                bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
+                if (out) {
+                    o[n] = rho;
+                    o[D.sq + n] = v[0];
+                    o[2 * D.sq + n] = v[1];
+                    if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1]))
+                        atomicOr(bp.status, STATUS_NAN);
+                }
+            }
+        }
+        cur ^= 1;
+        if (step + 1 < bp.nsteps) {
+            const bool skip = bp.withhold && blockIdx.x == 0 && step == 0;
+            if (!grid_barrier(bp, skip)) return;
+        }
+    }
+}
+
+template <class S>
+const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch<S>); }
+
+}  // namespace
+
+struct lbm_batch_ctx {
+    int ndom = 0, dtype = 0;
+    size_t esize = 4;
+    std::vector<DomDev> dom;
+    std::vector<char> inited, has_mask;
+    char* base = nullptr;
+    size_t bytes = 0, off_tables = 0, off_tiles = 0, off_bar = 0, off_stage = 0, stage_bytes = 0;
+    std::vector<int4> tiles;
+    int ntiles = 0;
+    cudaStream_t stream = nullptr;
+    int threads = 256, ctas = 0, tw = 128, th = 8;   // launch configuration
+    int sms = 0, tiles_tw = 0, tiles_th = 0;          // tiles currently uploaded for (tw, th)
+    int cur = 0;
+    long long t = 0, launches = 0, wait_limit = 20000000LL;
+    int withhold = 0;
+    bool use_graph = true;
+    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+static thread_local std::string g_batch_err;
+
+static int bfail(lbm_batch b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_batch_err = buf;
+    return code;
+}
+
+#define BCK(b, call, what)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return bfail((b), LBM_ECUDA, "%s: %s", (what),            \
+                                            cudaGetErrorString(e_));                    \
+    } while (0)
+
+static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static bool dev_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void drop_graphs(lbm_batch b)
+{
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+static const void* kernel_for(int dtype)
+{
+    return dtype == LBM_F16S ? batch_kernel_ptr<StoreF16S>() : batch_kernel_ptr<StoreF32S>();
+}
+
+// Build and upload the tile list for tile shape (tw, th).
+static int upload_tiles(lbm_batch b, int tw, int th)
+{
+    if (b->tiles_tw == tw && b->tiles_th == th) return LBM_OK;
+    std::vector<int4> tl;
+    for (int d = 0; d < b->ndom; ++d)
+        for (int y0 = 0; y0 < b->dom[d].ny; y0 += th)
+            for (int x0 = 0; x0 < b->dom[d].nx; x0 += tw) tl.push_back(make_int4(d, x0, y0, 0));
+    const size_t cap = b->off_bar - b->off_tiles;
+    if (tl.size() * sizeof(int4) > cap)
+        return bfail(b, LBM_EINVAL, "tile list of %zu tiles exceeds its reserve", tl.size());
+    BCK(b, cudaMemcpy(b->base + b->off_tiles, tl.data(), tl.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice),
+        "upload tiles");
+    b->ntiles = (int)tl.size();
+    b->tiles_tw = tw;
+    b->tiles_th = th;
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+static int max_ctas(lbm_batch b, int threads)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(b->dtype), threads, 0);
+    return per_sm * b->sms;
+}
+
+static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
+{
+    BatchParams bp;
+    bp.base = b->base;
+    bp.dom = reinterpret_cast<const DomDev*>(b->base + b->off_tables);
+    bp.tiles = reinterpret_cast<const int4*>(b->base + b->off_tiles);
+    bp.ntiles = b->ntiles;
+    bp.nsteps = nsteps;
+    bp.cur = from;
+    bp.th = b->th;
+    bp.bar = reinterpret_cast<unsigned*>(b->base + b->off_bar);
+    bp.status = reinterpret_cast<unsigned*>(b->base + b->off_bar + 8);
+    bp.wait_limit = b->wait_limit;
+    bp.withhold = b->withhold;
+    cudaError_t e = cudaMemsetAsync(bp.bar, 0, 8, b->stream);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(b->ctas);
+    cfg.blockDim = dim3(b->tw, b->threads / b->tw);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {&bp};
+    return cudaLaunchKernelExC(&cfg, kernel_for(b->dtype), args);
+}
+
+extern "C" {
+
+int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, int dtype,
+                     lbm_batch* out)
+{
+    if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ndom < 1 || !nx || !ny || !tau) return bfail(nullptr, LBM_EINVAL, "bad arguments");
+    if (dtype != LBM_F32S && dtype != LBM_F16S)
+        return bfail(nullptr, LBM_EINVAL, "batch storage must be LBM_F32S or LBM_F16S");
+    lbm_batch b = new lbm_batch_ctx();
+    b->ndom = ndom;
+    b->dtype = dtype;
+    b->esize = dtype == LBM_F16S ? 2 : 4;
+    b->dom.resize(ndom);
+    b->inited.assign(ndom, 0);
+    b->has_mask.assign(ndom, 0);
+    size_t o = 0, max_nodes = 0, max_tiles = 0;
+    for (int d = 0; d < ndom; ++d) {
+        if (nx[d] < 1 || ny[d] < 1 || !(tau[d] > 0.5) || !(tau[d] < 1e6)) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "domain %d: bad size or tau", d);
+        }
+        DomDev& D = b->dom[d];
+        D.nx = nx[d];
+        D.ny = ny[d];
+        D.nxp = (nx[d] + 31) / 32 * 32;
+        D.sq = ((long long)D.nxp * D.ny + 127) / 128 * 128;
+        if (D.sq > 0x7fffffffLL / 16) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "domain %d too large", d);
+        }
+        D.omega = (float)(1.0 / tau[d]);
+        D.gx = D.gy = 0.f;
+        D.has_force = 0;
+        D.pad = 0.f;
+        D.offA = (long long)o; o = a256(o + 9 * D.sq * b->esize);
+        D.offB = (long long)o; o = a256(o + 9 * D.sq * b->esize);
+        D.offF = (long long)o; o = a256(o + D.sq);
+        D.offO = (long long)o; o = a256(o + 3 * D.sq * 4);
+        max_nodes = std::max(max_nodes, (size_t)nx[d] * ny[d]);
+        // smallest tile shape the autotuner tries is 32 x 1
+        max_tiles += (size_t)((nx[d] + 31) / 32) * ny[d];
+    }
+    b->off_tables = o; o = a256(o + sizeof(DomDev) * ndom);
+    b->off_tiles = o; o = a256(o + sizeof(int4) * max_tiles);
+    b->off_bar = o; o = a256(o + 64);
+    b->off_stage = o;
+    b->stage_bytes = a256(max_nodes * 3 * 8);
+    o = a256(o + b->stage_bytes);
+    b->bytes = o;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, b->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(nullptr, LBM_ENOMEM, "cudaMalloc(%zu): %s", o, cudaGetErrorString(e));
+    }
+    b->base = static_cast<char*>(p);
+    e = cudaMemset(b->base, 0, b->bytes);   // flags = fluid, f = w (rest), status clear
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->base + b->off_tables, b->dom.data(), sizeof(DomDev) * ndom,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        delete b;
+        return bfail(nullptr, LBM_ECUDA, "initialise arena: %s", cudaGetErrorString(e));
+    }
+    int r = upload_tiles(b, b->tw, b->th);
+    if (r) {
+        std::string m = b->err;
+        cudaFree(p);
+        delete b;
+        return bfail(nullptr, r, "%s", m.c_str());
+    }
+    b->ctas = std::min(max_ctas(b, b->threads), std::max(1, b->ntiles));
+    if (b->ctas < 1) {
+        cudaFree(p);
+        delete b;
+        return bfail(nullptr, LBM_ECUDA, "batched kernel cannot be resident");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b)
+{
+    if (!b) return LBM_OK;
+    drop_graphs(b);
+    if (b->base) cudaFree(b->base);
+    delete b;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(lbm_batch b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+int lbm_batch_set_stream(lbm_batch b, void* stream)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (b->stream != static_cast<cudaStream_t>(stream)) drop_graphs(b);
+    b->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (d < 0 || d >= b->ndom || !mask) return bfail(b, LBM_EINVAL, "bad domain or mask");
+    const DomDev& D = b->dom[d];
+    const size_t n = (size_t)D.nx * D.ny;
+    uint8_t* stage = reinterpret_cast<uint8_t*>(b->base + b->off_stage);
+    BCK(b, cudaMemcpyAsync(stage, mask, n, dev_ptr(mask) ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice, b->stream),
+        "copy mask");
+    BCK(b, launch_flags(0, stage, reinterpret_cast<uint8_t*>(b->base + D.offF), D.nx, D.ny, 1,
+                        D.nxp, b->stream),
+        "node-type map kernel");
+    b->launches += 1;
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    b->has_mask[d] = 1;
+    return LBM_OK;
+}
+
+int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (d < 0 || d >= b->ndom || !std::isfinite(fx) || !std::isfinite(fy))
+        return bfail(b, LBM_EINVAL, "bad domain or force");
+    DomDev& D = b->dom[d];
+    D.gx = (float)fx;
+    D.gy = (float)fy;
+    D.has_force = (fx != 0.0 || fy != 0.0);
+    BCK(b, cudaMemcpy(b->base + b->off_tables + sizeof(DomDev) * d, &D, sizeof(DomDev),
+                      cudaMemcpyHostToDevice),
+        "upload domain table");
+    return LBM_OK;
+}
+
+int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
+                               int field_dtype)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (d < 0 || d >= b->ndom || !rho || !u) return bfail(b, LBM_EINVAL, "bad arguments");
+    if (field_dtype != LBM_FIELD_F32 && field_dtype != LBM_FIELD_F64)
+        return bfail(b, LBM_EINVAL, "unknown field dtype");
+    if (b->t != 0)
+        return bfail(b, LBM_ESTATE, "initialise every domain before the first step");
+    const DomDev& D = b->dom[d];
+    const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
+    const size_t nb = (size_t)D.nx * D.ny * fs;
+    char* stage = b->base + b->off_stage;
+    const void* dr = rho;
+    const void* du = u;
+    if (!dev_ptr(rho)) {
+        BCK(b, cudaMemcpyAsync(stage, rho, nb, cudaMemcpyHostToDevice, b->stream), "copy rho");
+        dr = stage;
+    }
+    if (!dev_ptr(u)) {
+        BCK(b, cudaMemcpyAsync(stage + nb, u, 2 * nb, cudaMemcpyHostToDevice, b->stream),
+            "copy u");
+        du = stage + nb;
+    }
+    BCK(b, launch_init(0, b->dtype, dr, du, field_dtype == LBM_FIELD_F32, b->base + D.offA, D.nx,
+                       D.ny, 1, D.nxp, D.sq, 0, 0, b->stream),
+        "init kernel");
+    b->launches += 1;
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    b->inited[d] = 1;
+    b->cur = 0;
+    b->t = 0;
+    return LBM_OK;
+}
+
+static int check_ready(lbm_batch b)
+{
+    for (int d = 0; d < b->ndom; ++d)
+        if (!b->inited[d]) return bfail(b, LBM_ESTATE, "domain %d not initialised", d);
+    return LBM_OK;
+}
+
+static int step_impl(lbm_batch b, int n)
+{
+    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th);
+    if (b->use_graph && b->stream != nullptr && !b->withhold) {
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g;
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+                "begin capture");
+            cudaError_t le = launch_batch(b, n, b->cur);
+            cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (le == cudaSuccess && ce == cudaSuccess) {
+                cudaGraphExec_t ge;
+                cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (ie == cudaSuccess) it = b->graphs.emplace(key, ge).first;
+            } else if (ce == cudaSuccess) {
+                cudaGraphDestroy(g);
+            }
+            if (it == b->graphs.end()) {   // capture not possible: launch directly
+                cudaGetLastError();
+                b->use_graph = false;
+            }
+        }
+        if (it != b->graphs.end()) {
+            BCK(b, cudaGraphLaunch(it->second, b->stream), "graph launch");
+            b->launches += 1;
+            b->cur ^= (n & 1);
+            b->t += n;
+            return LBM_OK;
+        }
+    }
+    BCK(b, launch_batch(b, n, b->cur), "persistent batched kernel");
+    b->launches += 1;
+    b->cur ^= (n & 1);
+    b->t += n;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int n)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (n < 1) return bfail(b, LBM_EINVAL, "n must be >= 1");
+    int r = check_ready(b);
+    if (r) return r;
+    return step_impl(b, n);
+}
+
+int lbm_batch_autotune(lbm_batch b)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    int r = check_ready(b);
+    if (r) return r;
+    // keep the state: copy the per-domain regions aside and restore them
+    const size_t span = b->off_tables;     // every per-domain region lies below the tables
+    void* save = nullptr;
+    BCK(b, cudaMalloc(&save, span), "autotune backup");
+    BCK(b, cudaMemcpyAsync(save, b->base, span, cudaMemcpyDeviceToDevice, b->stream), "backup");
+    const int saved_cur = b->cur;
+    const long long saved_t = b->t;
+    const bool saved_graph = b->use_graph;
+    b->use_graph = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th;
+    const int steps = 4;
+    for (int threads : {128, 256, 512})
+        for (int tw : {64, 128, 256}) {
+            if (tw > threads) continue;
+            const int mc = max_ctas(b, threads);
+            if (mc < 1) continue;
+            for (int th : {2, 4, 8, 16}) {
+                if (th < threads / tw) continue;
+                if (upload_tiles(b, tw, th)) continue;
+                const int per_sm = std::max(1, mc / b->sms);
+                for (int k = 1; k <= per_sm; k *= 2) {
+                    b->threads = threads; b->tw = tw; b->th = th;
+                    b->ctas = std::min(k * b->sms, b->ntiles);
+                    if (launch_batch(b, 1, b->cur) != cudaSuccess) { cudaGetLastError(); continue; }
+                    cudaEventRecord(e0, b->stream);
+                    cudaError_t le = launch_batch(b, steps, b->cur);
+                    cudaEventRecord(e1, b->stream);
+                    if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) { best = ms; bt = threads; bc = b->ctas; bw = tw; bh = th; }
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->threads = bt; b->ctas = bc;
+    int ur = upload_tiles(b, bw, bh);
+    b->tw = bw; b->th = bh;
+    BCK(b, cudaMemcpyAsync(b->base, save, span, cudaMemcpyDeviceToDevice, b->stream), "restore");
+    BCK(b, cudaMemsetAsync(b->base + b->off_bar, 0, 64, b->stream), "clear status");
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    cudaFree(save);
+    b->cur = saved_cur;
+    b->t = saved_t;
+    b->use_graph = saved_graph;
+    drop_graphs(b);
+    return ur;
+}
+
+int lbm_batch_get_config(lbm_batch b, int* out4)
+{
+    if (!b || !out4) return bfail(b, LBM_EINVAL, "NULL argument");
+    out4[0] = b->threads;
+    out4[1] = b->ctas;
+    out4[2] = b->tw;
+    out4[3] = b->th;
+    return LBM_OK;
+}
+
+int lbm_batch_set_wait_limit(lbm_batch b, long long spins)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (spins < 1) return bfail(b, LBM_EINVAL, "spins must be >= 1");
+    b->wait_limit = spins;
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+int lbm_batch_inject_missing_arrival(lbm_batch b, int on)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    b->withhold = on ? 1 : 0;
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch b)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    unsigned st = 0;
+    BCK(b, cudaMemcpyAsync(&st, b->base + b->off_bar + 8, 4, cudaMemcpyDeviceToHost, b->stream),
+        "read status");
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    if (st & STATUS_TIMEOUT) {
+        BCK(b, cudaMemset(b->base + b->off_bar + 8, 0, 4), "clear status");
+        return bfail(b, LBM_ETIMEOUT, "a grid-barrier wait gave up; the state is incomplete");
+    }
+    if (st & STATUS_NAN) return bfail(b, LBM_ENAN, "non-finite rho or v on an output step");
+    return LBM_OK;
+}
+
+int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (d < 0 || d >= b->ndom) return bfail(b, LBM_EINVAL, "bad domain");
+    if (field_dtype != LBM_FIELD_F32 && field_dtype != LBM_FIELD_F64)
+        return bfail(b, LBM_EINVAL, "unknown field dtype");
+    if (b->t == 0) return bfail(b, LBM_ESTATE, "no step has produced output yet");
+    const DomDev& D = b->dom[d];
+    const int f32 = field_dtype == LBM_FIELD_F32;
+    const size_t fs = f32 ? 4 : 8;
+    const size_t nb = (size_t)D.nx * D.ny * fs;
+    char* stage = b->base + b->off_stage;
+    struct { void* dst; long long off; int nf; } parts[2] = {{rho, 0, 1}, {u, D.sq * 4, 2}};
+    for (auto& pt : parts) {
+        if (!pt.dst) continue;
+        const bool dv = dev_ptr(pt.dst);
+        void* outp = dv ? pt.dst : stage;
+        BCK(b, launch_pack(0, b->base + D.offO + pt.off, f32, outp, pt.nf, D.nx, D.ny, 1, D.nxp,
+                           D.sq, b->stream),
+            "pack kernel");
+        b->launches += 1;
+        if (!dv)
+            BCK(b, cudaMemcpyAsync(pt.dst, outp, nb * pt.nf, cudaMemcpyDeviceToHost, b->stream),
+                "copy out");
+        BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    }
+    return lbm_batch_sync(b);
+}
+
+long long lbm_batch_launch_count(lbm_batch b) { return b ? b->launches : 0; }
+
+size_t lbm_batch_nodes(lbm_batch b)
+{
+    if (!b) return 0;
+    size_t n = 0;
+    for (const DomDev& D : b->dom) n += (size_t)D.nx * D.ny;
+    return n;
+}
+
+}  // extern "C"

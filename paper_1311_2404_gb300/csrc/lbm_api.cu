@@ -429,8 +429,8 @@ static StepParams make_params(lbm_ctx* h)
     p.has_force = (h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0);
     for (int k = 0; k < 19; ++k) {
         const double n2 = h->lattice == LBM_D3Q19 ? (double)mrt_norm2(k) : 1.0;
-        p.mrt_c[k] = (float)(h->s[k] / n2);
-        p.mrt_cf[k] = (float)((1.0 - 0.5 * h->s[k]) / n2);
+        p.mrt_c[k] = h->s[k] / n2;
+        p.mrt_cf[k] = (1.0 - 0.5 * h->s[k]) / n2;
     }
     p.alpha_mode = h->alpha_mode; p.max_iter = h->max_iter;
     p.guard_steps = h->guard_steps; p.feq_variant = h->feq_variant;

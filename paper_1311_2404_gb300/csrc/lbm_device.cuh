@@ -130,8 +130,8 @@ struct StepParams {
     int has_force;
     double omega;              // 1/tau
     double F[3];               // body force
-    float mrt_c[19];           // s_k / |M_k|^2
-    float mrt_cf[19];          // (1 - s_k/2) / |M_k|^2
+    double mrt_c[19];          // s_k / |M_k|^2
+    double mrt_cf[19];         // (1 - s_k/2) / |M_k|^2
     // ELBM
     int alpha_mode, max_iter, guard_steps, feq_variant;
     double tol, skip_eps, guard_tol;

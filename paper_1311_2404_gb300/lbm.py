@@ -92,12 +92,15 @@ _PROTOS = {
     "lbm_batch_step": (_i, [_vp, _i]),
     "lbm_batch_get_macro": (_i, [_vp, _i, _vp, _vp, _i]),
     "lbm_batch_sync": (_i, [_vp]),
+    "lbm_batch_set_wait_limit": (_i, [_vp, _ll]),
+    "lbm_batch_inject_missing_arrival": (_i, [_vp, _i]),
     "lbm_batch_launch_count": (_ll, [_vp]),
     "lbm_batch_nodes": (_sz, [_vp]),
     "lbm_elbm_collect_pairs": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(_i)]),
     "lbm_mlp_train": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "lbm_mlp_grad": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "lbm_mlp_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "lbm_mlp_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_L, _name)
@@ -128,9 +131,11 @@ def _ptr(x):
     raise TypeError(f"cannot pass {type(x)} as a pointer")
 
 
-def _check(code, handle=None, batch=False):
+def _check(code, handle=None, batch=False, mlp=False):
     if code != LBM_OK:
-        if batch:
+        if mlp:
+            msg = _L.lbm_mlp_last_error()
+        elif batch:
             msg = _L.lbm_batch_last_error(handle)
         else:
             msg = _L.lbm_last_error(handle)
@@ -284,7 +289,7 @@ def lbm_elbm_collect_pairs(h, stride, X_dev, y_dev):
 def lbm_mlp_train(X_dev, alpha_dev, n, cfg, params, loss_out, stream=None):
     c = np.ascontiguousarray(cfg, dtype=np.float64)
     _check(_L.lbm_mlp_train(_ptr(X_dev), _ptr(alpha_dev), int(n), _ptr(c), _ptr(params),
-                            _ptr(loss_out), stream), None)
+                            _ptr(loss_out), stream), mlp=True)
 
 
 def lbm_mlp_grad(X_dev, t_dev, n, params, stream=None):
@@ -292,13 +297,17 @@ def lbm_mlp_grad(X_dev, t_dev, n, params, stream=None):
     loss = np.zeros(1, dtype=np.float32)
     grad = np.zeros(MLP_NPARAM, dtype=np.float32)
     _check(_L.lbm_mlp_grad(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss), _ptr(grad),
-                           stream), None)
+                           stream), mlp=True)
     return float(loss[0]), grad
+
+
+def lbm_mlp_last_error():
+    return (_L.lbm_mlp_last_error() or b"").decode()
 
 
 def lbm_mlp_forward(X_dev, n, params, alpha_dev, stream=None):
     p = np.ascontiguousarray(params, dtype=np.float32)
-    _check(_L.lbm_mlp_forward(_ptr(X_dev), int(n), _ptr(p), _ptr(alpha_dev), stream), None)
+    _check(_L.lbm_mlp_forward(_ptr(X_dev), int(n), _ptr(p), _ptr(alpha_dev), stream), mlp=True)
 
 
 # ---- batch ABI --------------------------------------------------------------
@@ -352,6 +361,14 @@ def lbm_batch_get_macro(b, d, rho, u):
     ref = rho if rho is not None else u
     _check(_L.lbm_batch_get_macro(b, int(d), _ptr(rho), _ptr(u), _field_dtype(ref)), b,
            batch=True)
+
+
+def lbm_batch_set_wait_limit(b, spins):
+    _check(_L.lbm_batch_set_wait_limit(b, int(spins)), b, batch=True)
+
+
+def lbm_batch_inject_missing_arrival(b, on):
+    _check(_L.lbm_batch_inject_missing_arrival(b, int(bool(on))), b, batch=True)
 
 
 def lbm_batch_sync(b):
