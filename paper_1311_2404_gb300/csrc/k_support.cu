@@ -68,23 +68,27 @@ __global__ void k_init(const FT* __restrict__ rho, const FT* __restrict__ u, voi
         r = (double)rho[nd];
         for (int a = 0; a < L::D; ++a) uu[a] = (double)u[a * N + nd];
     }
-    double dev[L::Q];   // f_eq - w
+    using R = typename S::R;
     if (entropic) {
+        double dev[L::Q];   // f_eq - w, FP64 (the entropic form is only used by ELBM)
         elbm_feq<L>(r, uu, feq_variant, dev);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) dev[i] -= L::w(i);
+        for (int i = 0; i < L::Q; ++i)
+            A[(size_t)i * sq + n] = S::encode((R)(dev[i] - L::w(i)), L::w(i));
     } else {
-        // Eq. equilibrium in deviation form: w (rho - 1 + rho (3 eu + 9/2 eu^2 - 3/2 u^2))
-        const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+        // Eq. equilibrium in deviation form, w (rho - 1 + rho (3 eu + 9/2 eu^2 - 3/2 u^2)),
+        // in the storage's compute type (FP64 arithmetic runs at a small
+        // fraction of the FP32 rate on this GPU)
+        const R rr = (R)r, dr = (R)(r - 1.0);
+        const R u0 = (R)uu[0], u1 = (R)uu[1], u2 = (R)uu[2];
+        const R usq = u0 * u0 + u1 * u1 + u2 * u2;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const double eu = L::ex(i) * uu[0] + L::ey(i) * uu[1] + L::ez(i) * uu[2];
-            dev[i] = L::w(i) * ((r - 1.0) + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+            const R eu = L::ex(i) * u0 + L::ey(i) * u1 + L::ez(i) * u2;
+            const R dev = (R)L::w(i) * (dr + rr * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq));
+            A[(size_t)i * sq + n] = S::encode(dev, L::w(i));
         }
     }
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-        A[(size_t)i * sq + n] = S::encode((typename S::R)dev[i], L::w(i));
 }
 
 template <class L, class S>

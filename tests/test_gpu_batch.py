@@ -1,0 +1,147 @@
+"""Batched ensemble of uneven D2Q9 channels in one persistent launch (GPU).
+
+- every domain equals the same domain run alone through the single-domain
+  path, bitwise (same per-node arithmetic, FP32S and FP16S storage);
+- sampled domains match the FP64 oracle within 1e-5 (FP32S);
+- the autotuner leaves the state untouched and returns a valid configuration;
+- graph replay equals direct launches; one launch per lbm_batch_step call;
+- a withheld barrier arrival makes the bounded wait run out and the next
+  synchronising call report LBM_ETIMEOUT, with the context still usable.
+"""
+import numpy as np
+import pytest
+
+import analytic as an
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1311_2404_gb300 import lbm  # noqa: E402
+from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
+
+
+def _specs(k=6, seed=99):
+    specs = wl.batch_channel_specs(k, nmin=33, nmax=200, seed=seed)
+    return specs
+
+
+def _init_state(spec, seed):
+    rho, u = wl.random_state(spec["nx"], spec["ny"], 1, 2, seed=seed, u_amp=0.03, rho_amp=0.01)
+    return rho, u
+
+
+def _make_batch(specs, dtype, stream=None):
+    b = lbm.lbm_batch_create([s["nx"] for s in specs], [s["ny"] for s in specs],
+                             [s["tau"] for s in specs], dtype)
+    if stream is not None:
+        lbm.lbm_batch_set_stream(b, stream)
+    for d, s in enumerate(specs):
+        lbm.lbm_batch_set_geometry(b, d, wl.batch_channel_mask(s))
+        lbm.lbm_batch_set_force(b, d, s["gx"], 0.0)
+        rho, u = _init_state(s, 100 + d)
+        lbm.lbm_batch_init_equilibrium(b, d, rho, u)
+    return b
+
+
+def _batch_fields(b, specs):
+    out = []
+    for d, s in enumerate(specs):
+        r = np.empty((1, s["ny"], s["nx"]))
+        u = np.empty((2, 1, s["ny"], s["nx"]))
+        lbm.lbm_batch_get_macro(b, d, r, u)
+        out.append((r, u))
+    return out
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F32S, lbm.LBM_F16S])
+def test_batch_equals_single_domains_bitwise(dtype):
+    specs = _specs()
+    steps = 25
+    s = torch.cuda.Stream()
+    b = _make_batch(specs, dtype, s.cuda_stream)
+    lbm.lbm_batch_step(b, steps)
+    got = _batch_fields(b, specs)
+    assert lbm.lbm_batch_launch_count(b) >= 1
+    lbm.lbm_batch_destroy(b)
+    for d, sp in enumerate(specs):
+        sim = lbm.Simulation(sp["nx"], sp["ny"], 1, lbm.LBM_D2Q9, lbm.LBM_BGK, sp["tau"], dtype)
+        sim.set_geometry(wl.batch_channel_mask(sp))
+        sim.set_force(sp["gx"], 0.0)
+        rho, u = _init_state(sp, 100 + d)
+        sim.init(rho, u)
+        sim.step(steps)
+        r, v = sim.macro()
+        sim.close()
+        assert np.array_equal(r, got[d][0]) and np.array_equal(v, got[d][1]), d
+
+
+def test_batch_vs_oracle_sampled():
+    specs = _specs()
+    steps = 30
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_step(b, steps)
+    got = _batch_fields(b, specs)
+    lbm.lbm_batch_destroy(b)
+    for d in (0, 3):
+        sp = specs[d]
+        mask = wl.batch_channel_mask(sp)
+        rho, u = _init_state(sp, 100 + d)
+        p = oracle.make_params(sp["nx"], sp["ny"], 1, D=2, model=oracle.BGK, tau=sp["tau"],
+                               force=(sp["gx"], 0, 0))
+        F = oracle.init(p, rho, u)
+        ro, uo, _, _ = oracle.run(p, F, steps, mask)
+        assert an.rel_l2(got[d][1], uo) < 1e-5 and an.rel_l2(got[d][0], ro) < 1e-5
+
+
+def test_autotune_keeps_state_and_graph_equals_direct():
+    specs = _specs(5, seed=7)
+    s = torch.cuda.Stream()
+    b1 = _make_batch(specs, lbm.LBM_F32S, s.cuda_stream)
+    lbm.lbm_batch_autotune(b1)
+    cfg = lbm.lbm_batch_get_config(b1)
+    assert cfg[0] in (128, 256, 512) and cfg[1] >= 1 and cfg[2] in (64, 128, 256)
+    lbm.lbm_batch_step(b1, 7)
+    lbm.lbm_batch_step(b1, 7)
+    a = _batch_fields(b1, specs)
+    lbm.lbm_batch_destroy(b1)
+    b2 = _make_batch(specs, lbm.LBM_F32S)          # legacy stream: direct launches
+    lbm.lbm_batch_step(b2, 14)
+    c = _batch_fields(b2, specs)
+    lbm.lbm_batch_destroy(b2)
+    for (r1, u1), (r2, u2) in zip(a, c):
+        assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
+
+
+def test_barrier_timeout_reports_and_context_survives():
+    specs = _specs(4, seed=8)
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_set_wait_limit(b, 20000)        # a few ms of bounded spinning
+    lbm.lbm_batch_inject_missing_arrival(b, 1)
+    lbm.lbm_batch_step(b, 3)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_sync(b)
+    assert ei.value.code == lbm.LBM_ETIMEOUT
+    lbm.lbm_batch_destroy(b)
+    # the context is intact: a fresh batch runs normally
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_step(b, 3)
+    lbm.lbm_batch_sync(b)
+    lbm.lbm_batch_destroy(b)
+    x = torch.ones(4, device="cuda") * 2
+    assert float(x.sum()) == 8.0
+
+
+def test_batch_errors():
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_create([10, 0], [10, 10], [0.6, 0.6], lbm.LBM_F32S)
+    assert ei.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_batch_create([10], [10], [0.6], lbm.LBM_F64)
+    b = lbm.lbm_batch_create([40, 50], [30, 20], [0.6, 0.7], lbm.LBM_F32S)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_step(b, 1)                  # domains not initialised
+    assert ei.value.code == lbm.LBM_ESTATE
+    lbm.lbm_batch_destroy(b)

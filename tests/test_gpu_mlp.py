@@ -1,0 +1,150 @@
+"""The learned ELBM alpha guess (GPU).
+
+- GPU gradient of the surrogate's loss equals the FP64 reference's (which is
+  itself pinned to finite differences) within 1e-4 relative; forward within
+  1e-5.
+- Training on the GPU lowers the loss.
+- End to end: pairs from a Newton-solved ELBM run, GPU training, then the
+  MLP-guarded solve reproduces Newton's alpha (1e-8) with fewer g
+  evaluations per node, and the oracle running the same guarded mode with the
+  same BF16-rounded weights agrees on the fields.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mlp_oracle as mo
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1311_2404_gb300 import lbm  # noqa: E402
+from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
+
+
+def _rand(seed=0, B=1000):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((B, 8)) * np.array([1, 2, 3, 4, 1e-2, 2, 2, 1.0])
+    X[:, 4] = np.abs(X[:, 4]) + 1e-3
+    P = mo.init_params(seed, X.mean(0), 1.0 / X.std(0), 0.5)
+    P[mo.O_B1:mo.O_W2] = rng.standard_normal(mo.NH) * 0.1
+    t = rng.standard_normal(B) * 0.3
+    return X.astype(np.float32), P.astype(np.float32), t.astype(np.float32)
+
+
+def test_gradient_matches_fp64_reference():
+    X, P, t = _rand()
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    loss, g = lbm.lbm_mlp_grad(Xd, td, len(t), P)
+    lref, gref = mo.loss_and_grad(P.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lref) <= 1e-5 * abs(lref)
+    sl = slice(mo.TRAIN_LO, mo.TRAIN_HI)
+    rel = np.abs(g[sl] - gref[sl]).max() / np.abs(gref[sl]).max()
+    assert rel < 1e-4
+    assert np.all(g[:mo.TRAIN_LO] == 0)
+
+
+def test_forward_matches_fp64_reference():
+    X, P, _ = _rand(1)
+    Xd = torch.from_numpy(X).cuda()
+    out = torch.empty(len(X), dtype=torch.float32, device="cuda")
+    lbm.lbm_mlp_forward(Xd, len(X), P, out)
+    ref = mo.alpha_guess(P.astype(np.float64), X.astype(np.float64))
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+def test_training_lowers_loss():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((8192, 8)).astype(np.float32)
+    X[:, 4] = np.abs(X[:, 4]) + 0.1
+    alpha = 2.0 + 0.5 * X[:, 4] * (np.tanh(X[:, 0]) * 0.5 + 0.2 * X[:, 1])
+    P = mo.init_params(3, X.mean(0), 1.0 / X.std(0), 0.5).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    ad = torch.from_numpy(alpha.astype(np.float64)).cuda()
+    loss = np.zeros(30, dtype=np.float32)
+    lbm.lbm_mlp_train(Xd, ad, len(X), [30, 256, 3e-3, 5], P, loss)
+    assert loss[-1] < 0.05 * loss[0]
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """Pairs from a Newton-solved D3Q19 ELBM decaying-turbulence run (48^3,
+    tau 0.5005), trained on the GPU."""
+    n, tau = 48, 0.5005
+    rho, u = wl.turbulence(n, k0=4.0, u_rms=0.04)
+    sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
+    lbm.lbm_set_elbm(sim.h, lbm.LBM_ALPHA_NEWTON, 1e-12, 20, 1e-4)
+    sim.init(rho, u)
+    Xs, ys = [], []
+    cap = 200000
+    X = torch.empty((cap, 8), dtype=torch.float32, device="cuda")
+    y = torch.empty(cap, dtype=torch.float64, device="cuda")
+    for k in range(6):
+        sim.step(3)
+        cnt = lbm.lbm_elbm_collect_pairs(sim.h, 1, X, y)
+        Xs.append(X[:cnt].clone())
+        ys.append(y[:cnt].clone())
+    state, t = sim.state()
+    sim.close()
+    Xa = torch.cat(Xs)
+    ya = torch.cat(ys)
+    Xh = Xa.cpu().numpy().astype(np.float64)
+    tgt_scale = float(np.std((ya.cpu().numpy() - 2.0) / Xh[:, 4]))
+    P = mo.init_params(11, Xh.mean(0), 1.0 / (Xh.std(0) + 1e-12), tgt_scale).astype(np.float32)
+    loss = np.zeros(20, dtype=np.float32)
+    lbm.lbm_mlp_train(Xa, ya, len(ya), [20, 1024, 2e-3, 13], P, loss)
+    return dict(P=P, loss=loss, state=state, t=t, n=n, tau=tau, npairs=len(ya))
+
+
+def test_learned_alpha_gain_and_parity(trained):
+    P, n, tau = trained["P"], trained["n"], trained["tau"]
+    assert trained["npairs"] > 10000
+    assert trained["loss"][-1] < trained["loss"][0]
+    res = {}
+    for mode in (lbm.LBM_ALPHA_NEWTON, lbm.LBM_ALPHA_SERIES_GUARDED, lbm.LBM_ALPHA_MLP_GUARDED):
+        sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
+        lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-4)
+        lbm.lbm_load_alpha_mlp(sim.h, P)
+        lbm.lbm_set_alpha_output(sim.h, 1)
+        sim.set_state(trained["state"], trained["t"])
+        sim.step(1)
+        a = np.empty((n, n, n))
+        lbm.lbm_get_alpha(sim.h, a)
+        st = lbm.lbm_get_elbm_stats(sim.h)
+        sim.close()
+        res[mode] = (a, st[0] / st[5], st[4] / st[5])
+    a_n, ev_n, _ = res[lbm.LBM_ALPHA_NEWTON]
+    a_m, ev_m, acc_m = res[lbm.LBM_ALPHA_MLP_GUARDED]
+    a_s, ev_s, _ = res[lbm.LBM_ALPHA_SERIES_GUARDED]
+    assert np.abs(a_m - a_n).max() < 1e-8
+    assert np.abs(a_s - a_n).max() < 1e-8
+    assert acc_m > 0.9                     # most nodes accepted from the guess
+    assert ev_m < ev_n                     # fewer FP64 g evaluations than Newton from 2
+    print(f"evals/node: newton {ev_n:.3f} series {ev_s:.3f} mlp {ev_m:.3f}; mlp accepted {acc_m:.3f}")
+
+
+def test_mlp_guarded_oracle_parity(trained):
+    """The oracle's guarded mode with the same (BF16-rounded) weights in FP64
+    gives the same fields as the GPU within 1e-5 (FP32S storage)."""
+    P = trained["P"].astype(np.float32).copy()
+    Pb = torch.from_numpy(P[16:1393]).bfloat16().float().numpy()
+    Pr = P.astype(np.float64)
+    Pr[16:1393] = Pb
+    n, tau, steps = 20, 0.5005, 5
+    rho, u = wl.turbulence(n, k0=4.0, u_rms=0.04)
+    sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
+    lbm.lbm_set_elbm(sim.h, lbm.LBM_ALPHA_MLP_GUARDED, 1e-12, 20, 1e-4)
+    lbm.lbm_load_alpha_mlp(sim.h, P)
+    sim.init(rho, u)
+    sim.step(steps)
+    rg, ug = sim.macro()
+    sim.close()
+    p = oracle.make_params(n, n, n, D=3, model=oracle.ELBM, tau=tau, skip_eps=1e-4,
+                           alpha_mode=oracle.MLP_GUARDED, mlp=Pr)
+    F = oracle.init(p, rho, u)
+    ro, uo, _, _ = oracle.run(p, F, steps)
+    import analytic as an
+    assert an.rel_l2(ug, uo) < 1e-5 and an.rel_l2(rg, ro) < 1e-5
