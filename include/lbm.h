@@ -290,6 +290,29 @@ LBM_API int lbm_mlp_train(const float* X_dev, const double* alpha_dev, int n, co
 LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const float* params,
                  float* loss, float* grad, void* cuda_stream);
 
+/* Same as lbm_mlp_grad, but allocates nothing.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc, such as
+ * code running next to another framework's caching allocator that already
+ * holds nearly all free device memory, or host code on a real-time path where
+ * an allocation (which can synchronise the device) is not allowed.
+ *   - All scratch (parameters, gradient, 64 partial rows, loss) lives in one
+ *     file-scope static __device__ array of 364 KB, which every GPU that
+ *     loads the library holds until the process exits.
+ *   - n <= 4096 samples per call; larger n returns LBM_EINVAL (split the
+ *     batch).  X_dev [n][8] and t_dev [n] must be device memory; params
+ *     (1394 floats) may be host or device; loss and grad (1394 floats) are
+ *     written to host or device memory.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; the call
+ *     clears what must start at zero.  Calls that overlap on the GPU (other
+ *     streams, other threads) race on the array: serialise them.
+ *   - Synchronises the stream.  No cudaMalloc, cudaFree or allocating
+ *     library routine is called. */
+LBM_API int lbm_mlp_grad_static(const float* X_dev, const float* t_dev, int n,
+                                const float* params, float* loss, float* grad,
+                                void* cuda_stream);
+
 /* Message of the last failed lbm_mlp_* call on this thread. */
 LBM_API const char* lbm_mlp_last_error(void);
 

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <string>
 #include <vector>
@@ -339,6 +340,93 @@ int lbm_mlp_train(const float* X_dev, const double* alpha_dev, int n, const doub
     }
     MCK(cudaMemcpyAsync(params, P.p, NPARAM * 4, cudaMemcpyDeviceToHost, s), "copy parameters");
     MCK(cudaStreamSynchronize(s), "synchronise");
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient without allocation.  Some callers cannot call cudaMalloc: for
+// example a training loop embedded in an application whose own caching
+// allocator already holds nearly all free device memory, or host code on a
+// real-time path where an allocation (which can synchronise the device) is
+// not allowed.  lbm_mlp_grad_static runs the same forward/backward and
+// reduction kernels as lbm_mlp_grad, with all its scratch in the file-scope
+// array below instead of cudaMalloc'd buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxSamples = 4096;                     // per call
+constexpr int kStaticBlocks = kStaticMaxSamples / BS;       // partial rows
+constexpr int kPad = 1408;                                  // NPARAM rounded up
+constexpr size_t kOffP = 0, kOffG = kPad, kOffPart = 2 * kPad,
+                 kOffPl = kOffPart + (size_t)kStaticBlocks * NTRAIN,
+                 kOffLa = kOffPl + kStaticBlocks, kStaticFloats = kOffLa + 8;
+
+// 364 KB on every GPU that loads the library, held until the process exits.
+static __device__ __align__(256) float g_mlp_scratch[kStaticFloats];
+
+// Device address of g_mlp_scratch, looked up once per device (the host-side
+// name g_mlp_scratch is only a stand-in and must never be passed to a kernel).
+float* static_scratch(int* err)
+{
+    static std::mutex mu;
+    static float* addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = 1;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_mlp_scratch);
+        if (e != cudaSuccess) {
+            *err = 2;
+            g_mlp_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        addr[dev] = static_cast<float*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" int lbm_mlp_grad_static(const float* X_dev, const float* t_dev, int n,
+                                   const float* params, float* loss, float* grad, void* stream)
+{
+    if (!X_dev || !t_dev || !params || !loss || !grad || n < 1)
+        return mfail(LBM_EINVAL, "bad arguments");
+    if (n > kStaticMaxSamples)
+        return mfail(LBM_EINVAL, "lbm_mlp_grad_static: n exceeds the 4096-sample maximum of "
+                                 "its static scratch (split the batch)");
+    if (!is_dev(X_dev) || !is_dev(t_dev)) return mfail(LBM_EINVAL, "X, t must be device memory");
+    int err = 0;
+    float* base = static_scratch(&err);
+    if (!base) {
+        if (err == 1) return mfail(LBM_ECUDA, "no current CUDA device");
+        return LBM_ECUDA;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* P = base + kOffP;
+    float* G = base + kOffG;
+    float* part = base + kOffPart;
+    float* pl = base + kOffPl;
+    float* la = base + kOffLa;
+    const int nblk = (n + BS - 1) / BS;
+    // the gradient's untrained entries and the loss accumulator must start at
+    // zero; every other slot is overwritten by this call
+    MCK(cudaMemcpyAsync(P, params, NPARAM * 4, cudaMemcpyDefault, s), "upload parameters");
+    MCK(cudaMemsetAsync(G, 0, NPARAM * 4, s), "clear gradient");
+    MCK(cudaMemsetAsync(la, 0, 8, s), "clear loss");
+    k_fwd_bwd<<<nblk, BS, 0, s>>>(X_dev, t_dev, nullptr, n, P, part, pl);
+    k_reduce<<<(NTRAIN + 255) / 256, 256, 0, s>>>(part, pl, nblk, n, G, la);
+    MCK(cudaGetLastError(), "gradient kernels");
+    float lh[2];
+    MCK(cudaMemcpyAsync(grad, G, NPARAM * 4, cudaMemcpyDefault, s), "copy gradient");
+    MCK(cudaMemcpyAsync(lh, la, 8, cudaMemcpyDeviceToHost, s), "copy loss");
+    MCK(cudaStreamSynchronize(s), "synchronise");
+    *loss = lh[0];
     return LBM_OK;
 }
 

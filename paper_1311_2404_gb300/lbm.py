@@ -101,6 +101,7 @@ _PROTOS = {
     "lbm_mlp_grad": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "lbm_mlp_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
     "lbm_mlp_last_error": (ctypes.c_char_p, []),
+    "lbm_mlp_grad_static": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_L, _name)
@@ -298,6 +299,16 @@ def lbm_mlp_grad(X_dev, t_dev, n, params, stream=None):
     grad = np.zeros(MLP_NPARAM, dtype=np.float32)
     _check(_L.lbm_mlp_grad(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss), _ptr(grad),
                            stream), mlp=True)
+    return float(loss[0]), grad
+
+
+def lbm_mlp_grad_static(X_dev, t_dev, n, params, stream=None):
+    """lbm_mlp_grad without allocation (static device scratch, n <= 4096)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(_L.lbm_mlp_grad_static(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss),
+                                  _ptr(grad), stream), mlp=True)
     return float(loss[0]), grad
 
 
