@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg256", choices=["tg256", "duct", "elbm"])
+    ap.add_argument("--workload", default="tg256", choices=["tg256", "duct", "elbm", "batch"])
+    ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
+                    help="ELBM alpha solve for --workload elbm")
+    ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
     ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--size", type=int, default=0,
@@ -211,6 +214,15 @@ def run_ours(args):
             sim.set_geometry(mask)
         if any(spec["force"]):
             sim.set_force(*spec["force"])
+        if spec["model"] == lbm.LBM_ELBM:
+            mode = {"newton": lbm.LBM_ALPHA_NEWTON, "series": lbm.LBM_ALPHA_SERIES_GUARDED,
+                    "mlp": lbm.LBM_ALPHA_MLP_GUARDED}[args.alpha]
+            lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-3)
+            if args.alpha == "mlp":
+                from paper_1311_2404_gb300 import alpha_training as at
+                Xp, yp, _, _ = at.collect_pairs(n=64)
+                P, _ = at.train(Xp, yp)
+                lbm.lbm_load_alpha_mlp(sim.h, P)
         rho_d = torch.from_numpy(rho).cuda()
         u_d = torch.from_numpy(u).cuda()
         lbm.lbm_init_equilibrium(sim.h, rho_d, u_d)      # inputs resident in HBM
@@ -287,6 +299,7 @@ def run_ours(args):
         "config": {"workload": spec["name"], "lattice": "D3Q19",
                    "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
                    "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
+                   **({"alpha": args.alpha} if spec["model"] == 2 else {}),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
                          % (B_PER_NODE[args.dtype] * nodes / 1e9)},
@@ -402,10 +415,97 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """512 uneven D2Q9 LBGK channels with a cylinder, one persistent
+    cooperative launch per bench call of K steps (CUDA graph), autotuned."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1311_2404_gb300 import lbm
+    from paper_1311_2404_gb300 import workloads as wl
+    dt = {"f32s": lbm.LBM_F32S, "f16s": lbm.LBM_F16S}.get(args.dtype, lbm.LBM_F32S)
+    specs = wl.batch_channel_specs(args.ndom)
+    stream = torch.cuda.Stream()
+    b = lbm.lbm_batch_create([s["nx"] for s in specs], [s["ny"] for s in specs],
+                             [s["tau"] for s in specs], dt)
+    lbm.lbm_batch_set_stream(b, stream.cuda_stream)
+    rho_bytes = 0
+    for d, sp in enumerate(specs):
+        lbm.lbm_batch_set_geometry(b, d, wl.batch_channel_mask(sp))
+        lbm.lbm_batch_set_force(b, d, sp["gx"], 0.0)
+        r = np.ones((1, sp["ny"], sp["nx"]), dtype=np.float32)
+        u = np.zeros((2, 1, sp["ny"], sp["nx"]), dtype=np.float32)
+        lbm.lbm_batch_init_equilibrium(b, d, r, u)
+        rho_bytes += r.nbytes
+    nodes = lbm.lbm_batch_nodes(b)
+    lbm.lbm_batch_autotune(b)
+    cfg = lbm.lbm_batch_get_config(b)
+    lbm.lbm_batch_step(b, max(args.warmup, 3))
+    lbm.lbm_batch_sync(b)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = lbm.lbm_batch_launch_count(b)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lbm.lbm_batch_step(b, args.steps)                    # one persistent launch
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = lbm.lbm_batch_launch_count(b) - l0
+    clocks = sampler.stop() if sampler else None
+    lbm.lbm_batch_sync(b)
+    lbm.lbm_batch_destroy(b)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    ms_max = float(t[0])
+    glups = nodes * args.steps * world / (ms_max * 1e-3) / 1e9
+    bpn = (72 if dt == lbm.LBM_F32S else 36) + 1
+    achieved = bpn * nodes / (ms / 1e3 / args.steps) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
+        "value": round(glups, 4), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max / args.steps, 6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded channel geometries; no dataset)",
+        "config": {"workload": f"d2q9_lbgk_batched_channels_{args.ndom}", "lattice": "D2Q9",
+                   "model": "LBGK", "storage": args.dtype if args.dtype in ("f32s", "f16s") else "f32s",
+                   "domains": args.ndom, "nodes": nodes, "launch": [int(x) for x in cfg],
+                   "parallelism": "single" if world == 1 else f"replicas{world}",
+                   "l2": "working set %.1f GB > 129 MB L2" % (bpn * nodes / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_kind, "bytes_per_node": bpn},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
