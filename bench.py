@@ -48,6 +48,8 @@ def parse():
                     help="ELBM alpha solve for --workload elbm")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
     ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
+    ap.add_argument("--model", default="", choices=["", "bgk", "mrt"],
+                    help="override the collision model of the tg256 / duct workloads")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--size", type=int, default=0,
                     help="override the cube edge of the 256^3 workloads (profiling runs)")
@@ -151,6 +153,9 @@ def workload_spec(name, dtype, size=0):
     if size and name in ("tg256", "elbm"):
         spec["n"] = (size, size, size)
         spec["name"] = spec["name"].replace("256^3", f"{size}^3")
+    if size and name == "duct":
+        spec["n"] = (2 * size, size, size)
+        spec["name"] = spec["name"].replace("512x256x256", f"{2 * size}x{size}x{size}")
     return spec
 
 
@@ -159,14 +164,15 @@ def _workload_spec(name, dtype):
     dmap = {"f32s": lbm.LBM_F32S, "f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S,
             "bf16s": lbm.LBM_BF16S}
     if name == "tg256":
-        return dict(name="d3q19_lbgk_taylor_green_256^3", n=(256, 256, 256), lattice=lbm.LBM_D3Q19,
+        return dict(kind="tg", name="d3q19_lbgk_taylor_green_256^3", n=(256, 256, 256),
+                    lattice=lbm.LBM_D3Q19,
                     model=lbm.LBM_BGK, tau=0.6, dtype=dmap[dtype], mask=None, force=(0, 0, 0))
     if name == "duct":
-        return dict(name="d3q19_mrt_sphere_duct_512x256x256", n=(512, 256, 256),
+        return dict(kind="duct", name="d3q19_mrt_sphere_duct_512x256x256", n=(512, 256, 256),
                     lattice=lbm.LBM_D3Q19, model=lbm.LBM_MRT, tau=0.55, dtype=dmap[dtype],
                     mask="duct", force=(1e-5, 0, 0))
     if name == "elbm":
-        return dict(name="d3q19_elbm_decaying_turbulence_256^3", n=(256, 256, 256),
+        return dict(kind="turb", name="d3q19_elbm_decaying_turbulence_256^3", n=(256, 256, 256),
                     lattice=lbm.LBM_D3Q19, model=lbm.LBM_ELBM, tau=0.5005, dtype=dmap[dtype],
                     mask=None, force=(0, 0, 0))
     raise ValueError(name)
@@ -175,10 +181,10 @@ def _workload_spec(name, dtype):
 def workload_inputs(spec):
     from paper_1311_2404_gb300 import workloads as wl
     nx, ny, nz = spec["n"]
-    if spec["name"].startswith("d3q19_lbgk_taylor"):
+    if spec["kind"] == "tg":
         rho, u = wl.taylor_green(nx, 0.05, nz=nz, D=3)
         mask = None
-    elif "duct" in spec["name"]:
+    elif spec["kind"] == "duct":
         mask, _ = wl.duct_with_spheres(nx, ny, nz)
         rho = np.ones((nz, ny, nx))
         u = np.zeros((3, nz, ny, nx))
@@ -203,6 +209,9 @@ def run_ours(args):
     from paper_1311_2404_gb300 import lbm
 
     spec = workload_spec(args.workload, args.dtype, args.size)
+    if args.model:
+        spec["model"] = {"bgk": lbm.LBM_BGK, "mrt": lbm.LBM_MRT}[args.model]
+        spec["name"] = spec["name"].replace("lbgk", args.model).replace("mrt", args.model)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
@@ -330,11 +339,11 @@ def _oracle_sample(spec, nz_s, ny_s=None):
     model = {0: oracle.BGK, 1: oracle.MRT, 2: oracle.ELBM}[spec["model"]]
     p = oracle.make_params(nx, ny_s, nz_s, D=3, model=model, tau=spec["tau"],
                            force=spec["force"])
-    if spec["name"].startswith("d3q19_lbgk_taylor"):
+    if spec["kind"] == "tg":
         rho, u = wl.taylor_green(nx, 0.05, nz=nz_s, D=3)
         rho, u = rho[:, :ny_s].copy(), u[:, :, :ny_s].copy()
         mask = None
-    elif "duct" in spec["name"]:
+    elif spec["kind"] == "duct":
         m, _ = wl.duct_with_spheres(nx, ny, nz)
         mask = np.ascontiguousarray(m[:nz_s, :ny_s])
         rho = np.ones((nz_s, ny_s, nx))

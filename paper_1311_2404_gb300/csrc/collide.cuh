@@ -39,43 +39,94 @@ __host__ __device__ constexpr R first_order_coef(int i)
     return i < 5 ? ba : (R(1) - R(2) * ba) / R(4);
 }
 
+// e_i . (a0, a1, a2) with the lattice's constant components folded at
+// compile time (IEEE arithmetic does not let the compiler drop 0 * a).
+template <class L, class R>
+__host__ __device__ __forceinline__ R edot(int i, R a0, R a1, R a2)
+{
+    const int x = L::ex(i), y = L::ey(i), z = L::ez(i);
+    R s;
+    if (x) {
+        s = x > 0 ? a0 : -a0;
+        if (y) s = y > 0 ? s + a1 : s - a1;
+        if (z) s = z > 0 ? s + a2 : s - a2;
+    } else if (y) {
+        s = y > 0 ? a1 : -a1;
+        if (z) s = z > 0 ? s + a2 : s - a2;
+    } else if (z) {
+        s = z > 0 ? a2 : -a2;
+    } else {
+        s = R(0);
+    }
+    return s;
+}
+
 // ---------------------------------------------------------------------------
-// LBGK
+// LBGK, Eq. lbgk relaxed toward Eq. equilibrium, Guo forcing Eq. guo_force.
+// Opposite pairs (2q+1, 2q+2) share the even part of the equilibrium,
+// w_i (drho + rho (9/2 (e.u)^2 - 3/2 u^2)), and the odd part b_i rho e.u
+// changes sign, so each pair is computed once.  Multiply-adds are explicit
+// (fma) so that the operation sequence does not depend on the compiler's
+// contraction choices in different kernels.
 // ---------------------------------------------------------------------------
 template <class L, class R>
-__host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R F1, R F2, bool has_force,
-                                            R& rho_out, R (&v)[3])
+__host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R F1, R F2,
+                                                     bool has_force, R& rho_out, R (&v)[3])
 {
-    R drho = 0, j[3] = {0, 0, 0};
+    constexpr int NP = (L::Q - 1) / 2;
+    R S[NP], A[NP];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        drho += d[i];
-        if (L::ex(i)) j[0] += L::ex(i) * d[i];
-        if (L::ey(i)) j[1] += L::ey(i) * d[i];
-        if (L::ez(i)) j[2] += L::ez(i) * d[i];
+    for (int q = 0; q < NP; ++q) {
+        S[q] = d[2 * q + 1] + d[2 * q + 2];
+        A[q] = d[2 * q + 1] - d[2 * q + 2];
+    }
+    R drho = d[0];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) drho += S[q];
+    R j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
+        if (L::ex(i)) j[0] = L::ex(i) > 0 ? j[0] + A[q] : j[0] - A[q];
+        if (L::ey(i)) j[1] = L::ey(i) > 0 ? j[1] + A[q] : j[1] - A[q];
+        if (L::ez(i)) j[2] = L::ez(i) > 0 ? j[2] + A[q] : j[2] - A[q];
     }
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
-    v[0] = (j[0] + R(0.5) * F0) * irho;
-    v[1] = (j[1] + R(0.5) * F1) * irho;
-    v[2] = (L::D == 3) ? (j[2] + R(0.5) * F2) * irho : R(0);
-    const R usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const R cf = R(1) - R(0.5) * om;
-    const R vF = v[0] * F0 + v[1] * F1 + v[2] * F2;
+    v[0] = fma(R(0.5), F0, j[0]) * irho;
+    v[1] = fma(R(0.5), F1, j[1]) * irho;
+    v[2] = (L::D == 3) ? fma(R(0.5), F2, j[2]) * irho : R(0);
+    const R usq = fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2]));
+    const R m15 = R(-1.5) * usq;
+    const R cf = fma(R(-0.5), om, R(1));
+    const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
+    {
+        const R w0 = (R)L::w(0);
+        const R feq = fma(w0 * rho, m15, w0 * drho);
+        R d0 = fma(om, feq - d[0], d[0]);
+        if (has_force) d0 = fma(cf, R(-3) * w0 * vF, d0);
+        d[0] = d0;
+    }
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
         const R wi = (R)L::w(i);
         const R bi = first_order_coef<L, R>(i);
-        const R eu = L::ex(i) * v[0] + L::ey(i) * v[1] + L::ez(i) * v[2];
-        // Eq. equilibrium minus w_i, written as w_i drho + 3 w_i rho e.u
-        // + w_i rho (9/2 (e.u)^2 - 3/2 u^2)
-        const R feq = wi * drho + bi * (rho * eu) + wi * (rho * (R(4.5) * eu * eu - R(1.5) * usq));
-        R di = d[i] + om * (feq - d[i]);
+        const R eu = edot<L, R>(i, v[0], v[1], v[2]);
+        const R t = fma(R(4.5) * eu, eu, m15);
+        const R even = fma(wi * rho, t, wi * drho);
+        const R odd = (bi * rho) * eu;
+        R dp = fma(om, (even + odd) - d[i], d[i]);
+        R dm = fma(om, (even - odd) - d[i + 1], d[i + 1]);
         if (has_force) {
-            const R eF = L::ex(i) * F0 + L::ey(i) * F1 + L::ez(i) * F2;
-            di += cf * (bi * eF - R(3) * wi * vF + R(9) * wi * eu * eF);
+            const R eF = edot<L, R>(i, F0, F1, F2);
+            const R ge = cf * wi * fma(R(9) * eu, eF, R(-3) * vF);   // even part of the Guo term
+            const R go = cf * bi * eF;                                // odd part
+            dp += ge + go;
+            dm += ge - go;
         }
-        d[i] = di;
+        d[i] = dp;
+        d[i + 1] = dm;
     }
     rho_out = rho;
 }
@@ -120,59 +171,106 @@ __host__ __device__ constexpr int mrt_norm2(int k)
     return s;
 }
 
+// Rows odd under e -> -e (momentum, energy flux and the third-order m moments);
+// all other rows are even.
+__host__ __device__ constexpr bool mrt_odd(int k)
+{
+    return (k >= 3 && k <= 8) || k >= 16;
+}
+
+// MRT collision.  Every basis row is even or odd under e -> -e, and the
+// velocity set comes in opposite pairs (2q+1, 2q+2), so both transforms split
+// over the 9 pairs: even moments use pair sums, odd moments pair differences,
+// and the inverse transform returns an even part (added to both members) and
+// an odd part (added to one, subtracted from the other).  Same arithmetic as
+// m = M n, f' = f - M^T diag(1/|M_k|^2) t, with about half the operations.
 template <class R>
 __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& rho_out,
-                                            R (&v)[3])
+                                                     R (&v)[3])
 {
     using L = D3Q19;
-    R drho = 0, j[3] = {0, 0, 0};
+    R S[9], A[9];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        drho += d[i];
-        if (L::ex(i)) j[0] += L::ex(i) * d[i];
-        if (L::ey(i)) j[1] += L::ey(i) * d[i];
-        if (L::ez(i)) j[2] += L::ez(i) * d[i];
+    for (int q = 0; q < 9; ++q) {
+        S[q] = d[2 * q + 1] + d[2 * q + 2];
+        A[q] = d[2 * q + 1] - d[2 * q + 2];
+    }
+    R drho = d[0], j[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int i = 2 * q + 1;
+        drho += S[q];
+        if (L::ex(i)) j[0] += L::ex(i) * A[q];
+        if (L::ey(i)) j[1] += L::ey(i) * A[q];
+        if (L::ez(i)) j[2] += L::ez(i) * A[q];
     }
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
-    const R F0 = (R)p.F[0], F1 = (R)p.F[1], F2 = (R)p.F[2];
+    const R F0 = sel<R>(p.F_f[0], p.F[0]), F1 = sel<R>(p.F_f[1], p.F[1]),
+            F2 = sel<R>(p.F_f[2], p.F[2]);
     v[0] = (j[0] + R(0.5) * F0) * irho;
     v[1] = (j[1] + R(0.5) * F1) * irho;
     v[2] = (j[2] + R(0.5) * F2) * irho;
     const R usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     const R vF = v[0] * F0 + v[1] * F1 + v[2] * F2;
-    // non-equilibrium part n_i = f_i - f_eq_i = d_i - (f_eq_i - w_i)
-    R nq[19], Ft[19];
+    const bool force = p.has_force != 0;
+    // non-equilibrium parts: rest, pair sums (even), pair differences (odd)
+    const R w0 = (R)L::w(0);
+    const R n0 = d[0] - (w0 * drho + w0 * (rho * (R(-1.5) * usq)));
+    const R g0 = force ? R(-3) * w0 * vF : R(0);
+    R NS[9], NA[9], GS[9], GA[9];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    for (int q = 0; q < 9; ++q) {
+        const int i = 2 * q + 1;
         const R wi = (R)L::w(i);
         const R bi = first_order_coef<L, R>(i);
-        const R eu = L::ex(i) * v[0] + L::ey(i) * v[1] + L::ez(i) * v[2];
-        nq[i] = d[i] - (wi * drho + bi * (rho * eu) +
-                        wi * (rho * (R(4.5) * eu * eu - R(1.5) * usq)));
-        const R eF = L::ex(i) * F0 + L::ey(i) * F1 + L::ez(i) * F2;
-        Ft[i] = bi * eF - R(3) * wi * vF + R(9) * wi * eu * eF;
+        const R eu = edot<L, R>(i, v[0], v[1], v[2]);
+        NS[q] = S[q] - R(2) * (wi * drho + wi * (rho * (R(4.5) * eu * eu - R(1.5) * usq)));
+        NA[q] = A[q] - R(2) * (bi * (rho * eu));
+        if (force) {
+            const R eF = edot<L, R>(i, F0, F1, F2);
+            GS[q] = R(2) * wi * (R(9) * eu * eF - R(3) * vF);   // Guo term, pair sum
+            GA[q] = R(2) * bi * eF;                               // Guo term, pair difference
+        } else {
+            GS[q] = GA[q] = R(0);
+        }
     }
     R t[19];
 #pragma unroll
     for (int k = 0; k < 19; ++k) {
         R m = 0, mf = 0;
+        if (!mrt_odd(k) && mrt_M(k, 0) != 0) {
+            m += R(mrt_M(k, 0)) * n0;
+            mf += R(mrt_M(k, 0)) * g0;
+        }
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
+        for (int q = 0; q < 9; ++q) {
+            const int i = 2 * q + 1;
             if (mrt_M(k, i) != 0) {
-                m += R(mrt_M(k, i)) * nq[i];
-                mf += R(mrt_M(k, i)) * Ft[i];
+                m += R(mrt_M(k, i)) * (mrt_odd(k) ? NA[q] : NS[q]);
+                mf += R(mrt_M(k, i)) * (mrt_odd(k) ? GA[q] : GS[q]);
             }
         }
-        t[k] = R(p.mrt_c[k]) * m - (p.has_force ? R(p.mrt_cf[k]) * mf : R(0));
+        t[k] = sel<R>(p.mrt_c_f[k], p.mrt_c[k]) * m -
+               (force ? sel<R>(p.mrt_cf_f[k], p.mrt_cf[k]) * mf : R(0));
     }
+    R e0 = 0;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        R s = 0;
+    for (int k = 0; k < 19; ++k)
+        if (!mrt_odd(k) && mrt_M(k, 0) != 0) e0 += R(mrt_M(k, 0)) * t[k];
+    d[0] -= e0;
 #pragma unroll
-        for (int k = 0; k < 19; ++k)
-            if (mrt_M(k, i) != 0) s += R(mrt_M(k, i)) * t[k];
-        d[i] -= s;
+    for (int q = 0; q < 9; ++q) {
+        const int i = 2 * q + 1;
+        R ev = 0, od = 0;
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            if (mrt_M(k, i) == 0) continue;
+            if (mrt_odd(k)) od += R(mrt_M(k, i)) * t[k];
+            else ev += R(mrt_M(k, i)) * t[k];
+        }
+        d[i] -= ev + od;
+        d[i + 1] -= ev - od;
     }
     rho_out = rho;
 }
@@ -243,58 +341,77 @@ __host__ __device__ __forceinline__ void elbm_feq(double rho, const double (&u)[
 //   g(a)  = a A + sum_i f_i (1 + a x_i) log1p(a x_i)
 //   g'(a) = A + sum_i f_i x_i log1p(a x_i),      A = sum_i Delta_i ln(f_i / w_i)
 // (the termwise form of the H difference; sum Delta_i = 0 removes the
-// constant of dH/df).
+// constant of dH/df).  This is the definition; LogEval evaluates it.
 template <class L>
-__host__ __device__ __forceinline__ void elbm_g(const double (&f)[L::Q], const double (&x)[L::Q],
-                                       double A, double a, double& g, double& gp)
-{
-    double s = 0, sp = 0;
+struct LogEval {
+    const double* f;
+    const double* x;
+    double A;
+    __host__ __device__ bool valid(double) const { return true; }
+    __host__ __device__ void operator()(double a, double& g, double& gp) const
+    {
+        double s = 0, sp = 0;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const double ax = a * x[i];
-        const double l1 = log1p(ax);
-        s += f[i] * (1.0 + ax) * l1;
-        sp += f[i] * x[i] * l1;
+        for (int i = 0; i < L::Q; ++i) {
+            const double ax = a * x[i];
+            const double l1 = log1p(ax);
+            s += f[i] * (1.0 + ax) * l1;
+            sp += f[i] * x[i] * l1;
+        }
+        g = a * A + s;
+        gp = A + sp;
     }
-    g = a * A + s;
-    gp = A + sp;
-}
+};
 
-// Eight lattice-symmetry invariants fed to the alpha surrogate (FP64 in,
-// FP32 out): t3..t6 = (a_k / rho) / eps^k with a_k = sum f x^k and
-// eps = sqrt(a2 / rho), eps, max x / eps, min x / eps, A / a2.
-template <class L>
-__host__ __device__ __forceinline__ void elbm_features(const double (&f)[L::Q], const double (&x)[L::Q],
-                                              double rho, double A, double (&feat)[8],
-                                              double (&ak)[7])
-{
-    double a2 = 0, a3 = 0, a4 = 0, a5 = 0, a6 = 0, xmax = -1e300, xmin = 1e300;
+// The same g as a power series in a.  With a_k = sum_i f_i x_i^k and
+// (1 + y) log1p(y) = y + sum_{k>=2} (-1)^k y^k / (k (k-1)) (|y| < 1):
+//   g(a)  = a (A + a_1) + sum_{k=2}^{K} c_k a^k,   c_k = (-1)^k a_k / (k (k-1)),
+//   g'(a) = (A + a_1) + sum_{k=2}^{K} k c_k a^(k-1).
+// After one pass of FP64 multiply-adds per node every Newton evaluation is a
+// K-term polynomial instead of q logarithms.  Used when max|x| <= 0.03 and
+// for a <= 0.1 / max|x|, where the terms beyond K = 14 are below 1e-17 of
+// a_2 (the scale of g'); an iterate outside that range falls back to LogEval.
+constexpr int kSeriesK = 14;
+constexpr double kSeriesMaxX = 0.03;
+struct SeriesEval {
+    double c[kSeriesK + 1];      // c_k, k = 2..K
+    double A1;                   // A + a_1
+    double amax;                 // largest a the truncation is accurate for
+    __host__ __device__ bool valid(double a) const { return a <= amax; }
+    __host__ __device__ void operator()(double a, double& g, double& gp) const
+    {
+        double p = c[kSeriesK], q = kSeriesK * c[kSeriesK];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const double xi = x[i];
-        const double p2 = f[i] * xi * xi;
-        a2 += p2;
-        a3 += p2 * xi;
-        a4 += p2 * xi * xi;
-        a5 += p2 * xi * xi * xi;
-        a6 += p2 * xi * xi * xi * xi;
-        xmax = fmax(xmax, xi);
-        xmin = fmin(xmin, xi);
+        for (int k = kSeriesK - 1; k >= 2; --k) {
+            p = fma(p, a, c[k]);
+            q = fma(q, a, k * c[k]);
+        }
+        // p = sum c_k a^(k-2), q = sum k c_k a^(k-2)
+        g = a * (A1 + a * p);
+        gp = A1 + a * q;
     }
-    const double eps = sqrt(a2 / rho);
+};
+
+// Eight lattice-symmetry invariants fed to the alpha surrogate, from the
+// moments a_k = sum f x^k (k = 2..6), the extremes of x and A:
+// t_k = (a_k / rho) / eps^k (k = 3..6), eps = sqrt(a_2 / rho),
+// max x / eps, min x / eps, A / a_2.
+__host__ __device__ __forceinline__ void elbm_features(const double (&ak)[7], double xmax,
+                                                       double xmin, double rho, double A,
+                                                       double (&feat)[8])
+{
+    const double eps = sqrt(ak[2] / rho);
     const double ie = 1.0 / eps;
     const double ie2 = ie * ie;
     const double ir = 1.0 / rho;
-    feat[0] = a3 * ir * ie2 * ie;
-    feat[1] = a4 * ir * ie2 * ie2;
-    feat[2] = a5 * ir * ie2 * ie2 * ie;
-    feat[3] = a6 * ir * ie2 * ie2 * ie2;
+    feat[0] = ak[3] * ir * ie2 * ie;
+    feat[1] = ak[4] * ir * ie2 * ie2;
+    feat[2] = ak[5] * ir * ie2 * ie2 * ie;
+    feat[3] = ak[6] * ir * ie2 * ie2 * ie2;
     feat[4] = eps;
     feat[5] = xmax * ie;
     feat[6] = xmin * ie;
-    feat[7] = A / a2;
-    ak[0] = ak[1] = 0;
-    ak[2] = a2; ak[3] = a3; ak[4] = a4; ak[5] = a5; ak[6] = a6;
+    feat[7] = A / ak[2];
 }
 
 // MLP 8 -> 32 -> 32 -> 1 (tanh), parameters in shared memory (FP32 holding
@@ -335,90 +452,79 @@ struct AlphaResult {
     int evals;
     int status;
 };
+constexpr int ALPHA_NEEDS_LOG = 100;   // internal: series range left, redo with logs
 
-// Non-trivial root of g in [1, alpha_max) (Eq. alpha_cond).  Near-equilibrium
-// nodes (max |x| < skip_eps) take alpha = 2.  Safeguarded Newton keeps a
-// bracket [lo, hi]: g < 0 below the root, >= 0 at or above it (g is convex
-// with g(0) = 0).  If the positivity limit hi is reached with g(hi) < 0 there
-// is no root below it and alpha = hi = alpha_max (1 - 1e-10).
-template <class L>
-__host__ __device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double (&x)[L::Q], double A,
-                                  double rho, const StepParams& p, const float* smlp,
-                                  double (&feat)[8], bool& have_feat)
+// Non-trivial root of g in [1, alpha_max) (Eq. alpha_cond) with evaluator ev.
+// Safeguarded Newton keeps a bracket [lo, hi]: g < 0 below the root, >= 0 at
+// or above it (g is convex with g(0) = 0).  If the positivity limit hi is
+// reached with g(hi) < 0 there is no root below it and alpha = hi =
+// alpha_max (1 - 1e-10).  Guarded modes start from a guess (series or MLP),
+// take guard_steps Newton steps and accept when the last correction is below
+// guard_tol * alpha; otherwise the full solve runs from alpha = 2.
+template <class Ev>
+__host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const StepParams& p,
+                                           double guess, int evals0)
 {
-    AlphaResult r{2.0, 0, ALPHA_SKIP};
-    have_feat = false;
-    if (p.alpha_mode == 3) return r;          // fixed alpha = 2
-    double maxabs = 0, amax = 1e300;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        maxabs = fmax(maxabs, fabs(x[i]));
-        if (x[i] < 0) amax = fmin(amax, -1.0 / x[i]);   // f + a f x > 0  <=>  a < -1/x
-    }
-    if (maxabs < p.skip_eps || !(amax < 1e300)) return r;
+    AlphaResult r{2.0, evals0, ALPHA_NOCONV};
     double lo = 1.0, hi = amax * (1.0 - 1e-10);
     bool hi_known = false;
-    int evals = 0;
-    const bool guarded = (p.alpha_mode == 1 || p.alpha_mode == 2);
-    if (guarded || p.pairs_X != nullptr) {
-        double ak[7];
-        elbm_features<L>(f, x, rho, A, feat, ak);
-        have_feat = true;
-        if (guarded) {
-        double a;
-        if (p.alpha_mode == 1)
-            a = 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) + 4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
-        else
-            a = 2.0 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat) * feat[4];
-        a = fmin(fmax(a, lo), hi);
+    int evals = evals0;
+    if (p.alpha_mode == 1 || p.alpha_mode == 2) {
+        double a = fmin(fmax(guess, lo), hi);
         double corr = 1e300;
         for (int k = 0; k < p.guard_steps; ++k) {
+            if (!ev.valid(a)) return AlphaResult{a, evals, ALPHA_NEEDS_LOG};
             double g, gp;
-            elbm_g<L>(f, x, A, a, g, gp);
+            ev(a, g, gp);
             ++evals;
             double an = (gp > 0) ? a - g / gp : lo;
             an = fmin(fmax(an, lo), hi);
             corr = fabs(an - a);
             a = an;
         }
-        if (corr <= p.guard_tol * a) {
-            r.alpha = a;
-            r.evals = evals;
-            r.status = ALPHA_GUARDED;
-            return r;
-        }
-        }
+        if (corr <= p.guard_tol * a) return AlphaResult{a, evals, ALPHA_GUARDED};
     }
     double a = 2.0;
     if (!(a < hi)) a = 0.5 * (lo + hi);
-    int status = ALPHA_NOCONV;
     for (int it = 0; it < p.max_iter; ++it) {
+        if (!ev.valid(a)) return AlphaResult{a, evals, ALPHA_NEEDS_LOG};
         double g, gp;
-        elbm_g<L>(f, x, A, a, g, gp);
+        ev(a, g, gp);
         ++evals;
-        if (g == 0.0) { status = ALPHA_CONV; break; }
+        if (g == 0.0) { r.status = ALPHA_CONV; break; }
         if (g < 0) lo = a;
         else { hi = a; hi_known = true; }
         double an = (gp > 0) ? a - g / gp : -1.0;
         // a step below the tolerance is the answer, even when rounding has
         // collapsed the bracket onto the root
-        if (gp > 0 && fabs(an - a) <= p.tol * a) { a = an; status = ALPHA_CONV; break; }
+        if (gp > 0 && fabs(an - a) <= p.tol * a) { a = an; r.status = ALPHA_CONV; break; }
         if (!(an > lo && an < hi)) {
             if (!hi_known && !(an < hi)) {
+                if (!ev.valid(hi)) return AlphaResult{a, evals, ALPHA_NEEDS_LOG};
                 double gh, gph;
-                elbm_g<L>(f, x, A, hi, gh, gph);
+                ev(hi, gh, gph);
                 ++evals;
-                if (gh < 0) { a = hi; status = ALPHA_CLAMP; break; }
+                if (gh < 0) { a = hi; r.status = ALPHA_CLAMP; break; }
                 hi_known = true;
             }
             an = 0.5 * (lo + hi);
         }
-        if (fabs(an - a) <= p.tol * a) { a = an; status = ALPHA_CONV; break; }
+        if (fabs(an - a) <= p.tol * a) { a = an; r.status = ALPHA_CONV; break; }
         a = an;
     }
     r.alpha = a;
     r.evals = evals;
-    r.status = status;
+    return r;
+}
+
+// Reciprocal in FP64 from an FP32 seed refined by two Newton-Raphson steps
+// r <- r (2 - f r) (each step squares the relative error: 2^-24 -> 2^-48 ->
+// below FP64 rounding).  f > 0, as the distributions of a valid state are.
+__host__ __device__ __forceinline__ double recip_nr(double f)
+{
+    double r = (double)(1.0f / (float)f);
+    r = r * fma(-f, r, 2.0);
+    r = r * fma(-f, r, 2.0);
     return r;
 }
 
@@ -426,10 +532,11 @@ __host__ __device__ AlphaResult elbm_solve(const double (&f)[L::Q], const double
 // Returns the per-node outcome for the counters.
 template <class L, class R>
 __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const StepParams& p,
-                                                    const float* smlp, R& rho_out, R (&vout)[3],
-                                                    double (&feat)[8], bool& have_feat)
+                                                             const float* smlp, R& rho_out,
+                                                             R (&vout)[3], double (&feat)[8],
+                                                             bool& have_feat)
 {
-    double f[L::Q], x[L::Q];
+    double f[L::Q], x[L::Q], fe[L::Q], y[L::Q];
     double drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -443,19 +550,155 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     const double rho = 1.0 + drho;
     const double irho = 1.0 / rho;
     double u[3] = {j[0] * irho, j[1] * irho, (L::D == 3) ? j[2] * irho : 0.0};
-    double fe[L::Q];
-    elbm_feq<L>(rho, u, p.feq_variant, fe);
-    double A = 0;
+    // equilibrium; for the entropic form also its pieces: f_eq_i = P_i (1 + y_i)
+    // with P_i = c0 w_i prod_a r_a^e_ia (ln(P_i / w_i) affine in e_i) and y_i the
+    // relative mass/momentum restoration
+    double lc0 = 0, lr[3] = {0, 0, 0};
+    const bool entropic = (p.feq_variant == 0);
+    if (entropic) {
+        double c[3], r[3], ri[3];
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            const double s = sqrt(1.0 + 3.0 * u[a] * u[a]);
+            c[a] = 2.0 - s;
+            r[a] = (2.0 * u[a] + s) / (1.0 - u[a]);
+            ri[a] = 1.0 / r[a];
+        }
+        const double c0 = (L::D == 3) ? rho * c[0] * c[1] * c[2] : rho * c[0] * c[1];
+        const double ic0 = 1.0 / c0;
+        double m0 = 0, m1[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            double q = c0 * L::w(i), iq = ic0;        // P_i and (w_i / P_i)
+            if (L::ex(i) == 1) { q *= r[0]; iq *= ri[0]; }
+            if (L::ex(i) == -1) { q *= ri[0]; iq *= r[0]; }
+            if (L::ey(i) == 1) { q *= r[1]; iq *= ri[1]; }
+            if (L::ey(i) == -1) { q *= ri[1]; iq *= r[1]; }
+            if (L::D == 3) {
+                if (L::ez(i) == 1) { q *= r[2]; iq *= ri[2]; }
+                if (L::ez(i) == -1) { q *= ri[2]; iq *= r[2]; }
+            }
+            fe[i] = q;
+            y[i] = iq;
+            m0 += q;
+            m1[0] += L::ex(i) * q;
+            m1[1] += L::ey(i) * q;
+            m1[2] += L::ez(i) * q;
+        }
+        // put the residual mass and momentum back (zero up to rounding on
+        // D2Q9, O(u^3) on D3Q19): the root of g shifts with f_eq's mass defect
+        const double dr = rho - m0;
+        const double dj0 = rho * u[0] - m1[0], dj1 = rho * u[1] - m1[1],
+                     dj2 = rho * u[2] - m1[2];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double corr = dr + 3.0 * (L::ex(i) * dj0 + L::ey(i) * dj1 + L::ez(i) * dj2);
+            fe[i] += L::w(i) * corr;
+            y[i] *= corr;                               // w_i corr / P_i
+        }
+        lc0 = log(c0);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) lr[a] = log(r[a]);
+    } else {
+        elbm_feq<L>(rho, u, 1, fe);
+    }
+    double maxabs = 0, xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const double Dl = fe[i] - f[i];
-        x[i] = Dl / f[i];
-        A += Dl * log(f[i] / L::w(i));
+        x[i] = (fe[i] - f[i]) * recip_nr(f[i]);
+        maxabs = fmax(maxabs, fabs(x[i]));
+        xmin = fmin(xmin, x[i]);
+        xmax = fmax(xmax, x[i]);
     }
-    AlphaResult ar = elbm_solve<L>(f, x, A, rho, p, smlp, feat, have_feat);
-    const double ab = ar.alpha * 0.5 * p.omega;     // alpha * beta, beta = 1/(2 tau)
+    AlphaResult ar{2.0, 0, ALPHA_SKIP};
+    have_feat = false;
+    const double amax = xmin < 0 ? -1.0 / xmin : 1e300;   // f + a f x > 0  <=>  a < -1/x
+    if (p.alpha_mode != 3 && maxabs >= p.skip_eps && amax < 1e300) {
+        const bool want_feat = (p.alpha_mode == 1 || p.alpha_mode == 2 || p.pairs_X != nullptr);
+        double ak[7];
+        double A = 0;
+        bool solved = false;
+        if (entropic && maxabs <= kSeriesMaxX) {
+            // moments a_k and A from the series (no per-direction logarithm)
+            double a[kSeriesK + 1];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) d[i] = (R)((f[i] - L::w(i)) + ab * (f[i] * x[i]));
+            for (int k = 0; k <= kSeriesK; ++k) a[k] = 0;
+            double s0 = 0, s1[3] = {0, 0, 0}, sy = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const double Dl = f[i] * x[i];
+                double pw = Dl;
+                a[1] += pw;
+#pragma unroll
+                for (int k = 2; k <= kSeriesK; ++k) {
+                    pw *= x[i];
+                    a[k] += pw;
+                }
+                s0 += Dl;
+                s1[0] += L::ex(i) * Dl;
+                s1[1] += L::ey(i) * Dl;
+                s1[2] += L::ez(i) * Dl;
+                const double yi = y[i];
+                sy += Dl * (yi * (1.0 - yi * (0.5 - yi * (1.0 / 3.0 - 0.25 * yi))));
+            }
+            // A = sum Delta ln(f_eq/w) - sum Delta log1p(x), with
+            // sum Delta ln(f_eq/w) = ln c0 s0 + sum_a ln r_a s1_a + sum Delta log1p(y)
+            // and sum Delta log1p(x) = sum_{n>=1} (-1)^(n+1) a_(n+1) / n
+            double sl = 0;
+#pragma unroll
+            for (int n = kSeriesK - 1; n >= 1; --n) sl += ((n & 1) ? 1.0 : -1.0) * a[n + 1] / n;
+            A = lc0 * s0 + lr[0] * s1[0] + lr[1] * s1[1] + lr[2] * s1[2] + sy - sl;
+            SeriesEval ev;
+#pragma unroll
+            for (int k = 2; k <= kSeriesK; ++k)
+                ev.c[k] = ((k & 1) ? -1.0 : 1.0) * a[k] / (double)(k * (k - 1));
+            ev.c[0] = ev.c[1] = 0;
+            ev.A1 = A + a[1];
+            ev.amax = 0.1 / maxabs;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) ak[k] = a[k];
+            double guess = 2.0;
+            if (want_feat) {
+                elbm_features(ak, xmax, xmin, rho, A, feat);
+                have_feat = true;
+                guess = (p.alpha_mode == 2)
+                            ? 2.0 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat) * feat[4]
+                            : 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
+                                  4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+            }
+            ar = elbm_solve(ev, amax, p, guess, 0);
+            solved = (ar.status != ALPHA_NEEDS_LOG);
+        }
+        if (!solved) {
+            // the definition: logarithms per direction
+            A = 0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) ak[k] = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const double Dl = f[i] * x[i];
+                A += Dl * log(f[i] / L::w(i));
+                const double p2 = Dl * x[i];
+                ak[2] += p2;
+                ak[3] += p2 * x[i];
+                ak[4] += p2 * x[i] * x[i];
+                ak[5] += p2 * x[i] * x[i] * x[i];
+                ak[6] += p2 * x[i] * x[i] * x[i] * x[i];
+            }
+            double guess = 2.0;
+            if (want_feat) {
+                elbm_features(ak, xmax, xmin, rho, A, feat);
+                have_feat = true;
+                guess = (p.alpha_mode == 2)
+                            ? 2.0 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat) * feat[4]
+                            : 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
+                                  4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+            }
+            LogEval<L> ev{f, x, A};
+            ar = elbm_solve(ev, amax, p, guess, ar.evals);
+        }
+    }
+    const double ab = ar.alpha * 0.5 * p.omega;     // alpha * beta, beta = 1/(2 tau)
     if (p.has_force) {
         // EDM, Eq. edm_force: f_eq(rho, u + F/rho) - f_eq(rho, u)
         double us[3] = {u[0] + p.F[0] * irho, u[1] + p.F[1] * irho,
@@ -465,6 +708,9 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
             d[i] = (R)((f[i] - L::w(i)) + ab * (f[i] * x[i]) + (fs[i] - fe[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) d[i] = (R)((f[i] - L::w(i)) + ab * (f[i] * x[i]));
     }
     rho_out = (R)rho;
     vout[0] = (R)(u[0] + 0.5 * p.F[0] * irho);

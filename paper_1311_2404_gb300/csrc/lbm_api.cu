@@ -431,7 +431,11 @@ static StepParams make_params(lbm_ctx* h)
         const double n2 = h->lattice == LBM_D3Q19 ? (double)mrt_norm2(k) : 1.0;
         p.mrt_c[k] = h->s[k] / n2;
         p.mrt_cf[k] = (1.0 - 0.5 * h->s[k]) / n2;
+        p.mrt_c_f[k] = (float)p.mrt_c[k];
+        p.mrt_cf_f[k] = (float)p.mrt_cf[k];
     }
+    p.omega_f = (float)p.omega;
+    for (int a = 0; a < 3; ++a) p.F_f[a] = (float)p.F[a];
     p.alpha_mode = h->alpha_mode; p.max_iter = h->max_iter;
     p.guard_steps = h->guard_steps; p.feq_variant = h->feq_variant;
     p.tol = h->tol; p.skip_eps = h->skip_eps; p.guard_tol = h->guard_tol;

@@ -132,10 +132,24 @@ struct StepParams {
     double F[3];               // body force
     double mrt_c[19];          // s_k / |M_k|^2
     double mrt_cf[19];         // (1 - s_k/2) / |M_k|^2
+    // the same, rounded once on the host for the FP32 kernels (a per-node
+    // double -> float conversion runs on the GPU's FP64 pipe)
+    float omega_f;
+    float F_f[3];
+    float mrt_c_f[19];
+    float mrt_cf_f[19];
     // ELBM
     int alpha_mode, max_iter, guard_steps, feq_variant;
     double tol, skip_eps, guard_tol;
     const float* mlp;          // MLP_NPARAM floats (BF16-rounded weights)
 };
+
+// Parameter in the compute type: the FP32 copy for float, FP64 for double.
+template <class R>
+__host__ __device__ __forceinline__ R sel(float f, double d);
+template <>
+__host__ __device__ __forceinline__ float sel<float>(float f, double) { return f; }
+template <>
+__host__ __device__ __forceinline__ double sel<double>(float, double d) { return d; }
 
 }  // namespace lbm

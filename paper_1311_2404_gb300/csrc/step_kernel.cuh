@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
         bool have_feat = false;
         AlphaResult ar{2.0, 0, -1};
         if (MODEL == MODEL_BGK) {
-            bgk_collide<L, R>(d, (R)p.omega, (R)p.F[0], (R)p.F[1], (R)p.F[2], p.has_force != 0,
-                              rho, v);
+            bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
+                              sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
+                              p.has_force != 0, rho, v);
         } else if (MODEL == MODEL_MRT) {
             if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
         } else {
