@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
                     help="ELBM alpha solve for --workload elbm")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
+    ap.add_argument("--round", default="dither", choices=["dither", "nearest"],
+                    help="rounding of FP16/BF16 stores")
     ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
     ap.add_argument("--model", default="", choices=["", "bgk", "mrt"],
                     help="override the collision model of the tg256 / duct workloads")
@@ -223,6 +225,8 @@ def run_ours(args):
             sim.set_geometry(mask)
         if any(spec["force"]):
             sim.set_force(*spec["force"])
+        lbm.lbm_set_rounding(sim.h, lbm.LBM_ROUND_NEAREST if args.round == "nearest"
+                             else lbm.LBM_ROUND_DITHER)
         if spec["model"] == lbm.LBM_ELBM:
             mode = {"newton": lbm.LBM_ALPHA_NEWTON, "series": lbm.LBM_ALPHA_SERIES_GUARDED,
                     "mlp": lbm.LBM_ALPHA_MLP_GUARDED}[args.alpha]
@@ -309,6 +313,7 @@ def run_ours(args):
                    "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
                    "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
                    **({"alpha": args.alpha} if spec["model"] == 2 else {}),
+                   **({"rounding": args.round} if args.dtype in ("f16s", "bf16s") else {}),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
                          % (B_PER_NODE[args.dtype] * nodes / 1e9)},
@@ -443,6 +448,8 @@ def run_batch(args):
     b = lbm.lbm_batch_create([s["nx"] for s in specs], [s["ny"] for s in specs],
                              [s["tau"] for s in specs], dt)
     lbm.lbm_batch_set_stream(b, stream.cuda_stream)
+    lbm.lbm_batch_set_rounding(b, lbm.LBM_ROUND_NEAREST if args.round == "nearest"
+                               else lbm.LBM_ROUND_DITHER)
     rho_bytes = 0
     for d, sp in enumerate(specs):
         lbm.lbm_batch_set_geometry(b, d, wl.batch_channel_mask(sp))

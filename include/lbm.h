@@ -65,6 +65,13 @@ enum { LBM_BGK = 0, LBM_MRT = 1, LBM_ELBM = 2 }; /* Eqs. lbgk, mrt_collision, el
  * round-off-minimising form of Sec. 3.7); arithmetic is FP64 for LBM_F64 and
  * FP32 for all others. */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32S = 2, LBM_F16S = 3, LBM_BF16S = 4 };
+/* Rounding of FP16/BF16 stores.  DITHER (default): add to the dropped bits an
+ * offset from a hash of the value's bits, node and direction, then truncate;
+ * the rounding error is unbiased like stochastic rounding, without a random
+ * number generator (round-to-nearest of a value that barely changes from
+ * step to step repeats the same error and drifts).  NEAREST: round to
+ * nearest even. */
+enum { LBM_ROUND_DITHER = 0, LBM_ROUND_NEAREST = 1 };
 /* Element type of macroscopic-field arrays crossing the ABI. */
 enum { LBM_FIELD_F64 = 0, LBM_FIELD_F32 = 1 };
 /* ELBM alpha modes (Eq. alpha_cond).  NEWTON: safeguarded FP64 Newton from
@@ -163,6 +170,10 @@ LBM_API int lbm_load_alpha_mlp(lbm_handle h, const float* params, int n);
  * (ELBM only); read with lbm_get_alpha.  Costs 8 B/node on output steps. */
 LBM_API int lbm_set_alpha_output(lbm_handle h, int on);
 
+/* Rounding mode of FP16S / BF16S stores (LBM_ROUND_*); no effect on other
+ * storage types. */
+LBM_API int lbm_set_rounding(lbm_handle h, int mode);
+
 /* Capture the n launches of lbm_step(h, n) in a CUDA graph and replay it on
  * later calls with the same n (useful for small, launch-bound domains). */
 LBM_API int lbm_set_graph(lbm_handle h, int on);
@@ -242,16 +253,19 @@ LBM_API int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy);
  * must be initialised before the first lbm_batch_step; afterwards LBM_ESTATE. */
 LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
                                int field_dtype);
-/* Choose block size, tile shape and CTAs per SM by timing a few steps of
- * each candidate (CUDA events); restores the state afterwards. */
+/* Choose block size, tile shape, rows per thread and CTAs per SM by timing a
+ * few steps of each candidate (CUDA events); restores the state afterwards. */
 LBM_API int lbm_batch_autotune(lbm_batch b);
-/* Current launch configuration: threads per CTA, CTAs, tile width, tile rows. */
-LBM_API int lbm_batch_get_config(lbm_batch b, int* out4);
+/* Current launch configuration (5 ints): threads per CTA, CTAs, tile width,
+ * tile rows, rows per thread and pass (1 or 2). */
+LBM_API int lbm_batch_get_config(lbm_batch b, int* out5);
 /* Advance every domain n steps in one persistent launch.  The per-step
  * grid barrier spins a bounded number of times; if it gives up, the kernel
  * exits and the next synchronising call returns LBM_ETIMEOUT. */
 LBM_API int lbm_batch_step(lbm_batch b, int n);
 LBM_API int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype);
+/* Rounding mode of FP16S stores (LBM_ROUND_*; default LBM_ROUND_DITHER). */
+LBM_API int lbm_batch_set_rounding(lbm_batch b, int mode);
 /* Spin limit of the per-step grid barrier (default 2e7 spins of ~0.1 us,
  * about two seconds).  A wait that exceeds it ends the launch early and the
  * next synchronising call returns LBM_ETIMEOUT. */

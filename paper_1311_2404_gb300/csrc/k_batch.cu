@@ -50,6 +50,7 @@ struct BatchParams {
     unsigned* status;
     long long wait_limit;               // spins before giving up
     int withhold;                       // test hook: CTA 0 skips its first arrival
+    int round_nearest;                  // FP16 storage: 1 round to nearest, 0 dither
 };
 
 // Bounded grid barrier (generation counter).  Returns false when this CTA
@@ -89,11 +90,65 @@ __device__ bool grid_barrier(const BatchParams& bp, bool skip_arrive)
     return ok != 0;
 }
 
+// Loads of one node's incoming populations (pull, periodic, half-way
+// bounce-back at solid upstream nodes).  Returns false for a solid node.
 template <class S>
+__device__ __forceinline__ bool batch_load(const DomDev& D, const typename S::T* __restrict__ A,
+                                           const uint8_t* __restrict__ flags, int x, int y,
+                                           float (&d)[9], unsigned& fl)
+{
+    using L = D2Q9;
+    const int n = y * D.nxp + x;
+    fl = flags[n];
+    if (fl & FLAG_SOLID) return false;
+    const int cx[3] = {x == 0 ? D.nx - 1 : x - 1, x, x == D.nx - 1 ? 0 : x + 1};
+    const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
+                       (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        d[i] = S::load(A + (size_t)i * D.sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)], L::w(i));
+    if (fl & FLAG_NEAR_WALL) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+            if (flags[src] & FLAG_SOLID)
+                d[i] = S::load(A + (size_t)L::opp(i) * D.sq + n, L::w(L::opp(i)));
+        }
+    }
+    return true;
+}
+
+// Collision and store of one node (the single-domain kernel's arithmetic).
+template <class S>
+__device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams& bp,
+                                             typename S::T* __restrict__ B,
+                                             float* __restrict__ o, int n, bool out,
+                                             float (&d)[9])
+{
+    using L = D2Q9;
+    float rho, v[3];
+    bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
+    if (S::kHalf && !bp.round_nearest) {
+        const unsigned salt = (unsigned)n * kSaltNode;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            B[(size_t)i * D.sq + n] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
+    }
+    if (out) {
+        o[n] = rho;
+        o[D.sq + n] = v[0];
+        o[2 * D.sq + n] = v[1];
+        if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(bp.status, STATUS_NAN);
+    }
+}
+
+template <class S, int NPT>
 __global__ void k_batch(const BatchParams bp)
 {
     using T = typename S::T;
-    using L = D2Q9;
     const int G = gridDim.x;
     const long long t0 = (long long)bp.ntiles * blockIdx.x / G;
     const long long t1 = (long long)bp.ntiles * (blockIdx.x + 1) / G;
@@ -110,41 +165,28 @@ __global__ void k_batch(const BatchParams bp)
             float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
             const int x = tile.y + threadIdx.x;
             if (x >= D.nx) continue;
-            for (int r = threadIdx.y; r < bp.th; r += blockDim.y) {
-                const int y = tile.z + r;
-                if (y >= D.ny) break;
-                const int n = y * D.nxp + x;
-                const unsigned fl = flags[n];
-                if (fl & FLAG_SOLID) {
-                    if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
-                    continue;
+            // NPT rows per pass (1 or 2): with 2, both nodes' loads are in
+            // flight together at the cost of twice the registers
+            for (int r = threadIdx.y; r < bp.th; r += NPT * blockDim.y) {
+                const int ya = tile.z + r;
+                const int rb = r + blockDim.y;
+                const int yb = tile.z + rb;
+                const bool va = ya < D.ny;
+                const bool vb = NPT == 2 && rb < bp.th && yb < D.ny;
+                float da[9], db[9];
+                unsigned fa = 0, fb = 0;
+                bool la = false, lb = false;
+                if (va) la = batch_load<S>(D, A, flags, x, ya, da, fa);
+                if (vb) lb = batch_load<S>(D, A, flags, x, yb, db, fb);
+                if (va) {
+                    const int n = ya * D.nxp + x;
+                    if (la) batch_update<S>(D, bp, B, o, n, out, da);
+                    else if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
                 }
-                const int cx[3] = {x == 0 ? D.nx - 1 : x - 1, x, x == D.nx - 1 ? 0 : x + 1};
-                const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
-                                   (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
-                float d[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    d[i] = S::load(A + (size_t)i * D.sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)],
-                                   L::w(i));
-                if (fl & FLAG_NEAR_WALL) {
-#pragma unroll
-                    for (int i = 1; i < 9; ++i) {
-                        const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-                        if (flags[src] & FLAG_SOLID)
-                            d[i] = S::load(A + (size_t)L::opp(i) * D.sq + n, L::w(L::opp(i)));
-                    }
-                }
-                float rho, v[3];
-                bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
-                if (out) {
-                    o[n] = rho;
-                    o[D.sq + n] = v[0];
-                    o[2 * D.sq + n] = v[1];
-                    if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1]))
-                        atomicOr(bp.status, STATUS_NAN);
+                if (vb) {
+                    const int n = yb * D.nxp + x;
+                    if (lb) batch_update<S>(D, bp, B, o, n, out, db);
+                    else if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
                 }
             }
         }
@@ -156,8 +198,8 @@ __global__ void k_batch(const BatchParams bp)
     }
 }
 
-template <class S>
-const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch<S>); }
+template <class S, int NPT>
+const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch<S, NPT>); }
 
 }  // namespace
 
@@ -171,11 +213,12 @@ struct lbm_batch_ctx {
     std::vector<int4> tiles;
     int ntiles = 0;
     cudaStream_t stream = nullptr;
-    int threads = 256, ctas = 0, tw = 128, th = 8;   // launch configuration
+    int threads = 256, ctas = 0, tw = 128, th = 8, npt = 1;   // launch configuration
     int sms = 0, tiles_tw = 0, tiles_th = 0;          // tiles currently uploaded for (tw, th)
     int cur = 0;
     long long t = 0, launches = 0, wait_limit = 20000000LL;
     int withhold = 0;
+    int round_nearest = 0;
     bool use_graph = true;
     std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -220,9 +263,11 @@ static void drop_graphs(lbm_batch b)
     b->graphs.clear();
 }
 
-static const void* kernel_for(int dtype)
+static const void* kernel_for(int dtype, int npt)
 {
-    return dtype == LBM_F16S ? batch_kernel_ptr<StoreF16S>() : batch_kernel_ptr<StoreF32S>();
+    if (dtype == LBM_F16S)
+        return npt == 2 ? batch_kernel_ptr<StoreF16S, 2>() : batch_kernel_ptr<StoreF16S, 1>();
+    return npt == 2 ? batch_kernel_ptr<StoreF32S, 2>() : batch_kernel_ptr<StoreF32S, 1>();
 }
 
 // Build and upload the tile list for tile shape (tw, th).
@@ -246,10 +291,10 @@ static int upload_tiles(lbm_batch b, int tw, int th)
     return LBM_OK;
 }
 
-static int max_ctas(lbm_batch b, int threads)
+static int max_ctas(lbm_batch b, int threads, int npt)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(b->dtype), threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(b->dtype, npt), threads, 0);
     return per_sm * b->sms;
 }
 
@@ -267,6 +312,7 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     bp.status = reinterpret_cast<unsigned*>(b->base + b->off_bar + 8);
     bp.wait_limit = b->wait_limit;
     bp.withhold = b->withhold;
+    bp.round_nearest = b->round_nearest;
     cudaError_t e = cudaMemsetAsync(bp.bar, 0, 8, b->stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -281,7 +327,7 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void* args[] = {&bp};
-    return cudaLaunchKernelExC(&cfg, kernel_for(b->dtype), args);
+    return cudaLaunchKernelExC(&cfg, kernel_for(b->dtype, b->npt), args);
 }
 
 extern "C" {
@@ -362,7 +408,7 @@ int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, 
         delete b;
         return bfail(nullptr, r, "%s", m.c_str());
     }
-    b->ctas = std::min(max_ctas(b, b->threads), std::max(1, b->ntiles));
+    b->ctas = std::min(max_ctas(b, b->threads, b->npt), std::max(1, b->ntiles));
     if (b->ctas < 1) {
         cudaFree(p);
         delete b;
@@ -469,7 +515,7 @@ static int check_ready(lbm_batch b)
 
 static int step_impl(lbm_batch b, int n)
 {
-    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th);
+    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th * 4 + b->npt);
     if (b->use_graph && b->stream != nullptr && !b->withhold) {
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
@@ -533,37 +579,43 @@ int lbm_batch_autotune(lbm_batch b)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th;
+    int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th, bn = b->npt;
     const int steps = 4;
-    for (int threads : {128, 256, 512})
-        for (int tw : {64, 128, 256}) {
-            if (tw > threads) continue;
-            const int mc = max_ctas(b, threads);
-            if (mc < 1) continue;
-            for (int th : {2, 4, 8, 16}) {
-                if (th < threads / tw) continue;
-                if (upload_tiles(b, tw, th)) continue;
-                const int per_sm = std::max(1, mc / b->sms);
-                for (int k = 1; k <= per_sm; k *= 2) {
-                    b->threads = threads; b->tw = tw; b->th = th;
-                    b->ctas = std::min(k * b->sms, b->ntiles);
-                    if (launch_batch(b, 1, b->cur) != cudaSuccess) { cudaGetLastError(); continue; }
-                    cudaEventRecord(e0, b->stream);
-                    cudaError_t le = launch_batch(b, steps, b->cur);
-                    cudaEventRecord(e1, b->stream);
-                    if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-                        cudaGetLastError();
-                        continue;
+    for (int npt : {1, 2})
+        for (int threads : {128, 256, 512})
+            for (int tw : {64, 128, 256}) {
+                if (tw > threads) continue;
+                const int mc = max_ctas(b, threads, npt);
+                if (mc < 1) continue;
+                for (int th : {2, 4, 8, 16}) {
+                    if (th < npt * (threads / tw)) continue;
+                    if (upload_tiles(b, tw, th)) continue;
+                    const int per_sm = std::max(1, mc / b->sms);
+                    for (int k = 1; k <= per_sm; k *= 2) {
+                        b->threads = threads; b->tw = tw; b->th = th; b->npt = npt;
+                        b->ctas = std::min(k * b->sms, b->ntiles);
+                        if (launch_batch(b, 1, b->cur) != cudaSuccess) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        cudaEventRecord(e0, b->stream);
+                        cudaError_t le = launch_batch(b, steps, b->cur);
+                        cudaEventRecord(e1, b->stream);
+                        if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (ms < best) {
+                            best = ms; bt = threads; bc = b->ctas; bw = tw; bh = th; bn = npt;
+                        }
                     }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best) { best = ms; bt = threads; bc = b->ctas; bw = tw; bh = th; }
                 }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->threads = bt; b->ctas = bc;
+    b->threads = bt; b->ctas = bc; b->npt = bn;
     int ur = upload_tiles(b, bw, bh);
     b->tw = bw; b->th = bh;
     BCK(b, cudaMemcpyAsync(b->base, save, span, cudaMemcpyDeviceToDevice, b->stream), "restore");
@@ -577,13 +629,14 @@ int lbm_batch_autotune(lbm_batch b)
     return ur;
 }
 
-int lbm_batch_get_config(lbm_batch b, int* out4)
+int lbm_batch_get_config(lbm_batch b, int* out5)
 {
-    if (!b || !out4) return bfail(b, LBM_EINVAL, "NULL argument");
-    out4[0] = b->threads;
-    out4[1] = b->ctas;
-    out4[2] = b->tw;
-    out4[3] = b->th;
+    if (!b || !out5) return bfail(b, LBM_EINVAL, "NULL argument");
+    out5[0] = b->threads;
+    out5[1] = b->ctas;
+    out5[2] = b->tw;
+    out5[3] = b->th;
+    out5[4] = b->npt;
     return LBM_OK;
 }
 
@@ -592,6 +645,16 @@ int lbm_batch_set_wait_limit(lbm_batch b, long long spins)
     if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
     if (spins < 1) return bfail(b, LBM_EINVAL, "spins must be >= 1");
     b->wait_limit = spins;
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+int lbm_batch_set_rounding(lbm_batch b, int mode)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (mode != LBM_ROUND_DITHER && mode != LBM_ROUND_NEAREST)
+        return bfail(b, LBM_EINVAL, "unknown rounding mode %d", mode);
+    b->round_nearest = (mode == LBM_ROUND_NEAREST);
     drop_graphs(b);
     return LBM_OK;
 }

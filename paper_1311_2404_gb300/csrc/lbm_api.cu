@@ -47,7 +47,7 @@ struct lbm_ctx {
     double s[19];
     int alpha_mode = LBM_ALPHA_NEWTON, max_iter = 20, guard_steps = 2, feq_variant = 0;
     double tol = 1e-12, skip_eps = 1e-3, guard_tol = 1e-6;
-    bool mlp_loaded = false, alpha_out = false, use_graph = false;
+    bool mlp_loaded = false, alpha_out = false, use_graph = false, round_nearest = false;
     long long t = 0, launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -365,6 +365,16 @@ int lbm_set_alpha_output(lbm_handle h, int on)
     return LBM_OK;
 }
 
+int lbm_set_rounding(lbm_handle h, int mode)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (mode != LBM_ROUND_DITHER && mode != LBM_ROUND_NEAREST)
+        return fail(h, LBM_EINVAL, "unknown rounding mode %d", mode);
+    h->round_nearest = (mode == LBM_ROUND_NEAREST);
+    drop_graphs(h);
+    return LBM_OK;
+}
+
 int lbm_set_graph(lbm_handle h, int on)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
@@ -427,6 +437,7 @@ static StepParams make_params(lbm_ctx* h)
     p.omega = 1.0 / h->tau;
     p.F[0] = h->F[0]; p.F[1] = h->F[1]; p.F[2] = h->F[2];
     p.has_force = (h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0);
+    p.round_nearest = h->round_nearest ? 1 : 0;
     for (int k = 0; k < 19; ++k) {
         const double n2 = h->lattice == LBM_D3Q19 ? (double)mrt_norm2(k) : 1.0;
         p.mrt_c[k] = h->s[k] / n2;

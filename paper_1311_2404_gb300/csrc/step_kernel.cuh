@@ -91,8 +91,15 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
             evals = ar.evals;
             astat = ar.status;
         }
+        if (S::kHalf && !p.round_nearest) {
+            const unsigned salt = (unsigned)n * kSaltNode;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) S::store(B + (size_t)i * p.sq + n, d[i], L::w(i));
+            for (int i = 0; i < L::Q; ++i)
+                B[(size_t)i * p.sq + n] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) S::store(B + (size_t)i * p.sq + n, d[i], L::w(i));
+        }
         if (p.out) {
             static_cast<R*>(p.rho)[n] = rho;
 #pragma unroll

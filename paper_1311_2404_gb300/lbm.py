@@ -35,6 +35,7 @@ LBM_BGK, LBM_MRT, LBM_ELBM = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S = range(5)
 LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
 LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIXED2 = range(4)
+LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
 MLP_NPARAM = 1394
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ESTATE", 3: "LBM_ENOMEM",
@@ -68,6 +69,7 @@ _PROTOS = {
     "lbm_load_alpha_mlp": (_i, [_vp, _vp, _i]),
     "lbm_set_alpha_output": (_i, [_vp, _i]),
     "lbm_set_graph": (_i, [_vp, _i]),
+    "lbm_set_rounding": (_i, [_vp, _i]),
     "lbm_init_equilibrium": (_i, [_vp, _vp, _vp, _i]),
     "lbm_step": (_i, [_vp, _i]),
     "lbm_get_time": (_i, [_vp, ctypes.POINTER(_ll)]),
@@ -93,6 +95,7 @@ _PROTOS = {
     "lbm_batch_get_macro": (_i, [_vp, _i, _vp, _vp, _i]),
     "lbm_batch_sync": (_i, [_vp]),
     "lbm_batch_set_wait_limit": (_i, [_vp, _ll]),
+    "lbm_batch_set_rounding": (_i, [_vp, _i]),
     "lbm_batch_inject_missing_arrival": (_i, [_vp, _i]),
     "lbm_batch_launch_count": (_ll, [_vp]),
     "lbm_batch_nodes": (_sz, [_vp]),
@@ -212,6 +215,10 @@ def lbm_load_alpha_mlp(h, params):
 
 def lbm_set_alpha_output(h, on):
     _check(_L.lbm_set_alpha_output(h, int(bool(on))), h)
+
+
+def lbm_set_rounding(h, mode):
+    _check(_L.lbm_set_rounding(h, int(mode)), h)
 
 
 def lbm_set_graph(h, on):
@@ -359,7 +366,7 @@ def lbm_batch_autotune(b):
 
 
 def lbm_batch_get_config(b):
-    out = np.zeros(4, dtype=np.int32)
+    out = np.zeros(5, dtype=np.int32)
     _check(_L.lbm_batch_get_config(b, _ptr(out)), b, batch=True)
     return out
 
@@ -372,6 +379,10 @@ def lbm_batch_get_macro(b, d, rho, u):
     ref = rho if rho is not None else u
     _check(_L.lbm_batch_get_macro(b, int(d), _ptr(rho), _ptr(u), _field_dtype(ref)), b,
            batch=True)
+
+
+def lbm_batch_set_rounding(b, mode):
+    _check(_L.lbm_batch_set_rounding(b, int(mode)), b, batch=True)
 
 
 def lbm_batch_set_wait_limit(b, spins):

@@ -82,26 +82,32 @@ def test_elbm_turbulence_reduced_copy(dtype, tol, mode):
 
 
 def test_taylor_green_storage_precision_vs_analytic():
-    """256^3 vortex, 1000 steps, FP32S vs FP16S vs BF16S: relative L2 of the
-    velocity against the analytic field.  FP32S must stay within 1e-3 (the
-    stated error bar); the half-width storages are reported and bounded."""
+    """256^3 vortex, 1000 steps: relative L2 of the velocity against the
+    analytic field for FP32S, FP16S and BF16S storage.  FP32S and FP16S with
+    the default dithered rounding must stay within 1e-3 (the stated error
+    bar); FP16S with round-to-nearest (biased: 3e-3) and BF16S are reported
+    and loosely bounded."""
     n, tau, u0, T = 256, 0.6, 0.05, 1000
     nu = an.nu_of_tau(tau)
     rho, u = wl.taylor_green(n, u0, nz=n, D=3)
     ref = an.taylor_green_u(n, u0, nu, T, D=3, nz=1)
     errs = {}
-    for dt in (lbm.LBM_F32S, lbm.LBM_F16S, lbm.LBM_BF16S):
+    cases = (("f32s", lbm.LBM_F32S, lbm.LBM_ROUND_DITHER),
+             ("f16s", lbm.LBM_F16S, lbm.LBM_ROUND_DITHER),
+             ("f16s_nearest", lbm.LBM_F16S, lbm.LBM_ROUND_NEAREST),
+             ("bf16s", lbm.LBM_BF16S, lbm.LBM_ROUND_DITHER))
+    for name, dt, rnd in cases:
         sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_BGK, tau, dt)
+        lbm.lbm_set_rounding(sim.h, rnd)
         sim.init(rho.astype(np.float32), u.astype(np.float32))
         sim.step(T)
         ug = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
         lbm.lbm_get_macro(sim.h, None, ug)
         sim.close()
-        # every z plane of the extruded field; compare plane-averaged and worst plane
         ugp = ug.double().cpu().numpy()
-        errs[dt] = max(an.rel_l2(ugp[:, z:z + 1], ref) for z in (0, n // 3, n - 1))
-    print("TG256 rel-L2 u vs analytic: f32s %.3e f16s %.3e bf16s %.3e"
-          % (errs[lbm.LBM_F32S], errs[lbm.LBM_F16S], errs[lbm.LBM_BF16S]))
-    assert errs[lbm.LBM_F32S] < 1e-3
-    assert errs[lbm.LBM_F16S] < 5e-2
-    assert errs[lbm.LBM_BF16S] < 5e-1
+        errs[name] = max(an.rel_l2(ugp[:, z:z + 1], ref) for z in (0, n // 3, n - 1))
+    print("TG256 rel-L2 u vs analytic: " + " ".join(f"{k} {v:.3e}" for k, v in errs.items()))
+    assert errs["f32s"] < 1e-3
+    assert errs["f16s"] < 1e-3
+    assert errs["f16s_nearest"] < 5e-2
+    assert errs["bf16s"] < 5e-1
