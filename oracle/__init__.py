@@ -26,7 +26,7 @@ _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 # model / alpha-mode codes of the oracle's parameter block
-BGK, MRT, ELBM = 0, 1, 2
+BGK, MRT, ELBM, REG, SMAG = 0, 1, 2, 3, 4
 NEWTON, SERIES_GUARDED, MLP_GUARDED, FIXED2 = 0, 1, 2, 3
 # per-node alpha outcomes
 AL_CONV, AL_SKIP, AL_CLAMP, AL_NOCONV, AL_FIXED, AL_GUARDED = range(6)
@@ -55,6 +55,7 @@ class OracleParams(ctypes.Structure):
         ("s", ctypes.c_double * 19), ("tol", ctypes.c_double),
         ("skip_eps", ctypes.c_double), ("guard_tol", ctypes.c_double),
         ("mlp", ctypes.POINTER(ctypes.c_double)),
+        ("smag_cs", ctypes.c_double),
     ]
 
 
@@ -139,7 +140,8 @@ def mrt_matrix():
 
 def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0),
                 s=None, alpha_mode=NEWTON, max_iter=20, feq_variant=0, tol=1e-12,
-                skip_eps=1e-3, guard_tol=1e-6, guard_steps=2, mlp=None, nthreads=0):
+                skip_eps=1e-3, guard_tol=1e-6, guard_steps=2, mlp=None, nthreads=0,
+                smag_cs=0.1):
     p = OracleParams()
     p.nx, p.ny, p.nz, p.D, p.model = nx, ny, nz, D, model
     p.alpha_mode, p.max_iter, p.feq_variant = alpha_mode, max_iter, feq_variant
@@ -151,6 +153,7 @@ def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0)
     for k in range(19):
         p.s[k] = float(ss[k])
     p.tol, p.skip_eps, p.guard_tol = tol, skip_eps, guard_tol
+    p.smag_cs = smag_cs
     if mlp is not None:
         arr = np.ascontiguousarray(mlp, dtype=np.float64)
         p._mlp_keep = arr  # keep alive with the struct
@@ -159,7 +162,8 @@ def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0)
 
 
 def collide(p: OracleParams, f) -> tuple:
-    """One node: returns (f_post, rho, v[3], info[alpha, evals, status, |g|/a2])."""
+    """One node: returns (f_post, rho, v[3], info): info = [alpha, evals,
+    status, |g|/a2] for ELBM, info[0] = total relaxation time for SMAG."""
     ff = np.array(f, dtype=np.float64)
     rho = np.zeros(1)
     v = np.zeros(3)
@@ -235,3 +239,28 @@ def run(p: OracleParams, F: np.ndarray, nsteps: int, mask: np.ndarray | None = N
 
 def max_threads(nthreads: int = 0) -> int:
     return lib().oracle_max_threads(nthreads)
+
+
+def kinetic_energy_enstrophy(v: np.ndarray):
+    """E = (1/2V) sum |v|^2 and Omega = (1/2V) sum |curl v|^2 of a periodic
+    velocity field v [D, nz, ny, nx] (lattice units, D = 2 or 3), the
+    vorticity by second-order central differences (Sec. 5.2, Kida vortex
+    diagnostics); a 2-D field has only the z component of the vorticity.
+    FP64, whole-array NumPy."""
+    v = np.asarray(v, dtype=np.float64)
+
+    def d(f, axis):          # axis 0: z, 1: y, 2: x of a [nz, ny, nx] field
+        return 0.5 * (np.roll(f, -1, axis=axis) - np.roll(f, 1, axis=axis))
+
+    vx, vy = v[0], v[1]
+    vz = v[2] if v.shape[0] == 3 else np.zeros_like(vx)
+    wz = d(vy, 2) - d(vx, 1)
+    if v.shape[0] == 3:
+        wx = d(vz, 1) - d(vy, 0)
+        wy = d(vx, 0) - d(vz, 2)
+    else:
+        wx = wy = np.zeros_like(vx)
+    V = vx.size
+    E = 0.5 * (vx * vx + vy * vy + vz * vz).sum() / V
+    Om = 0.5 * (wx * wx + wy * wy + wz * wz).sum() / V
+    return E, Om

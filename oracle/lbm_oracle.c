@@ -15,7 +15,9 @@
  *   moments (Eq. lb_macro), force-shifted velocity (Eq. edm_momentum),
  *   LBGK (Eq. lbgk with the relaxation toward f_eq as in Algorithm cnp),
  *   MRT (Eq. mrt_collision), ELBM (Eqs. elbm and alpha_cond),
- *   Guo forcing (Eq. guo_force) and EDM forcing (Eq. edm_force).
+ *   Guo forcing (Eq. guo_force) and EDM forcing (Eq. edm_force),
+ *   regularized LBGK (Sec. 2.1.1) and LBGK with the Smagorinsky subgrid
+ *   model (Sec. 2.1.4, Eqs. smagorinsky and taut).
  *
  * Readings of garbled or silent passages (each also listed in the design notes):
  *   - Eq. lbgk / Eq. elbm print "+(f - f_eq)/tau"; Algorithm cnp relaxes
@@ -268,6 +270,7 @@ typedef struct {
     double skip_eps;  /* alpha = 2 when max_i |x_i| < skip_eps */
     double guard_tol; /* guarded modes: accept when the last correction <= guard_tol */
     const double* mlp;/* MLP parameters for alpha_mode 2 */
+    double smag_cs;   /* Smagorinsky constant C_S (model 4) */
 } oracle_params;
 
 /* Per-node ELBM outcome. */
@@ -541,6 +544,57 @@ static int collide_node(const olat* L, const oracle_params* p, double* f, double
         }
         if (info)
             for (int k = 0; k < 4; ++k) info[k] = al[k];
+    } else if (p->model == 3 || p->model == 4) {
+        /* Non-equilibrium momentum flux Pi_ab = sum_i (f_i - fe_i)(e_ia e_ib
+         * - delta_ab c_s^2), c_s^2 = 1/3, about an equilibrium fe of the
+         * node's own mass (so the delta term drops out):
+         *  REG (Sec. 2.1.1): fe = f_eq(rho, u), u = j / rho, so that f - fe
+         *    carries no mass and no momentum; the populations are replaced by
+         *    fe_i + f_reg_i, f_reg_i = w_i / (2 c_s^4) (e_ia e_ib - c_s^2
+         *    delta_ab) Pi_ab, and the LBGK collision with Guo's force then
+         *    acts on them: f' = f~ + (f_eq(rho, v) - f~) / tau + Guo term.
+         *  SMAG (Sec. 2.1.4): fe = f_eq(rho, v), the collision's own
+         *    equilibrium, Pi = Q of Eq. taut; LBGK with tau0 + tau_t. */
+        feq_poly(L, rho, v, feq);
+        double fe[OQMAX];
+        if (p->model == 3) feq_poly(L, rho, u, fe);
+        else
+            for (int i = 0; i < Q; ++i) fe[i] = feq[i];
+        double Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int i = 0; i < Q; ++i) {
+            double fn = f[i] - fe[i];
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b)
+                    Pi[a][b] += fn * (L->e[i][a] * L->e[i][b] - (a == b ? 1.0 / 3.0 : 0.0));
+        }
+        double tau = p->tau;
+        if (p->model == 4) {
+            /* Eq. taut: tau_t = (sqrt(tau0^2 + 4 C_S^2 |Q| / c_s^4) - tau0) / 2,
+             * |Q| = (Q_ab Q_ab)^(1/2); total relaxation time tau0 + tau_t
+             * (Eq. smagorinsky with nu_t = tau_t / 3). */
+            double qq = 0.0;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) qq += Pi[a][b] * Pi[a][b];
+            double tau_t = 0.5 * (sqrt(p->tau * p->tau + 4.0 * 9.0 * p->smag_cs * p->smag_cs *
+                                       sqrt(qq)) - p->tau);
+            tau = p->tau + tau_t;
+            if (info) info[0] = tau;
+        }
+        for (int i = 0; i < Q; ++i) {
+            double ev = edot(L, i, v), fi = 0.0;
+            for (int a = 0; a < D; ++a)
+                fi += (3.0 * (L->e[i][a] - v[a]) + 9.0 * ev * L->e[i][a]) * F[a];
+            double guo = (1.0 - 0.5 / tau) * L->w[i] * fi;
+            double ft = f[i];
+            if (p->model == 3) {
+                double pr = 0.0;
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b)
+                        pr += (L->e[i][a] * L->e[i][b] - (a == b ? 1.0 / 3.0 : 0.0)) * Pi[a][b];
+                ft = fe[i] + L->w[i] * 4.5 * pr;
+            }
+            f[i] = ft + (feq[i] - ft) / tau + guo;
+        }
     } else {
         return -1;
     }

@@ -131,12 +131,35 @@ def turbulence(n: int = 256, k0: float = 4.0, u_rms: float = 0.04, seed: int = 2
     with np.errstate(divide="ignore", invalid="ignore"):
         kdotu = (kx * uh[0] + ky * uh[1] + kz * uh[2]) / np.where(k2 > 0, k2, 1.0)
     uh = [uh[0] - kx * kdotu, uh[1] - ky * kdotu, uh[2] - kz * kdotu]
-    u = np.stack([np.fft.irfftn(c, s=(n, n, n)) for c in uh])     # [3, z, y, x]
+    u = np.stack([np.fft.irfftn(c, s=(n, n, n), axes=(0, 1, 2)) for c in uh])   # [3, z, y, x]
     u -= u.mean(axis=(1, 2, 3), keepdims=True)
     rms = math.sqrt(float((u * u).sum(axis=0).mean()) / 3.0)
     u *= u_rms / rms
     rho = np.ones((n, n, n))
     return rho, u
+
+
+# --------------------------------------------------------------------------
+# Kida vortex (Sec. 5.2)
+# --------------------------------------------------------------------------
+def kida(n: int = 256, u0: float = 0.05, rho0: float = 1.0):
+    """Kida's initial field on an n^3 periodic box of face 2 pi (node i at
+    x = 2 pi i / n):
+
+        u_x = u0 sin x (cos 3y cos z - cos y cos 3z)
+        u_y = u0 sin y (cos 3z cos x - cos z cos 3x)
+        u_z = u0 sin z (cos 3x cos y - cos x cos 3y)
+
+    with uniform density rho0 (the free decay starts from this velocity field;
+    Sec. 5.2 runs it at u0 = 0.05).  Returns (rho [n,n,n], u [3,n,n,n]) in
+    float64."""
+    c = 2.0 * math.pi * np.arange(n) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    u = np.empty((3, n, n, n))
+    u[0] = u0 * np.sin(x) * (np.cos(3 * y) * np.cos(z) - np.cos(y) * np.cos(3 * z))
+    u[1] = u0 * np.sin(y) * (np.cos(3 * z) * np.cos(x) - np.cos(z) * np.cos(3 * x))
+    u[2] = u0 * np.sin(z) * (np.cos(3 * x) * np.cos(y) - np.cos(x) * np.cos(3 * y))
+    return np.full((n, n, n), rho0), u
 
 
 # --------------------------------------------------------------------------
