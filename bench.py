@@ -7,7 +7,7 @@ u0 0.05.  One bench step = one lattice Boltzmann time step over all nodes
 (one fused stream-collide launch).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tg256|duct|elbm|batch] [--dtype f32s|f16s|bf16s|f32]
+                  [--workload tg256|duct|elbm|kida|batch] [--dtype f32s|f16s|bf16s|f32]
 
 For N > 1 (torchrun) every rank runs an independent replica of the workload
 (the domains do not exchange data; weak scaling) and rank 0 reports the
@@ -43,15 +43,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tg256", choices=["tg256", "duct", "elbm", "batch"])
+    ap.add_argument("--workload", default="tg256",
+                    choices=["tg256", "duct", "elbm", "kida", "batch"])
     ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
                     help="ELBM alpha solve for --workload elbm")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
+    ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
+                    help="distribution access pattern (AA: one array)")
     ap.add_argument("--round", default="dither", choices=["dither", "nearest"],
                     help="rounding of FP16/BF16 stores")
     ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
-    ap.add_argument("--model", default="", choices=["", "bgk", "mrt"],
-                    help="override the collision model of the tg256 / duct workloads")
+    ap.add_argument("--model", default="", choices=["", "bgk", "mrt", "reg", "smag"],
+                    help="override the collision model of the tg256 / duct / kida workloads")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--size", type=int, default=0,
                     help="override the cube edge of the 256^3 workloads (profiling runs)")
@@ -150,11 +153,16 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def workload_spec(name, dtype, size=0):
+def workload_spec(name, dtype, size=0, model=""):
     spec = _workload_spec(name, dtype)
-    if size and name in ("tg256", "elbm"):
+    if model:
+        spec["model"] = {"bgk": 0, "mrt": 1, "reg": 3, "smag": 4}[model]
+        for m in ("lbgk", "mrt", "smag"):
+            if f"_{m}_" in spec["name"]:
+                spec["name"] = spec["name"].replace(f"_{m}_", f"_{model}_")
+    if size and name in ("tg256", "elbm", "kida"):
         spec["n"] = (size, size, size)
-        spec["name"] = spec["name"].replace("256^3", f"{size}^3")
+        spec["name"] = spec["name"].replace("256^3", f"{size}^3").replace("350^3", f"{size}^3")
     if size and name == "duct":
         spec["n"] = (2 * size, size, size)
         spec["name"] = spec["name"].replace("512x256x256", f"{2 * size}x{size}x{size}")
@@ -177,6 +185,11 @@ def _workload_spec(name, dtype):
         return dict(kind="turb", name="d3q19_elbm_decaying_turbulence_256^3", n=(256, 256, 256),
                     lattice=lbm.LBM_D3Q19, model=lbm.LBM_ELBM, tau=0.5005, dtype=dmap[dtype],
                     mask=None, force=(0, 0, 0))
+    if name == "kida":
+        # Re = N u0 / nu = 4000 at N = 350, u0 = 0.05 (the paper's smaller Kida case)
+        return dict(kind="kida", name="d3q19_smag_kida_vortex_350^3", n=(350, 350, 350),
+                    lattice=lbm.LBM_D3Q19, model=lbm.LBM_SMAG, tau=0.5 + 3 * 350 * 0.05 / 4000,
+                    dtype=dmap[dtype], mask=None, force=(0, 0, 0))
     raise ValueError(name)
 
 
@@ -190,6 +203,9 @@ def workload_inputs(spec):
         mask, _ = wl.duct_with_spheres(nx, ny, nz)
         rho = np.ones((nz, ny, nx))
         u = np.zeros((3, nz, ny, nx))
+    elif spec["kind"] == "kida":
+        rho, u = wl.kida(nx, 0.05)
+        mask = None
     else:
         rho, u = wl.turbulence(nx)
         mask = None
@@ -210,17 +226,16 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1311_2404_gb300 import lbm
 
-    spec = workload_spec(args.workload, args.dtype, args.size)
-    if args.model:
-        spec["model"] = {"bgk": lbm.LBM_BGK, "mrt": lbm.LBM_MRT}[args.model]
-        spec["name"] = spec["name"].replace("lbgk", args.model).replace("mrt", args.model)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(nx, ny, nz, spec["lattice"], spec["model"], spec["tau"],
-                             spec["dtype"], stream=stream.cuda_stream)
+                             spec["dtype"], stream=stream.cuda_stream,
+                             pattern=lbm.LBM_PATTERN_AA if args.pattern == "aa"
+                             else lbm.LBM_PATTERN_AB)
         if mask is not None:
             sim.set_geometry(mask)
         if any(spec["force"]):
@@ -263,6 +278,18 @@ def run_ours(args):
         launches = lbm.lbm_launch_count(sim.h) - l0
         clocks = sampler.stop() if sampler else None
         lbm.lbm_sync(sim.h)
+        elbm_stats = None
+        diag = None
+        if spec["kind"] == "kida":
+            E, Om = lbm.lbm_kinetic_energy_enstrophy(sim.h)
+            diag = {"t": int(lbm.lbm_get_time(sim.h)), "E": E, "Omega": Om,
+                    "E_over_E0": round(E / (3 * 0.05 ** 2 / 8), 6)}
+        if spec["model"] == lbm.LBM_ELBM:
+            st = lbm.lbm_get_elbm_stats(sim.h)
+            elbm_stats = {"g_evals_per_node": round(st[0] / max(st[5], 1), 4),
+                          "skipped_frac": round(st[1] / max(st[5], 1), 4),
+                          "guess_accepted_frac": round(st[4] / max(st[5], 1), 4),
+                          "at_cap": int(st[3])}
 
         # end to end through the public API with host buffers
         pin_r = torch.from_numpy(rho).pin_memory()
@@ -310,10 +337,13 @@ def run_ours(args):
         "dtype": {"f32s": "f32", "f32": "f32", "f16s": "f32", "bf16s": "f32"}[args.dtype],
         "data": "synthetic (seeded analytic/random initial fields; no dataset)",
         "config": {"workload": spec["name"], "lattice": "D3Q19",
-                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
+                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG",
+                             4: "SMAG"}[spec["model"]],
+                   **({"smagorinsky_cs": 0.1} if spec["model"] == 4 else {}),
                    "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
                    **({"alpha": args.alpha} if spec["model"] == 2 else {}),
                    **({"rounding": args.round} if args.dtype in ("f16s", "bf16s") else {}),
+                   **({"pattern": "AA"} if args.pattern == "aa" else {}),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
                          % (B_PER_NODE[args.dtype] * nodes / 1e9)},
@@ -326,6 +356,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if elbm_stats:
+        line["elbm"] = elbm_stats
+    if diag:
+        line["kida"] = diag
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=12.0)
     print(json.dumps(line), flush=True)
@@ -341,7 +375,8 @@ def _oracle_sample(spec, nz_s, ny_s=None):
     from paper_1311_2404_gb300 import workloads as wl
     nx, ny, nz = spec["n"]
     ny_s = ny_s or ny
-    model = {0: oracle.BGK, 1: oracle.MRT, 2: oracle.ELBM}[spec["model"]]
+    model = {0: oracle.BGK, 1: oracle.MRT, 2: oracle.ELBM, 3: oracle.REG,
+             4: oracle.SMAG}[spec["model"]]
     p = oracle.make_params(nx, ny_s, nz_s, D=3, model=model, tau=spec["tau"],
                            force=spec["force"])
     if spec["kind"] == "tg":
@@ -354,7 +389,7 @@ def _oracle_sample(spec, nz_s, ny_s=None):
         rho = np.ones((nz_s, ny_s, nx))
         u = np.zeros((3, nz_s, ny_s, nx))
     else:
-        r, uu = wl.turbulence(nx)
+        r, uu = wl.kida(nx, 0.05) if spec["kind"] == "kida" else wl.turbulence(nx)
         rho = np.ascontiguousarray(r[:nz_s, :ny_s])
         u = np.ascontiguousarray(uu[:, :nz_s, :ny_s])
         mask = None
@@ -386,7 +421,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec = workload_spec(args.workload, args.dtype, args.size)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model)
     import oracle
     oracle.build()
     cores = oracle.max_threads(0)
@@ -418,7 +453,9 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded analytic/random initial fields; no dataset)",
         "config": {"workload": spec["name"], "lattice": "D3Q19",
-                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM"}[spec["model"]],
+                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG",
+                             4: "SMAG"}[spec["model"]],
+                   **({"smagorinsky_cs": 0.1} if spec["model"] == 4 else {}),
                    "storage": "f64 (oracle)", "tau": spec["tau"],
                    "nodes": spec["n"][0] * spec["n"][1] * spec["n"][2]},
         "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",

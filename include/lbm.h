@@ -60,7 +60,13 @@ enum {
 
 /* ---- lattices, collision models, storage types ------------------------ */
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };          /* Sec. 2, Fig. lattices, Table bgkweights */
-enum { LBM_BGK = 0, LBM_MRT = 1, LBM_ELBM = 2 }; /* Eqs. lbgk, mrt_collision, elbm */
+/* Collision models: LBGK (Eq. lbgk, Guo forcing), MRT (Eq. mrt_collision,
+ * D3Q19), ELBM (Eqs. elbm and alpha_cond, exact-difference forcing),
+ * regularized LBGK (Sec. 2.1.1: the non-equilibrium part is replaced by its
+ * projection w_i/(2 c_s^4) (e_i e_i - c_s^2 I) : Pi^neq before the LBGK
+ * relaxation) and LBGK with the Smagorinsky subgrid model (Sec. 2.1.4,
+ * Eqs. smagorinsky and taut: tau = tau0 + tau_t per node). */
+enum { LBM_BGK = 0, LBM_MRT = 1, LBM_ELBM = 2, LBM_REG = 3, LBM_SMAG = 4 };
 /* Storage of f_i in device memory.  *_S types store f_i - w_i (the
  * round-off-minimising form of Sec. 3.7); arithmetic is FP64 for LBM_F64 and
  * FP32 for all others. */
@@ -72,6 +78,11 @@ enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32S = 2, LBM_F16S = 3, LBM_BF16S = 4 };
  * step to step repeats the same error and drifts).  NEAREST: round to
  * nearest even. */
 enum { LBM_ROUND_DITHER = 0, LBM_ROUND_NEAREST = 1 };
+/* Access patterns (Sec. 3.3): AB keeps two copies of the distributions and
+ * alternates between them; AA keeps one copy, alternating a pull/push step
+ * (even t) with an in-place step (odd t).  Same bytes moved per update; AA
+ * halves the footprint. */
+enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 };
 /* Element type of macroscopic-field arrays crossing the ABI. */
 enum { LBM_FIELD_F64 = 0, LBM_FIELD_F32 = 1 };
 /* ELBM alpha modes (Eq. alpha_cond).  NEWTON: safeguarded FP64 Newton from
@@ -119,6 +130,13 @@ LBM_API size_t lbm_required_bytes(lbm_handle h);
  * LBM_EINVAL (NULL, misaligned or not device memory). */
 LBM_API int lbm_bind_memory(lbm_handle h, void* dev_ptr, size_t bytes);
 
+/* Access pattern (LBM_PATTERN_AB default, or LBM_PATTERN_AA).  Must precede
+ * any call that puts device memory in use (lbm_bind_memory, lbm_set_geometry,
+ * lbm_init_equilibrium, ...); lbm_required_bytes reflects it afterwards.
+ * Results are bitwise equal for both patterns.  LBM_ESTATE if memory is
+ * already in use. */
+LBM_API int lbm_set_access_pattern(lbm_handle h, int pattern);
+
 /* Enqueue all work on this cudaStream_t (NULL = legacy default stream). */
 LBM_API int lbm_set_stream(lbm_handle h, void* cuda_stream);
 
@@ -143,6 +161,11 @@ LBM_API int lbm_set_force(lbm_handle h, double fx, double fy, double fz);
  * my, mz.  q must be 19.  Default: 0 for conserved moments, 1/tau for the
  * five stress moments, 1.19, 1.4, 1.2, 1.4, 1.98 for the others. */
 LBM_API int lbm_set_mrt_rates(lbm_handle h, const double* s, int q);
+
+/* Smagorinsky constant C_S of an LBM_SMAG handle (Eq. taut; default 0.1,
+ * the value Sec. 2.1.4 gives for LB models).  C_S = 0 is plain LBGK.
+ * LBM_EINVAL for another model or C_S < 0 / not finite. */
+LBM_API int lbm_set_smagorinsky(lbm_handle h, double cs);
 
 /* ELBM alpha solve (Eq. alpha_cond): mode (LBM_ALPHA_*), Newton relative
  * step tolerance tol (default 1e-12), Newton evaluation cap max_iter
@@ -211,6 +234,16 @@ LBM_API int lbm_get_alpha(lbm_handle h, double* alpha);
  * out[1..D] = sum rho v_a, out[D+1] = sum rho |v|^2 / 2.  out is host
  * memory of D + 2 doubles.  Synchronises. */
 LBM_API int lbm_reduce(lbm_handle h, double* out);
+
+/* Kinetic energy and enstrophy of the last step's velocity field (the
+ * decaying-turbulence diagnostics of Sec. 5.2): out[0] = E = (1/2N) sum |v|^2,
+ * out[1] = Omega = (1/2N) sum |curl v|^2 over all N nodes, the vorticity by
+ * second-order central differences with periodic wrap (on D2Q9 only its z
+ * component).  Accumulated in FP64 on the GPU in a fixed order (bitwise
+ * reproducible).  out is host memory of 2 doubles.  LBM_ESTATE before the
+ * first output step or when a geometry is set (the stencil assumes a fully
+ * periodic domain).  Synchronises. */
+LBM_API int lbm_kinetic_energy_enstrophy(lbm_handle h, double* out);
 
 /* ELBM counters accumulated since init (host, 6 values): g evaluations,
  * skipped nodes, clamped nodes, nodes at the iteration cap, nodes accepted

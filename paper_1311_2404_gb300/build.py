@@ -23,7 +23,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # same sequence of IEEE operations so that a batched domain is bitwise equal
 # to the same domain run alone: no multiply-add contraction in those units
 # (both are HBM-bound; the extra ALU work is free).
-PER_FILE = {"k_bgk.cu": ["-fmad=false"], "k_batch.cu": ["-fmad=false"]}
+# Every translation unit holding a stream-and-collide kernel is compiled
+# without multiply-add contraction: the kernels write their fused operations
+# explicitly, so the AB and AA instances, the batched kernel and the
+# single-domain kernel apply the same operation sequence and agree bitwise.
+NO_CONTRACT = ["-fmad=false"]
+PER_FILE = {f: NO_CONTRACT for f in ("k_bgk.cu", "k_mrt.cu", "k_elbm2.cu", "k_elbm3.cu",
+                                      "k_les.cu", "k_batch.cu")}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-fvisibility=hidden", "--ftz=false", "--prec-div=true",
          "--prec-sqrt=true", "-I", INCLUDE, "-I", CSRC]

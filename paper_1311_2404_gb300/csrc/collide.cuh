@@ -132,6 +132,166 @@ __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R
 }
 
 // ---------------------------------------------------------------------------
+// Regularized LBGK (Sec. 2.1.1) and LBGK with the Smagorinsky subgrid model
+// (Sec. 2.1.4).  Both need the non-equilibrium momentum flux
+//   Pi_ab = sum_i (f_i - fe_i) e_ia e_ib
+// about an equilibrium fe of the node's own mass; only the even (pair-sum)
+// parts contribute.
+//  REG:  fe = f_eq(rho, u), u = j / rho, so that f - fe has no mass and no
+//        momentum; the populations become f~ = fe + f_reg,
+//        f_reg_i = w_i / (2 c_s^4) (e_ia e_ib - c_s^2 delta_ab) Pi_ab, and the
+//        LBGK collision with Guo's force acts on them:
+//        f' = f~ + omega (f_eq(rho, v) - f~) + Guo term.
+//  SMAG: fe = f_eq(rho, v), Pi = Q of Eq. taut,
+//        tau = tau0 + tau_t, tau_t = (sqrt(tau0^2 + 4 C_S^2 |Q| / c_s^4) - tau0)/2,
+//        |Q| = (Q_ab Q_ab)^(1/2); then LBGK with that tau.
+// ---------------------------------------------------------------------------
+template <class L, class R>
+__host__ __device__ __forceinline__ void eq_pairs(R rho, R drho, R u0, R u1, R u2,
+                                                  R (&ev)[(L::Q - 1) / 2],
+                                                  R (&od)[(L::Q - 1) / 2], R& e0)
+{
+    const R m15 = R(-1.5) * fma(u0, u0, fma(u1, u1, u2 * u2));
+    const R w0 = (R)L::w(0);
+    e0 = fma(w0 * rho, m15, w0 * drho);
+#pragma unroll
+    for (int q = 0; q < (L::Q - 1) / 2; ++q) {
+        const int i = 2 * q + 1;
+        const R wi = (R)L::w(i);
+        const R eu = edot<L, R>(i, u0, u1, u2);
+        ev[q] = fma(wi * rho, fma(R(4.5) * eu, eu, m15), wi * drho);
+        od[q] = (first_order_coef<L, R>(i) * rho) * eu;
+    }
+}
+
+template <class L, class R, bool SMAG>
+__host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0, R cs2smag,
+                                                     R F0, R F1, R F2, bool has_force,
+                                                     R& rho_out, R (&v)[3])
+{
+    constexpr int NP = (L::Q - 1) / 2;
+    R S[NP], A[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        S[q] = d[2 * q + 1] + d[2 * q + 2];
+        A[q] = d[2 * q + 1] - d[2 * q + 2];
+    }
+    R drho = d[0];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) drho += S[q];
+    R j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
+        if (L::ex(i)) j[0] = L::ex(i) > 0 ? j[0] + A[q] : j[0] - A[q];
+        if (L::ey(i)) j[1] = L::ey(i) > 0 ? j[1] + A[q] : j[1] - A[q];
+        if (L::ez(i)) j[2] = L::ez(i) > 0 ? j[2] + A[q] : j[2] - A[q];
+    }
+    const R rho = R(1) + drho;
+    const R irho = R(1) / rho;
+    v[0] = fma(R(0.5), F0, j[0]) * irho;
+    v[1] = fma(R(0.5), F1, j[1]) * irho;
+    v[2] = (L::D == 3) ? fma(R(0.5), F2, j[2]) * irho : R(0);
+    const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
+    // equilibrium the flux is taken about (even/odd pair parts, rest value)
+    R ev[NP], od[NP], e0;
+    if (SMAG)
+        eq_pairs<L, R>(rho, drho, v[0], v[1], v[2], ev, od, e0);
+    else
+        eq_pairs<L, R>(rho, drho, j[0] * irho, j[1] * irho, (L::D == 3) ? j[2] * irho : R(0),
+                       ev, od, e0);
+    R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
+        const R ns = fma(R(-2), ev[q], S[q]);        // pair sum of f - fe
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        if (ex) P[0] += ns;
+        if (ey) P[1] += ns;
+        if (ez) P[2] += ns;
+        if (ex && ey) P[3] = (ex * ey > 0) ? P[3] + ns : P[3] - ns;
+        if (ex && ez) P[4] = (ex * ez > 0) ? P[4] + ns : P[4] - ns;
+        if (ey && ez) P[5] = (ey * ez > 0) ? P[5] + ns : P[5] - ns;
+    }
+    R om = om0;
+    if (SMAG) {
+        const R qq = fma(P[0], P[0], fma(P[1], P[1], P[2] * P[2])) +
+                     R(2) * fma(P[3], P[3], fma(P[4], P[4], P[5] * P[5]));
+        const R tau_t = R(0.5) * (sqrt(fma(tau0, tau0, R(36) * cs2smag * sqrt(qq))) - tau0);
+        om = R(1) / (tau0 + tau_t);
+    }
+    const R cf = fma(R(-0.5), om, R(1));
+    if (SMAG) {
+        R d0 = fma(om, e0 - d[0], d[0]);
+        if (has_force) d0 = fma(cf, R(-3) * (R)L::w(0) * vF, d0);
+        d[0] = d0;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int i = 2 * q + 1;
+            R dp = fma(om, (ev[q] + od[q]) - d[i], d[i]);
+            R dm = fma(om, (ev[q] - od[q]) - d[i + 1], d[i + 1]);
+            if (has_force) {
+                const R wi = (R)L::w(i);
+                const R eu = edot<L, R>(i, v[0], v[1], v[2]);
+                const R eF = edot<L, R>(i, F0, F1, F2);
+                const R ge = cf * wi * fma(R(9) * eu, eF, R(-3) * vF);
+                const R go = cf * first_order_coef<L, R>(i) * eF;
+                dp += ge + go;
+                dm += ge - go;
+            }
+            d[i] = dp;
+            d[i + 1] = dm;
+        }
+    } else {
+        // collision equilibrium at v (equal to fe without a force)
+        R evv[NP], odv[NP], e0v;
+        if (has_force) {
+            eq_pairs<L, R>(rho, drho, v[0], v[1], v[2], evv, odv, e0v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) { evv[q] = ev[q]; odv[q] = od[q]; }
+            e0v = e0;
+        }
+        const R tr3 = (P[0] + P[1] + P[2]) * R(1.0 / 3.0);
+        {
+            const R ft = fma((R)L::w(0) * R(4.5), -tr3, e0);
+            R d0 = fma(om, e0v - ft, ft);
+            if (has_force) d0 = fma(cf, R(-3) * (R)L::w(0) * vF, d0);
+            d[0] = d0;
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int i = 2 * q + 1;
+            const R wi = (R)L::w(i);
+            // e.Pi.e for this pair (the same for both members)
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            R ePe = R(0);
+            if (ex) ePe += P[0];
+            if (ey) ePe += P[1];
+            if (ez) ePe += P[2];
+            if (ex && ey) ePe = (ex * ey > 0) ? fma(R(2), P[3], ePe) : fma(R(-2), P[3], ePe);
+            if (ex && ez) ePe = (ex * ez > 0) ? fma(R(2), P[4], ePe) : fma(R(-2), P[4], ePe);
+            if (ey && ez) ePe = (ey * ez > 0) ? fma(R(2), P[5], ePe) : fma(R(-2), P[5], ePe);
+            const R freg = wi * R(4.5) * (ePe - tr3);
+            const R ftp = (ev[q] + od[q]) + freg, ftm = (ev[q] - od[q]) + freg;
+            R dp = fma(om, (evv[q] + odv[q]) - ftp, ftp);
+            R dm = fma(om, (evv[q] - odv[q]) - ftm, ftm);
+            if (has_force) {
+                const R eu = edot<L, R>(i, v[0], v[1], v[2]);
+                const R eF = edot<L, R>(i, F0, F1, F2);
+                const R ge = cf * wi * fma(R(9) * eu, eF, R(-3) * vF);
+                const R go = cf * first_order_coef<L, R>(i) * eF;
+                dp += ge + go;
+                dm += ge - go;
+            }
+            d[i] = dp;
+            d[i + 1] = dm;
+        }
+    }
+    rho_out = rho;
+}
+
+// ---------------------------------------------------------------------------
 // MRT (D3Q19)
 // ---------------------------------------------------------------------------
 // Moment polynomials of d'Humieres et al. (2002), evaluated on this file's
@@ -200,23 +360,24 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
     for (int q = 0; q < 9; ++q) {
         const int i = 2 * q + 1;
         drho += S[q];
-        if (L::ex(i)) j[0] += L::ex(i) * A[q];
-        if (L::ey(i)) j[1] += L::ey(i) * A[q];
-        if (L::ez(i)) j[2] += L::ez(i) * A[q];
+        if (L::ex(i)) j[0] = L::ex(i) > 0 ? j[0] + A[q] : j[0] - A[q];
+        if (L::ey(i)) j[1] = L::ey(i) > 0 ? j[1] + A[q] : j[1] - A[q];
+        if (L::ez(i)) j[2] = L::ez(i) > 0 ? j[2] + A[q] : j[2] - A[q];
     }
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
     const R F0 = sel<R>(p.F_f[0], p.F[0]), F1 = sel<R>(p.F_f[1], p.F[1]),
             F2 = sel<R>(p.F_f[2], p.F[2]);
-    v[0] = (j[0] + R(0.5) * F0) * irho;
-    v[1] = (j[1] + R(0.5) * F1) * irho;
-    v[2] = (j[2] + R(0.5) * F2) * irho;
-    const R usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const R vF = v[0] * F0 + v[1] * F1 + v[2] * F2;
+    v[0] = fma(R(0.5), F0, j[0]) * irho;
+    v[1] = fma(R(0.5), F1, j[1]) * irho;
+    v[2] = fma(R(0.5), F2, j[2]) * irho;
+    const R usq = fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2]));
+    const R m15 = R(-1.5) * usq;
+    const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
     const bool force = p.has_force != 0;
     // non-equilibrium parts: rest, pair sums (even), pair differences (odd)
     const R w0 = (R)L::w(0);
-    const R n0 = d[0] - (w0 * drho + w0 * (rho * (R(-1.5) * usq)));
+    const R n0 = d[0] - fma(w0 * rho, m15, w0 * drho);
     const R g0 = force ? R(-3) * w0 * vF : R(0);
     R NS[9], NA[9], GS[9], GA[9];
 #pragma unroll
@@ -225,11 +386,11 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
         const R wi = (R)L::w(i);
         const R bi = first_order_coef<L, R>(i);
         const R eu = edot<L, R>(i, v[0], v[1], v[2]);
-        NS[q] = S[q] - R(2) * (wi * drho + wi * (rho * (R(4.5) * eu * eu - R(1.5) * usq)));
-        NA[q] = A[q] - R(2) * (bi * (rho * eu));
+        NS[q] = fma(R(-2), fma(wi * rho, fma(R(4.5) * eu, eu, m15), wi * drho), S[q]);
+        NA[q] = fma(R(-2), (bi * rho) * eu, A[q]);
         if (force) {
             const R eF = edot<L, R>(i, F0, F1, F2);
-            GS[q] = R(2) * wi * (R(9) * eu * eF - R(3) * vF);   // Guo term, pair sum
+            GS[q] = R(2) * wi * fma(R(9) * eu, eF, R(-3) * vF);  // Guo term, pair sum
             GA[q] = R(2) * bi * eF;                               // Guo term, pair difference
         } else {
             GS[q] = GA[q] = R(0);
@@ -240,24 +401,24 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
     for (int k = 0; k < 19; ++k) {
         R m = 0, mf = 0;
         if (!mrt_odd(k) && mrt_M(k, 0) != 0) {
-            m += R(mrt_M(k, 0)) * n0;
-            mf += R(mrt_M(k, 0)) * g0;
+            m = fma(R(mrt_M(k, 0)), n0, m);
+            mf = fma(R(mrt_M(k, 0)), g0, mf);
         }
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int i = 2 * q + 1;
             if (mrt_M(k, i) != 0) {
-                m += R(mrt_M(k, i)) * (mrt_odd(k) ? NA[q] : NS[q]);
-                mf += R(mrt_M(k, i)) * (mrt_odd(k) ? GA[q] : GS[q]);
+                m = fma(R(mrt_M(k, i)), mrt_odd(k) ? NA[q] : NS[q], m);
+                mf = fma(R(mrt_M(k, i)), mrt_odd(k) ? GA[q] : GS[q], mf);
             }
         }
-        t[k] = sel<R>(p.mrt_c_f[k], p.mrt_c[k]) * m -
-               (force ? sel<R>(p.mrt_cf_f[k], p.mrt_cf[k]) * mf : R(0));
+        const R c = sel<R>(p.mrt_c_f[k], p.mrt_c[k]);
+        t[k] = force ? fma(c, m, -(sel<R>(p.mrt_cf_f[k], p.mrt_cf[k]) * mf)) : c * m;
     }
     R e0 = 0;
 #pragma unroll
     for (int k = 0; k < 19; ++k)
-        if (!mrt_odd(k) && mrt_M(k, 0) != 0) e0 += R(mrt_M(k, 0)) * t[k];
+        if (!mrt_odd(k) && mrt_M(k, 0) != 0) e0 = fma(R(mrt_M(k, 0)), t[k], e0);
     d[0] -= e0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -266,8 +427,8 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
             if (mrt_M(k, i) == 0) continue;
-            if (mrt_odd(k)) od += R(mrt_M(k, i)) * t[k];
-            else ev += R(mrt_M(k, i)) * t[k];
+            if (mrt_odd(k)) od = fma(R(mrt_M(k, i)), t[k], od);
+            else ev = fma(R(mrt_M(k, i)), t[k], ev);
         }
         d[i] -= ev + od;
         d[i + 1] -= ev - od;
@@ -355,8 +516,8 @@ struct LogEval {
         for (int i = 0; i < L::Q; ++i) {
             const double ax = a * x[i];
             const double l1 = log1p(ax);
-            s += f[i] * (1.0 + ax) * l1;
-            sp += f[i] * x[i] * l1;
+            s = fma(f[i] * (1.0 + ax), l1, s);
+            sp = fma(f[i] * x[i], l1, sp);
         }
         g = a * A + s;
         gp = A + sp;
@@ -387,8 +548,8 @@ struct SeriesEval {
             q = fma(q, a, k * c[k]);
         }
         // p = sum c_k a^(k-2), q = sum k c_k a^(k-2)
-        g = a * (A1 + a * p);
-        gp = A1 + a * q;
+        g = a * fma(a, p, A1);
+        gp = fma(a, q, A1);
     }
 };
 
@@ -522,6 +683,7 @@ __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const Step
 // below FP64 rounding).  f > 0, as the distributions of a valid state are.
 __host__ __device__ __forceinline__ double recip_nr(double f)
 {
+    if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
     double r = (double)(1.0f / (float)f);
     r = r * fma(-f, r, 2.0);
     r = r * fma(-f, r, 2.0);
@@ -548,7 +710,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         j[2] += L::ez(i) * di;
     }
     const double rho = 1.0 + drho;
-    const double irho = 1.0 / rho;
+    const double irho = recip_nr(rho);
     double u[3] = {j[0] * irho, j[1] * irho, (L::D == 3) ? j[2] * irho : 0.0};
     // equilibrium; for the entropic form also its pieces: f_eq_i = P_i (1 + y_i)
     // with P_i = c0 w_i prod_a r_a^e_ia (ln(P_i / w_i) affine in e_i) and y_i the
@@ -561,11 +723,11 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         for (int a = 0; a < L::D; ++a) {
             const double s = sqrt(1.0 + 3.0 * u[a] * u[a]);
             c[a] = 2.0 - s;
-            r[a] = (2.0 * u[a] + s) / (1.0 - u[a]);
-            ri[a] = 1.0 / r[a];
+            r[a] = (2.0 * u[a] + s) * recip_nr(1.0 - u[a]);
+            ri[a] = (1.0 - u[a]) * recip_nr(2.0 * u[a] + s);
         }
         const double c0 = (L::D == 3) ? rho * c[0] * c[1] * c[2] : rho * c[0] * c[1];
-        const double ic0 = 1.0 / c0;
+        const double ic0 = recip_nr(c0);
         double m0 = 0, m1[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
@@ -612,7 +774,8 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     }
     AlphaResult ar{2.0, 0, ALPHA_SKIP};
     have_feat = false;
-    const double amax = xmin < 0 ? -1.0 / xmin : 1e300;   // f + a f x > 0  <=>  a < -1/x
+    // positivity limit: f_i + a f_i x_i > 0 for all i  <=>  a < -1 / min x
+    const double amax = xmin < -1e-30 ? recip_nr(-xmin) : 1e300;
     if (p.alpha_mode != 3 && maxabs >= p.skip_eps && amax < 1e300) {
         const bool want_feat = (p.alpha_mode == 1 || p.alpha_mode == 2 || p.pairs_X != nullptr);
         double ak[7];
@@ -639,7 +802,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                 s1[1] += L::ey(i) * Dl;
                 s1[2] += L::ez(i) * Dl;
                 const double yi = y[i];
-                sy += Dl * (yi * (1.0 - yi * (0.5 - yi * (1.0 / 3.0 - 0.25 * yi))));
+                sy = fma(Dl, yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
             }
             // A = sum Delta ln(f_eq/w) - sum Delta log1p(x), with
             // sum Delta ln(f_eq/w) = ln c0 s0 + sum_a ln r_a s1_a + sum Delta log1p(y)
@@ -647,7 +810,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             double sl = 0;
 #pragma unroll
             for (int n = kSeriesK - 1; n >= 1; --n) sl += ((n & 1) ? 1.0 : -1.0) * a[n + 1] / n;
-            A = lc0 * s0 + lr[0] * s1[0] + lr[1] * s1[1] + lr[2] * s1[2] + sy - sl;
+            A = fma(lc0, s0, fma(lr[0], s1[0], fma(lr[1], s1[1], fma(lr[2], s1[2], sy - sl))));
             SeriesEval ev;
 #pragma unroll
             for (int k = 2; k <= kSeriesK; ++k)
@@ -707,10 +870,10 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         elbm_feq<L>(rho, us, p.feq_variant, fs);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
-            d[i] = (R)((f[i] - L::w(i)) + ab * (f[i] * x[i]) + (fs[i] - fe[i]));
+            d[i] = (R)(fma(ab, f[i] * x[i], f[i] - L::w(i)) + (fs[i] - fe[i]));
     } else {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) d[i] = (R)((f[i] - L::w(i)) + ab * (f[i] * x[i]));
+        for (int i = 0; i < L::Q; ++i) d[i] = (R)fma(ab, f[i] * x[i], f[i] - L::w(i));
     }
     rho_out = (R)rho;
     vout[0] = (R)(u[0] + 0.5 * p.F[0] * irho);

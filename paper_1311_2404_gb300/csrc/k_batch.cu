@@ -496,7 +496,7 @@ int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* 
         du = stage + nb;
     }
     BCK(b, launch_init(0, b->dtype, dr, du, field_dtype == LBM_FIELD_F32, b->base + D.offA, D.nx,
-                       D.ny, 1, D.nxp, D.sq, 0, 0, b->stream),
+                       D.ny, 1, D.nxp, D.sq, 0, 0, 0, b->stream),
         "init kernel");
     b->launches += 1;
     BCK(b, cudaStreamSynchronize(b->stream), "synchronise");

@@ -51,9 +51,12 @@ cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, int 
 // F = f_eq(rho, u) (polynomial, or the entropic form for ELBM) at every node.
 // rho [nz][ny][nx], u [D][nz][ny][nx] dense, element type FT.
 // ---------------------------------------------------------------------------
+// opp != 0 stores f_eq_i in slot opp(i) (the AA pattern's in-place placement,
+// which the first AA step, a pull/push step, reads).
 template <class L, class S, class FT>
 __global__ void k_init(const FT* __restrict__ rho, const FT* __restrict__ u, void* Aout, int nx,
-                       int ny, int nz, int nxp, long long sq, int entropic, int feq_variant)
+                       int ny, int nz, int nxp, long long sq, int entropic, int feq_variant,
+                       int opp)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -74,7 +77,7 @@ __global__ void k_init(const FT* __restrict__ rho, const FT* __restrict__ u, voi
         elbm_feq<L>(r, uu, feq_variant, dev);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
-            A[(size_t)i * sq + n] = S::encode((R)(dev[i] - L::w(i)), L::w(i));
+            A[(size_t)(opp ? L::opp(i) : i) * sq + n] = S::encode((R)(dev[i] - L::w(i)), L::w(i));
     } else {
         // Eq. equilibrium in deviation form, w (rho - 1 + rho (3 eu + 9/2 eu^2 - 3/2 u^2)),
         // in the storage's compute type (FP64 arithmetic runs at a small
@@ -86,50 +89,50 @@ __global__ void k_init(const FT* __restrict__ rho, const FT* __restrict__ u, voi
         for (int i = 0; i < L::Q; ++i) {
             const R eu = L::ex(i) * u0 + L::ey(i) * u1 + L::ez(i) * u2;
             const R dev = (R)L::w(i) * (dr + rr * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq));
-            A[(size_t)i * sq + n] = S::encode(dev, L::w(i));
+            A[(size_t)(opp ? L::opp(i) : i) * sq + n] = S::encode(dev, L::w(i));
         }
     }
 }
 
 template <class L, class S>
 static cudaError_t init_t(const void* rho, const void* u, int field_f32, void* A, int nx, int ny,
-                          int nz, int nxp, long long sq, int entropic, int feq_variant,
+                          int nz, int nxp, long long sq, int entropic, int feq_variant, int opp,
                           cudaStream_t s)
 {
     dim3 block(128), grid((nxp + 127) / 128, ny, nz);
     if (field_f32)
         k_init<L, S, float><<<grid, block, 0, s>>>((const float*)rho, (const float*)u, A, nx, ny,
-                                                   nz, nxp, sq, entropic, feq_variant);
+                                                   nz, nxp, sq, entropic, feq_variant, opp);
     else
         k_init<L, S, double><<<grid, block, 0, s>>>((const double*)rho, (const double*)u, A, nx,
-                                                    ny, nz, nxp, sq, entropic, feq_variant);
+                                                    ny, nz, nxp, sq, entropic, feq_variant, opp);
     return cudaGetLastError();
 }
 
 template <class L>
 static cudaError_t init_l(int store, const void* rho, const void* u, int field_f32, void* A,
                           int nx, int ny, int nz, int nxp, long long sq, int entropic,
-                          int feq_variant, cudaStream_t s)
+                          int feq_variant, int opp, cudaStream_t s)
 {
     switch (store) {
-    case 0: return init_t<L, StoreF64>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
-    case 1: return init_t<L, StoreF32>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
-    case 2: return init_t<L, StoreF32S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
-    case 3: return init_t<L, StoreF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
-    case 4: return init_t<L, StoreBF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, s);
+    case 0: return init_t<L, StoreF64>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, opp, s);
+    case 1: return init_t<L, StoreF32>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, opp, s);
+    case 2: return init_t<L, StoreF32S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, opp, s);
+    case 3: return init_t<L, StoreF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, opp, s);
+    case 4: return init_t<L, StoreBF16S>(rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant, opp, s);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
-                        int feq_variant, cudaStream_t s)
+                        int feq_variant, int opposite_slots, cudaStream_t s)
 {
     if (lattice == 0)
         return init_l<D2Q9>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
-                            feq_variant, s);
+                            feq_variant, opposite_slots, s);
     return init_l<D3Q19>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant,
-                         s);
+                         opposite_slots, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,6 +245,98 @@ cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint8_t
         k_reduce_partial<float><<<kReduceBlocks, 256, 0, s>>>(
             (const float*)rho, (const float*)u, flags, D, nx, ny, nz, nxp, sq, partials);
     k_reduce_final<<<1, 256, 0, s>>>(partials, kReduceBlocks, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Kinetic energy and enstrophy (Sec. 5.2 diagnostics): per-row partial sums
+// of |v|^2 and |curl v|^2 (second-order central differences, periodic wrap),
+// then one CTA combines the partials in a fixed tree and normalises by 2N.
+// ---------------------------------------------------------------------------
+template <class RT>
+__global__ void __launch_bounds__(256) k_diag_partial(const RT* __restrict__ u, int D, int nx,
+                                                     int ny, int nz, int nxp, long long sq,
+                                                     double* __restrict__ part)
+{
+    __shared__ double sh[256][2];
+    double e = 0, om = 0;
+    const long long rows = (long long)ny * nz;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+        const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+        const long long c = r * nxp;
+        const long long cyp = ((long long)z * ny + yp) * nxp, cym = ((long long)z * ny + ym) * nxp;
+        const long long czp = ((long long)zp * ny + y) * nxp, czm = ((long long)zm * ny + y) * nxp;
+        const RT* ux = u;
+        const RT* uy = u + sq;
+        const RT* uz = u + 2 * sq;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+            const double vx = ux[c + x], vy = uy[c + x];
+            const double vz = D == 3 ? (double)uz[c + x] : 0.0;
+            e += vx * vx + vy * vy + vz * vz;
+            const double dxvy = 0.5 * ((double)uy[c + xp] - (double)uy[c + xm]);
+            const double dyvx = 0.5 * ((double)ux[cyp + x] - (double)ux[cym + x]);
+            const double wz = dxvy - dyvx;
+            double w2 = wz * wz;
+            if (D == 3) {
+                const double dyvz = 0.5 * ((double)uz[cyp + x] - (double)uz[cym + x]);
+                const double dzvy = 0.5 * ((double)uy[czp + x] - (double)uy[czm + x]);
+                const double dzvx = 0.5 * ((double)ux[czp + x] - (double)ux[czm + x]);
+                const double dxvz = 0.5 * ((double)uz[c + xp] - (double)uz[c + xm]);
+                const double wx = dyvz - dzvy, wy = dzvx - dxvz;
+                w2 += wx * wx + wy * wy;
+            }
+            om += w2;
+        }
+    }
+    sh[threadIdx.x][0] = e;
+    sh[threadIdx.x][1] = om;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[threadIdx.x][0] += sh[threadIdx.x + s][0];
+            sh[threadIdx.x][1] += sh[threadIdx.x + s][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) part[blockIdx.x * 2 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_diag_final(const double* __restrict__ part, int nblocks,
+                                                   double inv2n, double* __restrict__ out)
+{
+    __shared__ double sh[256][2];
+    double acc[2] = {0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        acc[0] += part[b * 2];
+        acc[1] += part[b * 2 + 1];
+    }
+    sh[threadIdx.x][0] = acc[0];
+    sh[threadIdx.x][1] = acc[1];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[threadIdx.x][0] += sh[threadIdx.x + s][0];
+            sh[threadIdx.x][1] += sh[threadIdx.x + s][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) out[threadIdx.x] = sh[0][threadIdx.x] * inv2n;
+}
+
+cudaError_t launch_diagnostics(int f64, const void* u, int D, int nx, int ny, int nz, int nxp,
+                               long long sq, double* partials, double* out, cudaStream_t s)
+{
+    if (f64)
+        k_diag_partial<double><<<kReduceBlocks, 256, 0, s>>>((const double*)u, D, nx, ny, nz, nxp,
+                                                             sq, partials);
+    else
+        k_diag_partial<float><<<kReduceBlocks, 256, 0, s>>>((const float*)u, D, nx, ny, nz, nxp,
+                                                            sq, partials);
+    k_diag_final<<<1, 256, 0, s>>>(partials, kReduceBlocks,
+                                   0.5 / ((double)nx * (double)ny * (double)nz), out);
     return cudaGetLastError();
 }
 

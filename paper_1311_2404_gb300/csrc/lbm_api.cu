@@ -47,7 +47,9 @@ struct lbm_ctx {
     double s[19];
     int alpha_mode = LBM_ALPHA_NEWTON, max_iter = 20, guard_steps = 2, feq_variant = 0;
     double tol = 1e-12, skip_eps = 1e-3, guard_tol = 1e-6;
+    double smag_cs = 0.1;   // Smagorinsky constant C_S
     bool mlp_loaded = false, alpha_out = false, use_graph = false, round_nearest = false;
+    bool aa = false;        // AA access pattern (one distribution array)
     long long t = 0, launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -124,7 +126,8 @@ static void layout(lbm_ctx* h)
     size_t o = 0;
     const size_t dist = (size_t)h->Q * h->sq * h->esize;
     h->off_A = o; o = align256(o + dist);
-    h->off_B = o; o = align256(o + dist);
+    h->off_B = o;
+    if (!h->aa) o = align256(o + dist);   // AA: a single array
     h->off_flags = o; o = align256(o + (size_t)h->sq);
     h->off_rho = o; o = align256(o + (size_t)h->sq * h->rsize);
     h->off_u = o; o = align256(o + (size_t)h->D * h->sq * h->rsize);
@@ -193,7 +196,8 @@ int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int d
         return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lattice);
     if (lattice == LBM_D2Q9 && nz != 1)
         return fail(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1 (got %d)", nz);
-    if (model != LBM_BGK && model != LBM_MRT && model != LBM_ELBM)
+    if (model != LBM_BGK && model != LBM_MRT && model != LBM_ELBM && model != LBM_REG &&
+        model != LBM_SMAG)
         return fail(nullptr, LBM_EINVAL, "unknown model %d", model);
     if (model == LBM_MRT && lattice != LBM_D3Q19)
         return fail(nullptr, LBM_EINVAL, "MRT is implemented for D3Q19 only");
@@ -304,6 +308,16 @@ int lbm_set_mrt_rates(lbm_handle h, const double* s, int q)
     return LBM_OK;
 }
 
+int lbm_set_smagorinsky(lbm_handle h, double cs)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_SMAG) return fail(h, LBM_EINVAL, "not a Smagorinsky handle");
+    if (!std::isfinite(cs) || cs < 0) return fail(h, LBM_EINVAL, "C_S must be finite and >= 0");
+    h->smag_cs = cs;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
 int lbm_set_elbm(lbm_handle h, int alpha_mode, double tol, int max_iter, double skip_eps)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
@@ -365,6 +379,18 @@ int lbm_set_alpha_output(lbm_handle h, int on)
     return LBM_OK;
 }
 
+int lbm_set_access_pattern(lbm_handle h, int pattern)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (pattern != LBM_PATTERN_AB && pattern != LBM_PATTERN_AA)
+        return fail(h, LBM_EINVAL, "unknown access pattern %d", pattern);
+    if (h->base) return fail(h, LBM_ESTATE, "choose the access pattern before memory is in use");
+    h->aa = (pattern == LBM_PATTERN_AA);
+    layout(h);
+    drop_graphs(h);
+    return LBM_OK;
+}
+
 int lbm_set_rounding(lbm_handle h, int mode)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
@@ -409,7 +435,7 @@ int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field
     }
     CK(h, launch_init(h->lattice, h->dtype, drho, du, field_dtype == LBM_FIELD_F32,
                       h->base + h->off_A, h->nx, h->ny, h->nz, h->nxp, h->sq,
-                      h->model == LBM_ELBM, h->feq_variant, h->stream),
+                      h->model == LBM_ELBM, h->feq_variant, h->aa ? 1 : 0, h->stream),
        "init kernel");
     h->launches += 1;
     CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
@@ -446,6 +472,10 @@ static StepParams make_params(lbm_ctx* h)
         p.mrt_cf_f[k] = (float)p.mrt_cf[k];
     }
     p.omega_f = (float)p.omega;
+    p.tau = h->tau;
+    p.smag_cs2 = h->smag_cs * h->smag_cs;
+    p.tau_f = (float)p.tau;
+    p.smag_cs2_f = (float)p.smag_cs2;
     for (int a = 0; a < 3; ++a) p.F_f[a] = (float)p.F[a];
     p.alpha_mode = h->alpha_mode; p.max_iter = h->max_iter;
     p.guard_steps = h->guard_steps; p.feq_variant = h->feq_variant;
@@ -455,15 +485,28 @@ static StepParams make_params(lbm_ctx* h)
     return p;
 }
 
+// One step from buffer `from` (AB) or, for the AA pattern, of parity `from`
+// (0: pull/push step at even t, 1: in-place step at odd t).
 static cudaError_t launch_one(lbm_ctx* h, StepParams& p, int from, bool out)
 {
-    p.A = h->base + (from == 0 ? h->off_A : h->off_B);
-    p.B = h->base + (from == 0 ? h->off_B : h->off_A);
+    if (h->aa) {
+        p.A = h->base + h->off_A;
+        p.B = h->base + h->off_A;
+        p.aa_pushpull = (from == 0) ? 1 : 0;
+    } else {
+        p.A = h->base + (from == 0 ? h->off_A : h->off_B);
+        p.B = h->base + (from == 0 ? h->off_B : h->off_A);
+        p.aa_pushpull = 0;
+    }
     p.out = out ? 1 : 0;
     const bool mask = h->has_mask;
-    if (h->model == LBM_BGK) return launch_step_bgk(h->lattice, h->dtype, p, mask, h->stream);
-    if (h->model == LBM_MRT) return launch_step_mrt(h->lattice, h->dtype, p, mask, h->stream);
-    return launch_step_elbm(h->lattice, h->dtype, p, mask, h->stream);
+    const bool aa = h->aa;
+    if (h->model == LBM_BGK) return launch_step_bgk(h->lattice, h->dtype, p, mask, aa, h->stream);
+    if (h->model == LBM_MRT) return launch_step_mrt(h->lattice, h->dtype, p, mask, aa, h->stream);
+    if (h->model == LBM_REG) return launch_step_reg(h->lattice, h->dtype, p, mask, aa, h->stream);
+    if (h->model == LBM_SMAG) return launch_step_smag(h->lattice, h->dtype, p, mask, aa, h->stream);
+    if (h->lattice == LBM_D2Q9) return launch_step_elbm2(h->dtype, p, mask, aa, h->stream);
+    return launch_step_elbm3(h->dtype, p, mask, aa, h->stream);
 }
 
 static int check_step_ready(lbm_ctx* h)
@@ -588,6 +631,26 @@ int lbm_reduce(lbm_handle h, double* out)
     return r;
 }
 
+int lbm_kinetic_energy_enstrophy(lbm_handle h, double* out)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (!h->have_out) return fail(h, LBM_ESTATE, "no step has produced output yet");
+    if (h->has_mask) return fail(h, LBM_ESTATE, "E/Omega diagnostics need a fully periodic domain");
+    double* dres = at<double>(h, h->off_misc + MISC_RED);
+    CK(h, launch_diagnostics(h->rsize == 8, h->base + h->off_u, h->D, h->nx, h->ny, h->nz,
+                             h->nxp, h->sq, at<double>(h, h->off_part), dres, h->stream),
+       "diagnostics kernels");
+    h->launches += 2;
+    double tmp[2];
+    CK(h, cudaMemcpyAsync(tmp, dres, sizeof tmp, cudaMemcpyDeviceToHost, h->stream),
+       "copy diagnostics");
+    int r = sync_status(h);
+    out[0] = tmp[0];
+    out[1] = tmp[1];
+    return r;
+}
+
 int lbm_get_elbm_stats(lbm_handle h, double* out)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
@@ -613,7 +676,7 @@ int lbm_get_state(lbm_handle h, void* dst, long long* t)
     if (!dst) return fail(h, LBM_EINVAL, "dst is NULL");
     if (!h->inited) return fail(h, LBM_ESTATE, "no state yet");
     const size_t nb = lbm_state_bytes(h);
-    CK(h, cudaMemcpyAsync(dst, h->base + (h->cur == 0 ? h->off_A : h->off_B), nb,
+    CK(h, cudaMemcpyAsync(dst, h->base + ((h->cur == 0 || h->aa) ? h->off_A : h->off_B), nb,
                           cudaMemcpyDefault, h->stream),
        "copy state");
     CK(h, cudaStreamSynchronize(h->stream), "synchronise");
@@ -631,7 +694,9 @@ int lbm_set_state(lbm_handle h, const void* src, long long t)
     CK(h, cudaMemcpyAsync(h->base + h->off_A, src, nb, cudaMemcpyDefault, h->stream),
        "copy state");
     CK(h, cudaStreamSynchronize(h->stream), "synchronise");
-    h->cur = 0;
+    // AB: the state now sits in A.  AA: one array, whose placement is fixed
+    // by the parity of t (the step after an even t is a pull/push step).
+    h->cur = h->aa ? (int)(t & 1) : 0;
     h->t = t;
     h->inited = true;
     h->have_out = false;

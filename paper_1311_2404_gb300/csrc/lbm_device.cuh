@@ -74,11 +74,14 @@ struct D3Q19 {
 // direction) and then truncating rounds up with probability equal to the
 // dropped fraction, like stochastic rounding: the errors lose their bias
 // (6e-4 on the same vortex).  The offset needs no counter, so CUDA-graph
-// replay and the batched kernel see identical results.  FP16 values below the
-// normal range (|d| < 2^-14, absolute error < 3e-8) are rounded to nearest.
+// replay and the batched kernel see identical results.  FP16 values below its
+// normal range (|d| < 2^-14) are dithered on the fixed subnormal grid 2^-24
+// instead (a stochastic floor of |d| 2^24); a flow started from rest keeps
+// most deviations there for many steps, and truncating them would bias every
+// store toward zero.  Inf and NaN are narrowed unchanged.
 __device__ __forceinline__ unsigned dither_hash(unsigned bits, unsigned salt)
 {
-    return (bits ^ salt) * 0x9E3779B1u;
+    return bits * 0x9E3779B1u + salt;
 }
 constexpr unsigned kSaltNode = 0x85EBCA77u, kSaltDir = 0xC2B2AE3Du;
 
@@ -118,10 +121,16 @@ struct StoreF16S {
     __device__ static T encode(R d, double) { return __float2half_rn(d); }
     __device__ static T encode_dither(R d, unsigned salt)
     {
-        unsigned b = __float_as_uint(d);
-        if ((b & 0x7fffffffu) < 0x38800000u) return __float2half_rn(d);   // below 2^-14
-        b = (b + (dither_hash(b, salt) >> 19)) & ~0x1fffu;                // 13 dropped bits
-        return __float2half_rz(__uint_as_float(b));                        // exact
+        const unsigned b = __float_as_uint(d), a = b & 0x7fffffffu;
+        const unsigned h = dither_hash(b, salt);
+        if (a >= 0x7f800000u) return __float2half_rn(d);                  // Inf, NaN
+        if (a >= 0x38800000u)                                              // normal range
+            return __float2half_rz(__uint_as_float((b + (h >> 19)) & ~0x1fffu));  // 13 bits
+        // subnormal: k = floor(|d| 2^24 + r), r uniform in [0, 1); k <= 1024
+        // is the half's magnitude bit pattern (1024 = 2^-14, the smallest normal)
+        const float r = __uint_as_float(0x3f800000u | (h >> 9)) - 1.0f;
+        const unsigned k = __float2uint_rz(fmaf(__uint_as_float(a), 16777216.0f, r));
+        return __ushort_as_half((unsigned short)(k | ((b >> 16) & 0x8000u)));
     }
 };
 struct StoreBF16S {
@@ -133,16 +142,17 @@ struct StoreBF16S {
     __device__ static T encode(R d, double) { return __float2bfloat16_rn(d); }
     __device__ static T encode_dither(R d, unsigned salt)
     {
-        unsigned b = __float_as_uint(d);
-        b = (b + (dither_hash(b, salt) >> 16)) & 0xffff0000u;             // 16 dropped bits
-        return __float2bfloat16_rz(__uint_as_float(b));                    // exact
+        const unsigned b = __float_as_uint(d);
+        if ((b & 0x7fffffffu) >= 0x7f800000u) return __float2bfloat16_rn(d);   // Inf, NaN
+        return __float2bfloat16_rz(
+            __uint_as_float((b + (dither_hash(b, salt) >> 16)) & 0xffff0000u));  // 16 bits, exact
     }
 };
 
 // ---------------------------------------------------------------------------
 // Kernel parameters (passed by value).
 // ---------------------------------------------------------------------------
-enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2 };
+enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2, MODEL_REG = 3, MODEL_SMAG = 4 };
 enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2 };
 enum { STATUS_NAN = 1u, STATUS_NOCONV = 2u, STATUS_TIMEOUT = 4u };
 // ELBM per-node outcome, shared meaning with the counters of the ABI
@@ -167,6 +177,7 @@ struct StepParams {
     int out;                   // write rho/u (and alpha) this step
     int has_force;
     int round_nearest;         // half-width stores: 1 round to nearest, 0 dither
+    int aa_pushpull;           // AA pattern: 1 = pull/push step (even t), 0 = in-place step
     double omega;              // 1/tau
     double F[3];               // body force
     double mrt_c[19];          // s_k / |M_k|^2
@@ -175,6 +186,8 @@ struct StepParams {
     // double -> float conversion runs on the GPU's FP64 pipe)
     float omega_f;
     float F_f[3];
+    double tau, smag_cs2;      // tau0 and C_S^2 (Smagorinsky)
+    float tau_f, smag_cs2_f;
     float mrt_c_f[19];
     float mrt_cf_f[19];
     // ELBM

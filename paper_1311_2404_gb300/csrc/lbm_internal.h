@@ -10,15 +10,24 @@ namespace lbm {
 
 constexpr int kReduceBlocks = 1024;   // FP64 partial sums: kReduceBlocks x 5 doubles
 
-cudaError_t launch_step_bgk(int lattice, int store, const StepParams& p, bool mask, cudaStream_t s);
-cudaError_t launch_step_mrt(int lattice, int store, const StepParams& p, bool mask, cudaStream_t s);
-cudaError_t launch_step_elbm(int lattice, int store, const StepParams& p, bool mask, cudaStream_t s);
+cudaError_t launch_step_bgk(int lattice, int store, const StepParams& p, bool mask, bool aa,
+                            cudaStream_t s);
+cudaError_t launch_step_mrt(int lattice, int store, const StepParams& p, bool mask, bool aa,
+                            cudaStream_t s);
+cudaError_t launch_step_reg(int lattice, int store, const StepParams& p, bool mask, bool aa,
+                            cudaStream_t s);
+cudaError_t launch_step_smag(int lattice, int store, const StepParams& p, bool mask, bool aa,
+                             cudaStream_t s);
+cudaError_t launch_diagnostics(int f64, const void* u, int D, int nx, int ny, int nz, int nxp,
+                               long long sq, double* partials, double* out, cudaStream_t s);
+cudaError_t launch_step_elbm2(int store, const StepParams& p, bool mask, bool aa, cudaStream_t s);
+cudaError_t launch_step_elbm3(int store, const StepParams& p, bool mask, bool aa, cudaStream_t s);
 
 cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, int nx, int ny,
                          int nz, int nxp, cudaStream_t s);
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
-                        int feq_variant, cudaStream_t s);
+                        int feq_variant, int opposite_slots, cudaStream_t s);
 cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, int nfields, int nx,
                         int ny, int nz, int nxp, long long sq, cudaStream_t s);
 cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint8_t* flags, int D,

@@ -11,6 +11,16 @@
 // e_x = +-1 reads are shifted by one element and touch one extra 32-byte
 // sector per warp row, which the L2 serves (DRAM moves each byte once).
 // On output steps the same pass writes rho and v (Eq. edm_momentum).
+//
+// AA pattern (one array, Sec. 3.3): the post-collision values alternate
+// between two placements.  A pull/push step (even t) reads f_i(x) from slot
+// opp(i) of node x - e_i and writes f*_i(x) to slot i of node x + e_i; an
+// in-place step (odd t) reads slot i of node x and writes f*_i(x) to slot
+// opp(i) of node x.  Each location is read and then written by the same
+// thread, so the update is race-free.  Half-way bounce-back: on a pull/push
+// step the bounced value is node x's own slot i (its previous in-place
+// write), on an in-place step it is slot opp(i) of the solid node x - e_i
+// (where node x's own push landed).
 #pragma once
 
 #include "collide.cuh"
@@ -19,7 +29,7 @@ namespace lbm {
 
 constexpr int kStepThreads = 128;
 
-template <class L, class S, int MODEL, bool MASK>
+template <class L, class S, int MODEL, bool MASK, bool AA>
 __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParams p)
 {
     using R = typename S::R;
@@ -53,8 +63,8 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
     }
     int evals = 0, astat = -1;
     if (active) {
-        const T* __restrict__ A = static_cast<const T*>(p.A);
-        T* __restrict__ B = static_cast<T*>(p.B);
+        const T* A = static_cast<const T*>(p.A);
+        T* B = static_cast<T*>(p.B);
         // neighbour coordinates (periodic)
         const int cx[3] = {x == 0 ? p.nx - 1 : x - 1, x, x == p.nx - 1 ? 0 : x + 1};
         const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nxp, y * p.nxp,
@@ -62,18 +72,30 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
         const int zm = (L::D == 3) ? (z == 0 ? p.nz - 1 : z - 1) : z;
         const int zp = (L::D == 3) ? (z == p.nz - 1 ? 0 : z + 1) : z;
         const int rz[3] = {zm * plane, z * plane, zp * plane};
+        const bool pushpull = AA && p.aa_pushpull;
         R d[L::Q];
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-            d[i] = S::load(A + (size_t)i * p.sq + src, L::w(i));
+            if (!AA)
+                d[i] = S::load(A + (size_t)i * p.sq + src, L::w(i));
+            else if (pushpull)
+                d[i] = S::load(A + (size_t)L::opp(i) * p.sq + src, L::w(i));
+            else
+                d[i] = S::load(A + (size_t)i * p.sq + n, L::w(i));
         }
         if (MASK && (fl & FLAG_NEAR_WALL)) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-                if (p.flags[src] & FLAG_SOLID)
-                    d[i] = S::load(A + (size_t)L::opp(i) * p.sq + n, L::w(L::opp(i)));
+                if (p.flags[src] & FLAG_SOLID) {
+                    if (!AA)
+                        d[i] = S::load(A + (size_t)L::opp(i) * p.sq + n, L::w(i));
+                    else if (pushpull)
+                        d[i] = S::load(A + (size_t)i * p.sq + n, L::w(i));
+                    else
+                        d[i] = S::load(A + (size_t)L::opp(i) * p.sq + src, L::w(i));
+                }
             }
         }
         R rho, v[3];
@@ -86,19 +108,33 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
                               p.has_force != 0, rho, v);
         } else if (MODEL == MODEL_MRT) {
             if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+        } else if (MODEL == MODEL_REG || MODEL == MODEL_SMAG) {
+            les_collide<L, R, MODEL == MODEL_SMAG>(
+                d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
+                sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
+                sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho, v);
         } else {
             ar = elbm_collide<L, R>(d, p, smlp, rho, v, feat, have_feat);
             evals = ar.evals;
             astat = ar.status;
         }
-        if (S::kHalf && !p.round_nearest) {
-            const unsigned salt = (unsigned)n * kSaltNode;
+        // destination of population i: own node, slot i (AB); node x + e_i,
+        // slot i (AA pull/push); own node, slot opp(i) (AA in place)
+        const bool dith = S::kHalf && !p.round_nearest;
+        const unsigned salt = (unsigned)n * kSaltNode;
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i)
-                B[(size_t)i * p.sq + n] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
-        } else {
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) S::store(B + (size_t)i * p.sq + n, d[i], L::w(i));
+        for (int i = 0; i < L::Q; ++i) {
+            size_t dst;
+            if (!AA)
+                dst = (size_t)i * p.sq + n;
+            else if (pushpull)
+                dst = (size_t)i * p.sq + (rz[1 + L::ez(i)] + ry[1 + L::ey(i)] + cx[1 + L::ex(i)]);
+            else
+                dst = (size_t)L::opp(i) * p.sq + n;
+            if (dith)
+                B[dst] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
+            else
+                S::store(B + dst, d[i], L::w(i));
         }
         if (p.out) {
             static_cast<R*>(p.rho)[n] = rho;
@@ -156,39 +192,50 @@ inline dim3 step_block(int nxp)
 }
 
 template <class L, class S, int MODEL>
-cudaError_t launch_step_t(const StepParams& p, bool mask, cudaStream_t s)
+cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t s)
 {
     const dim3 block = step_block(p.nxp);
     const dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y, p.nz);
-    if (mask)
-        k_stream_collide<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
-    else
-        k_stream_collide<L, S, MODEL, false><<<grid, block, 0, s>>>(p);
+    if (aa) {
+        if (mask)
+            k_stream_collide<L, S, MODEL, true, true><<<grid, block, 0, s>>>(p);
+        else
+            k_stream_collide<L, S, MODEL, false, true><<<grid, block, 0, s>>>(p);
+    } else {
+        if (mask)
+            k_stream_collide<L, S, MODEL, true, false><<<grid, block, 0, s>>>(p);
+        else
+            k_stream_collide<L, S, MODEL, false, false><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
-template <int MODEL>
-cudaError_t launch_step_model(int lattice, int store, const StepParams& p, bool mask,
+// lattice: 0 D2Q9, 1 D3Q19; LAT restricts a translation unit to one lattice
+// (-1: both).
+template <int MODEL, int LAT = -1>
+cudaError_t launch_step_model(int lattice, int store, const StepParams& p, bool mask, bool aa,
                               cudaStream_t s)
 {
     if (lattice == 0) {
-        if constexpr (MODEL != MODEL_MRT) {
+        if constexpr (MODEL != MODEL_MRT && LAT != 1) {
             switch (store) {
-            case 0: return launch_step_t<D2Q9, StoreF64, MODEL>(p, mask, s);
-            case 1: return launch_step_t<D2Q9, StoreF32, MODEL>(p, mask, s);
-            case 2: return launch_step_t<D2Q9, StoreF32S, MODEL>(p, mask, s);
-            case 3: return launch_step_t<D2Q9, StoreF16S, MODEL>(p, mask, s);
-            case 4: return launch_step_t<D2Q9, StoreBF16S, MODEL>(p, mask, s);
+            case 0: return launch_step_t<D2Q9, StoreF64, MODEL>(p, mask, aa, s);
+            case 1: return launch_step_t<D2Q9, StoreF32, MODEL>(p, mask, aa, s);
+            case 2: return launch_step_t<D2Q9, StoreF32S, MODEL>(p, mask, aa, s);
+            case 3: return launch_step_t<D2Q9, StoreF16S, MODEL>(p, mask, aa, s);
+            case 4: return launch_step_t<D2Q9, StoreBF16S, MODEL>(p, mask, aa, s);
             }
         }
         return cudaErrorInvalidValue;
     }
-    switch (store) {
-    case 0: return launch_step_t<D3Q19, StoreF64, MODEL>(p, mask, s);
-    case 1: return launch_step_t<D3Q19, StoreF32, MODEL>(p, mask, s);
-    case 2: return launch_step_t<D3Q19, StoreF32S, MODEL>(p, mask, s);
-    case 3: return launch_step_t<D3Q19, StoreF16S, MODEL>(p, mask, s);
-    case 4: return launch_step_t<D3Q19, StoreBF16S, MODEL>(p, mask, s);
+    if constexpr (LAT != 0) {
+        switch (store) {
+        case 0: return launch_step_t<D3Q19, StoreF64, MODEL>(p, mask, aa, s);
+        case 1: return launch_step_t<D3Q19, StoreF32, MODEL>(p, mask, aa, s);
+        case 2: return launch_step_t<D3Q19, StoreF32S, MODEL>(p, mask, aa, s);
+        case 3: return launch_step_t<D3Q19, StoreF16S, MODEL>(p, mask, aa, s);
+        case 4: return launch_step_t<D3Q19, StoreBF16S, MODEL>(p, mask, aa, s);
+        }
     }
     return cudaErrorInvalidValue;
 }

@@ -31,11 +31,12 @@ _L = ctypes.CDLL(LIB_PATH)
 # ---- constants (mirror include/lbm.h) -------------------------------------
 LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ENOCONV = range(8)
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_BGK, LBM_MRT, LBM_ELBM = 0, 1, 2
+LBM_BGK, LBM_MRT, LBM_ELBM, LBM_REG, LBM_SMAG = 0, 1, 2, 3, 4
 LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S = range(5)
 LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
 LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIXED2 = range(4)
 LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
+LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
 MLP_NPARAM = 1394
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ESTATE", 3: "LBM_ENOMEM",
@@ -60,9 +61,11 @@ _PROTOS = {
     "lbm_required_bytes": (_sz, [_vp]),
     "lbm_bind_memory": (_i, [_vp, _vp, _sz]),
     "lbm_set_stream": (_i, [_vp, _vp]),
+    "lbm_set_access_pattern": (_i, [_vp, _i]),
     "lbm_set_geometry": (_i, [_vp, _vp]),
     "lbm_set_force": (_i, [_vp, _d, _d, _d]),
     "lbm_set_mrt_rates": (_i, [_vp, _vp, _i]),
+    "lbm_set_smagorinsky": (_i, [_vp, _d]),
     "lbm_set_elbm": (_i, [_vp, _i, _d, _i, _d]),
     "lbm_set_elbm_guard": (_i, [_vp, _i, _d]),
     "lbm_set_elbm_feq": (_i, [_vp, _i]),
@@ -76,6 +79,7 @@ _PROTOS = {
     "lbm_get_macro": (_i, [_vp, _vp, _vp, _i]),
     "lbm_get_alpha": (_i, [_vp, _vp]),
     "lbm_reduce": (_i, [_vp, _vp]),
+    "lbm_kinetic_energy_enstrophy": (_i, [_vp, _vp]),
     "lbm_get_elbm_stats": (_i, [_vp, _vp]),
     "lbm_state_bytes": (_sz, [_vp]),
     "lbm_get_state": (_i, [_vp, _vp, ctypes.POINTER(_ll)]),
@@ -179,6 +183,10 @@ def lbm_bind_memory(h, dev, nbytes):
     _check(_L.lbm_bind_memory(h, _ptr(dev), nbytes), h)
 
 
+def lbm_set_access_pattern(h, pattern):
+    _check(_L.lbm_set_access_pattern(h, int(pattern)), h)
+
+
 def lbm_set_stream(h, stream):
     _check(_L.lbm_set_stream(h, stream), h)
 
@@ -194,6 +202,10 @@ def lbm_set_force(h, fx, fy, fz=0.0):
 def lbm_set_mrt_rates(h, s):
     s = np.ascontiguousarray(s, dtype=np.float64)
     _check(_L.lbm_set_mrt_rates(h, _ptr(s), int(s.size)), h)
+
+
+def lbm_set_smagorinsky(h, cs):
+    _check(_L.lbm_set_smagorinsky(h, float(cs)), h)
 
 
 def lbm_set_elbm(h, alpha_mode, tol=1e-12, max_iter=20, skip_eps=1e-3):
@@ -256,6 +268,13 @@ def lbm_reduce(h, D):
     out = np.zeros(D + 2)
     _check(_L.lbm_reduce(h, _ptr(out)), h)
     return out
+
+
+def lbm_kinetic_energy_enstrophy(h):
+    """(E, Omega) of the last output step, FP64, computed on the GPU."""
+    out = np.zeros(2)
+    _check(_L.lbm_kinetic_energy_enstrophy(h, _ptr(out)), h)
+    return float(out[0]), float(out[1])
 
 
 def lbm_get_elbm_stats(h):
@@ -413,12 +432,15 @@ class Simulation:
     >>> sim.init(rho, u); sim.step(100); rho, u = sim.macro()
     """
 
-    def __init__(self, nx, ny, nz, lattice, model, tau, dtype, stream=None, torch_memory=True):
+    def __init__(self, nx, ny, nz, lattice, model, tau, dtype, stream=None, torch_memory=True,
+                 pattern=LBM_PATTERN_AB):
         import torch
         self.nx, self.ny, self.nz = nx, ny, nz
         self.lattice, self.model, self.dtype = lattice, model, dtype
         self.D = 2 if lattice == LBM_D2Q9 else 3
         self.h = lbm_create(nx, ny, nz, lattice, model, tau, dtype)
+        if pattern != LBM_PATTERN_AB:
+            lbm_set_access_pattern(self.h, pattern)
         self._mem = None
         if torch_memory:
             nb = lbm_required_bytes(self.h)
