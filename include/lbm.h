@@ -367,6 +367,69 @@ LBM_API const char* lbm_mlp_last_error(void);
 LBM_API int lbm_mlp_forward(const float* X_dev, int n, const float* params, float* alpha_dev,
                     void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Subdomain decomposition with ghost layers (Sec. 3.6), all subdomains on
+ * this GPU.
+ *
+ * The domain is cut into nsub slabs of whole rows of its slowest axis (z on
+ * D3Q19, y on D2Q9; slab s holds rows [floor(n s / nsub), floor(n (s+1) /
+ * nsub))).  Each slab is stored with one ghost row on each side.  After every
+ * step the populations that cross a slab face, the directions with a
+ * component toward the neighbour (5 of 19 on D3Q19, 3 of 9 on D2Q9, Sec.
+ * 3.6's direction-limited exchange), are collected from the slab's boundary
+ * row into a linear send buffer, moved to the neighbour's receive buffer and
+ * distributed into the neighbour's ghost row (periodic: the last slab's
+ * neighbour is the first).  With overlap on (default) each step updates the
+ * two boundary rows of every slab first and runs the exchange on a second
+ * stream while the bulk rows update.  Results equal the single-domain
+ * handle's bit for bit, for every model and storage type.  AB pattern only.
+ * Arguments as lbm_create; nsub in [1, rows of the decomposed axis].
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_multi_ctx* lbm_multi;
+
+LBM_API int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau,
+                             int dtype, int nsub, lbm_multi* out);
+LBM_API int lbm_multi_destroy(lbm_multi m);
+LBM_API const char* lbm_multi_last_error(lbm_multi m);
+/* Stream of the updates (the exchange runs on an internal stream that
+ * joins it every step). */
+LBM_API int lbm_multi_set_stream(lbm_multi m, void* cuda_stream);
+/* 1: boundary rows first, exchange overlapped with the bulk (default);
+ * 0: whole slabs, then the exchange, on one stream. */
+LBM_API int lbm_multi_set_overlap(lbm_multi m, int on);
+/* Transfer of the face buffers: LBM_TRANSFER_STAGED (default) collects the
+ * outgoing runs into a send buffer, copies it to the receiver's buffer and
+ * distributes from there, as a run with one GPU per slab would;
+ * LBM_TRANSFER_DIRECT stores the runs straight into the neighbour's ghost row
+ * in one kernel (the form of a peer-to-peer store). */
+enum { LBM_TRANSFER_STAGED = 0, LBM_TRANSFER_DIRECT = 1 };
+LBM_API int lbm_multi_set_transfer(lbm_multi m, int mode);
+/* Capture lbm_multi_step(n) as one CUDA graph (both streams) and replay it. */
+LBM_API int lbm_multi_set_graph(lbm_multi m, int on);
+/* As lbm_set_force / lbm_set_rounding / lbm_set_smagorinsky / lbm_set_elbm,
+ * applied to every slab. */
+LBM_API int lbm_multi_set_force(lbm_multi m, double fx, double fy, double fz);
+LBM_API int lbm_multi_set_rounding(lbm_multi m, int mode);
+LBM_API int lbm_multi_set_smagorinsky(lbm_multi m, double cs);
+LBM_API int lbm_multi_set_elbm(lbm_multi m, int alpha_mode, double tol, int max_iter,
+                               double skip_eps);
+/* Whole-domain mask and initial fields, laid out as for lbm_set_geometry and
+ * lbm_init_equilibrium (host or device); each slab takes its rows plus the
+ * neighbouring row on each side. */
+LBM_API int lbm_multi_set_geometry(lbm_multi m, const uint8_t* mask);
+LBM_API int lbm_multi_init_equilibrium(lbm_multi m, const void* rho, const void* u,
+                                       int field_dtype);
+/* n time steps, each followed by the ghost-row exchange.  Asynchronous. */
+LBM_API int lbm_multi_step(lbm_multi m, int n);
+/* Whole-domain rho and v of the last step (as lbm_get_macro).  Synchronises. */
+LBM_API int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype);
+/* Bytes that cross slab faces per step: 2 nsub faces x directions x nodes
+ * per row x storage element size (what a multi-GPU run would send). */
+LBM_API int lbm_multi_halo_bytes(lbm_multi m, long long* per_step);
+/* Kernels this handle has launched (stream-collide, collect, distribute, pack). */
+LBM_API long long lbm_multi_launch_count(lbm_multi m);
+LBM_API int lbm_multi_sync(lbm_multi m);
+
 #ifdef __cplusplus
 }
 #endif

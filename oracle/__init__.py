@@ -56,6 +56,7 @@ class OracleParams(ctypes.Structure):
         ("skip_eps", ctypes.c_double), ("guard_tol", ctypes.c_double),
         ("mlp", ctypes.POINTER(ctypes.c_double)),
         ("smag_cs", ctypes.c_double),
+        ("q", ctypes.c_int),
     ]
 
 
@@ -107,7 +108,12 @@ def _dp(a: np.ndarray):
 
 
 def Q_of(D: int) -> int:
-    return 9 if D == 2 else 19
+    """Velocities of a lattice code: 2 / 9 D2Q9, 3 / 19 D3Q19, 15 D3Q15, 27 D3Q27."""
+    return {2: 9, 9: 9, 3: 19, 19: 19, 15: 15, 27: 27}[D]
+
+
+def dim_of(code: int) -> int:
+    return 2 if code in (2, 9) else 3
 
 
 def lattice(D: int):
@@ -141,9 +147,14 @@ def mrt_matrix():
 def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0),
                 s=None, alpha_mode=NEWTON, max_iter=20, feq_variant=0, tol=1e-12,
                 skip_eps=1e-3, guard_tol=1e-6, guard_steps=2, mlp=None, nthreads=0,
-                smag_cs=0.1):
+                smag_cs=0.1, q=0):
+    """D is the dimension or a lattice code (15, 19, 27 for D3Q15/19/27)."""
+    if D in (9, 15, 19, 27):
+        q = D
+        D = dim_of(D)
     p = OracleParams()
     p.nx, p.ny, p.nz, p.D, p.model = nx, ny, nz, D, model
+    p.q = q
     p.alpha_mode, p.max_iter, p.feq_variant = alpha_mode, max_iter, feq_variant
     p.nthreads, p.guard_steps = nthreads, guard_steps
     p.tau = tau
@@ -209,7 +220,7 @@ def init(p: OracleParams, rho: np.ndarray, u: np.ndarray) -> np.ndarray:
     N = p.nx * p.ny * p.nz
     rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(N)
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(D * N)
-    F = np.zeros((Q_of(D), p.nz, p.ny, p.nx))
+    F = np.zeros((Q_of(p.q or D), p.nz, p.ny, p.nx))
     r = lib().oracle_init(ctypes.byref(p), _dp(rho), _dp(u), _dp(F))
     assert r == 0
     return F
@@ -220,7 +231,7 @@ def run(p: OracleParams, F: np.ndarray, nsteps: int, mask: np.ndarray | None = N
     """Advance F in place by nsteps.  Returns (rho, u, alpha|None, stats)."""
     D = p.D
     N = p.nx * p.ny * p.nz
-    assert F.shape == (Q_of(D), p.nz, p.ny, p.nx) and F.dtype == np.float64
+    assert F.shape == (Q_of(p.q or D), p.nz, p.ny, p.nx) and F.dtype == np.float64
     assert F.flags.c_contiguous
     tmp = np.empty_like(F)
     rho = np.zeros((p.nz, p.ny, p.nx))

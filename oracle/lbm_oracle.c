@@ -46,7 +46,7 @@
 #include <omp.h>
 #endif
 
-#define OQMAX 19
+#define OQMAX 27
 
 /* ------------------------------------------------------------------ */
 /* Lattices: Sec. 2, Fig. lattices and Table bgkweights.               */
@@ -58,16 +58,25 @@ typedef struct {
     int opp[OQMAX];
 } olat;
 
-/* Enumerate e in {-1,0,1}^D with |e|^2 <= 2 (D2Q9: all nine; D3Q19: rest,
- * six links of length 1 and twelve of length sqrt 2).  Weights by link length
- * from Table bgkweights. */
-static int olat_build(olat* L, int D)
+/* Enumerate e in {-1,0,1}^D and keep the links whose squared length the
+ * lattice uses (Sec. 2, Fig. lattices): D2Q9 all nine; D3Q15 lengths 0, 1,
+ * sqrt 3; D3Q19 lengths 0, 1, sqrt 2; D3Q27 all.  Weights by link length from
+ * Table bgkweights (a negative entry marks an unused length). */
+static int olat_build(olat* L, int D, int Q)
 {
-    double w_by_len2[3];
-    if (D == 2) {
+    double w_by_len2[4];
+    if (D == 2 && Q == 9) {
         w_by_len2[0] = 4.0 / 9.0; w_by_len2[1] = 1.0 / 9.0; w_by_len2[2] = 1.0 / 36.0;
-    } else if (D == 3) {
+        w_by_len2[3] = -1.0;
+    } else if (D == 3 && Q == 15) {
+        w_by_len2[0] = 2.0 / 9.0; w_by_len2[1] = 1.0 / 9.0; w_by_len2[2] = -1.0;
+        w_by_len2[3] = 1.0 / 72.0;
+    } else if (D == 3 && Q == 19) {
         w_by_len2[0] = 1.0 / 3.0; w_by_len2[1] = 1.0 / 18.0; w_by_len2[2] = 1.0 / 36.0;
+        w_by_len2[3] = -1.0;
+    } else if (D == 3 && Q == 27) {
+        w_by_len2[0] = 8.0 / 27.0; w_by_len2[1] = 2.0 / 27.0; w_by_len2[2] = 1.0 / 54.0;
+        w_by_len2[3] = 1.0 / 216.0;
     } else {
         return -1;
     }
@@ -78,7 +87,7 @@ static int olat_build(olat* L, int D)
         for (int ey = -1; ey <= 1; ++ey)
             for (int ex = -1; ex <= 1; ++ex) {
                 int n2 = ex * ex + ey * ey + ez * ez;
-                if (n2 > 2) continue;
+                if (w_by_len2[n2] < 0.0) continue;
                 L->e[q][0] = ex; L->e[q][1] = ey; L->e[q][2] = ez;
                 L->w[q] = w_by_len2[n2];
                 ++q;
@@ -92,19 +101,30 @@ static int olat_build(olat* L, int D)
     return q;
 }
 
-static const olat* get_lattice(int D)
+/* Lattice by code: 2 = D2Q9, 3 = D3Q19 (the dimension's default), 15 =
+ * D3Q15, 19 = D3Q19, 27 = D3Q27, 9 = D2Q9. */
+static const olat* get_lattice(int code)
 {
-    static olat L2, L3;
+    static olat L9, L15, L19, L27;
     static int built = 0;
     if (!built) {           /* tables are tiny; building twice is harmless */
-        olat_build(&L2, 2);
-        olat_build(&L3, 3);
+        olat_build(&L9, 2, 9);
+        olat_build(&L15, 3, 15);
+        olat_build(&L19, 3, 19);
+        olat_build(&L27, 3, 27);
         built = 1;
     }
-    if (D == 2) return &L2;
-    if (D == 3) return &L3;
-    return NULL;
+    switch (code) {
+    case 2: case 9: return &L9;
+    case 3: case 19: return &L19;
+    case 15: return &L15;
+    case 27: return &L27;
+    default: return NULL;
+    }
 }
+
+/* the lattice of a parameter block: q selects it, else the dimension's default */
+#define PLAT(p) get_lattice((p)->q ? (p)->q : (p)->D)
 
 static double edot(const olat* L, int i, const double* u)
 {
@@ -271,6 +291,7 @@ typedef struct {
     double guard_tol; /* guarded modes: accept when the last correction <= guard_tol */
     const double* mlp;/* MLP parameters for alpha_mode 2 */
     double smag_cs;   /* Smagorinsky constant C_S (model 4) */
+    int q;            /* velocity set: 0 = D2Q9 / D3Q19 by D, or 9, 15, 19, 27 */
 } oracle_params;
 
 /* Per-node ELBM outcome. */
@@ -502,7 +523,7 @@ static int collide_node(const olat* L, const oracle_params* p, double* f, double
     } else if (p->model == 1) {
         /* MRT, Eq. mrt_collision, with Guo's term taken to moment space:
          * m' = m - S (m - m_eq) + (I - S/2) M Ft,  f' = M^-1 m'. */
-        if (D != 3) return -1;
+        if (L->Q != 19) return -1;
         const omrt* T = get_mrt();
         double Ft[OQMAX], m[19], meq[19], mF[19], mp[19];
         feq_poly(L, rho, v, feq);
@@ -627,7 +648,7 @@ int oracle_feq(int D, int kind, double rho, const double* u, double* feq)
     const olat* L = get_lattice(D);
     if (!L) return -1;
     double uu[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < D; ++a) uu[a] = u[a];
+    for (int a = 0; a < L->D; ++a) uu[a] = u[a];
     if (kind == 0) feq_poly(L, rho, uu, feq);
     else if (kind == 1) feq_entropic_product(L, rho, uu, feq);
     else if (kind == 2) feq_entropic(L, rho, uu, feq);
@@ -650,7 +671,7 @@ int oracle_mrt_matrix(double* M, double* Minv)
 /* One node: f (Q values, post-streaming) -> post-collision f in place. */
 int oracle_collide(const oracle_params* p, double* f, double* rho, double* v, double* info)
 {
-    const olat* L = get_lattice(p->D);
+    const olat* L = PLAT(p);
     if (!L) return -1;
     double inf4[4] = {0, 0, 0, 0};
     int r = collide_node(L, p, f, rho, v, inf4);
@@ -676,7 +697,7 @@ int oracle_elbm_g(int D, const double* f, const double* feq, double alpha, doubl
 /* alpha solve for given f and f_eq; out = {alpha, evals, status, |g|/a2}. */
 int oracle_elbm_alpha(const oracle_params* p, const double* f, const double* feq, double* out)
 {
-    const olat* L = get_lattice(p->D);
+    const olat* L = PLAT(p);
     if (!L) return -1;
     double rho = 0.0;
     for (int i = 0; i < L->Q; ++i) rho += f[i];
@@ -709,7 +730,7 @@ double oracle_mlp_guess(const double* P, const double* feat)
  * LBGK and MRT; ELBM's own for ELBM).  u is [D][z][y][x]. */
 int oracle_init(const oracle_params* p, const double* rho, const double* u, double* F)
 {
-    const olat* L = get_lattice(p->D);
+    const olat* L = PLAT(p);
     if (!L) return -1;
     size_t N = (size_t)p->nx * p->ny * p->nz;
     for (size_t n = 0; n < N; ++n) {
@@ -731,9 +752,9 @@ int oracle_init(const oracle_params* p, const double* rho, const double* u, doub
 int oracle_run(const oracle_params* p, double* F, double* Ftmp, const uint8_t* mask,
                int nsteps, double* rho, double* u, double* alpha, double* stats)
 {
-    const olat* L = get_lattice(p->D);
+    const olat* L = PLAT(p);
     if (!L) return -1;
-    if (p->model == 1 && p->D != 3) return -1;
+    if (p->model == 1 && L->Q != 19) return -1;
     const int nx = p->nx, ny = p->ny, nz = p->nz, Q = L->Q, D = L->D;
     const size_t N = (size_t)nx * ny * nz;
     double st[6] = {0, 0, 0, 0, 0, 0};

@@ -128,11 +128,14 @@ __device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams&
     using L = D2Q9;
     float rho, v[3];
     bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
-    if (S::kHalf && !bp.round_nearest) {
-        const unsigned salt = (unsigned)n * kSaltNode;
+    if constexpr (S::kHalf) {
+        if (!bp.round_nearest) {
+            store_node_sr<L, S>(B, d, (unsigned)n * kSaltNode,
+                                [&](int i) -> size_t { return (size_t)i * D.sq + n; });
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            B[(size_t)i * D.sq + n] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
+            for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));

@@ -16,9 +16,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "collide.cuh"
@@ -460,6 +462,9 @@ static StepParams make_params(lbm_ctx* h)
                                       : nullptr;
     p.nx = h->nx; p.ny = h->ny; p.nz = h->nz; p.nxp = h->nxp;
     p.sq = h->sq;
+    p.row0 = 0;
+    p.nrows = h->D == 3 ? h->nz : h->ny;
+    p.salt_off = 0;
     p.omega = 1.0 / h->tau;
     p.F[0] = h->F[0]; p.F[1] = h->F[1]; p.F[2] = h->F[2];
     p.has_force = (h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0);
@@ -740,6 +745,550 @@ int lbm_elbm_collect_pairs(lbm_handle h, int stride, float* X_dev, double* y_dev
     r = sync_status(h);
     *count = hc < cap ? hc : cap;
     return r;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Subdomain decomposition with ghost layers (Sec. 3.6), all subdomains on
+// this GPU.  The domain is cut into S slabs of whole rows of its slowest axis
+// (z on D3Q19, y on D2Q9); slab s holds rows [lo_s, hi_s) plus one ghost row
+// on each side, as an ordinary handle of nrows + 2 rows whose step kernels
+// are restricted to the interior rows.  After every step the boundary rows'
+// outgoing directions are collected into a linear send buffer, moved to the
+// neighbour's receive buffer (the transfer a multi-GPU run would make) and
+// distributed into the neighbour's ghost row.  With overlap on, the two
+// boundary rows of every slab are updated first, the exchange runs on a
+// second stream while the bulk rows update (Sec. 3.6's bulk/boundary split).
+// The dither salt of each slab is offset to the global node index, so every
+// storage type reproduces the single-domain run bit for bit.
+// ===========================================================================
+struct lbm_multi_ctx {
+    int nx = 0, ny = 0, nz = 0, lattice = 0, D = 0, Q = 0, S = 0, dtype = 0;
+    int axis_n = 0;              // rows of the decomposed axis
+    long long layer = 0;         // padded elements per row (ny * nxp, or nxp on D2Q9)
+    long long layer_dense = 0;   // dense nodes per row (nx * ny, or nx)
+    size_t esize = 0;
+    std::vector<int> lo, hi;
+    std::vector<lbm_ctx*> sub;
+    int ndir = 0;
+    int dir_up[9], dir_dn[9];    // directions with +1 / -1 along the decomposed axis
+    bool overlap = true, use_graph = false, inited = false;
+    bool direct = false;         // one kernel stores into the neighbour's ghost row
+    cudaStream_t stream = nullptr, comm = nullptr;
+    cudaEvent_t ev_bnd = nullptr, ev_halo = nullptr;
+    char* mem = nullptr;         // send, recv buffers, segment tables, scratch
+    size_t face_bytes = 0;       // one face: ndir runs of one row
+    size_t off_send = 0, off_recv = 0, off_tab = 0, off_scr = 0, scr_bytes = 0;
+    int nseg = 0;                // segments per table (2 S ndir)
+    long long t = 0, launches = 0;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+static thread_local std::string g_multi_err;
+
+static int mfail(lbm_multi_ctx* m, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    (m ? m->err : g_multi_err) = buf;
+    return code;
+}
+
+#define MCK(m, expr, what)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return mfail((m), LBM_ECUDA, "%s: %s", (what), cudaGetErrorString(e_));         \
+    } while (0)
+
+// propagate a sub-handle's error message
+static int msub(lbm_multi_ctx* m, lbm_ctx* h, int r)
+{
+    if (r) m->err = h->err;
+    return r;
+}
+
+static void mdrop_graphs(lbm_multi_ctx* m)
+{
+    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second);
+    m->graphs.clear();
+}
+
+static void multi_free(lbm_multi_ctx* m)
+{
+    mdrop_graphs(m);
+    for (auto* h : m->sub) lbm_destroy(h);
+    if (m->mem) cudaFree(m->mem);
+    if (m->ev_bnd) cudaEventDestroy(m->ev_bnd);
+    if (m->ev_halo) cudaEventDestroy(m->ev_halo);
+    if (m->comm) cudaStreamDestroy(m->comm);
+    delete m;
+}
+
+// segment tables, per parity (the buffer, 0: A or 1: B, that holds the new
+// state after the step): collect, distribute, direct
+static HaloSeg* mtable(lbm_multi_ctx* m, int parity, int kind)
+{
+    return reinterpret_cast<HaloSeg*>(m->mem + m->off_tab) + (size_t)(3 * parity + kind) * m->nseg;
+}
+
+static int multi_build_tables(lbm_multi_ctx* m)
+{
+    const int S = m->S;
+    std::vector<HaloSeg> tab((size_t)6 * m->nseg);
+    const long long n16 = m->layer * (long long)m->esize / 16;
+    for (int parity = 0; parity < 2; ++parity) {
+        HaloSeg* pk = &tab[(size_t)(3 * parity) * m->nseg];
+        HaloSeg* up = &tab[(size_t)(3 * parity + 1) * m->nseg];
+        HaloSeg* dr = &tab[(size_t)(3 * parity + 2) * m->nseg];
+        for (int s = 0; s < S; ++s) {
+            lbm_ctx* h = m->sub[s];
+            char* arr = h->base + (parity == 0 ? h->off_A : h->off_B);
+            const int nloc = m->hi[s] - m->lo[s];
+            for (int f = 0; f < 2; ++f) {        // 0: upper face (row nloc), 1: lower face (row 1)
+                const int row = f == 0 ? nloc : 1;
+                const int r = f == 0 ? (s + 1) % S : (s + S - 1) % S;   // receiver
+                lbm_ctx* hr = m->sub[r];
+                char* arr_r = hr->base + (parity == 0 ? hr->off_A : hr->off_B);
+                const int ghost = f == 0 ? 0 : (m->hi[r] - m->lo[r]) + 1;
+                for (int k = 0; k < m->ndir; ++k) {
+                    const int i = f == 0 ? m->dir_up[k] : m->dir_dn[k];
+                    const size_t seg = ((size_t)s * 2 + f) * m->ndir + k;
+                    const size_t boff = seg * (size_t)m->layer * m->esize;
+                    const char* src = arr + ((size_t)i * h->sq + (size_t)row * m->layer) * m->esize;
+                    char* dst = arr_r + ((size_t)i * hr->sq + (size_t)ghost * m->layer) * m->esize;
+                    pk[seg] = HaloSeg{reinterpret_cast<const uint4*>(src),
+                                      reinterpret_cast<uint4*>(m->mem + m->off_send + boff), n16};
+                    up[seg] = HaloSeg{reinterpret_cast<const uint4*>(m->mem + m->off_recv + boff),
+                                      reinterpret_cast<uint4*>(dst), n16};
+                    dr[seg] = HaloSeg{reinterpret_cast<const uint4*>(src),
+                                      reinterpret_cast<uint4*>(dst), n16};
+                }
+            }
+        }
+    }
+    MCK(m, cudaMemcpy(m->mem + m->off_tab, tab.data(), tab.size() * sizeof(HaloSeg),
+                      cudaMemcpyHostToDevice),
+        "upload segment tables");
+    return LBM_OK;
+}
+
+// The exchange after a step whose new state is in buffer `parity`.
+static cudaError_t multi_exchange(lbm_multi_ctx* m, int parity, cudaStream_t s)
+{
+    const long long n16 = m->layer * (long long)m->esize / 16;
+    if (m->direct) return launch_halo_copy(mtable(m, parity, 2), m->nseg, n16, s);
+    cudaError_t e = launch_halo_copy(mtable(m, parity, 0), m->nseg, n16, s);
+    if (e != cudaSuccess) return e;
+    // transfer: face (s, f) goes to its receiver's buffer slot of the same index
+    for (int sd = 0; sd < m->S; ++sd)
+        for (int f = 0; f < 2; ++f) {
+            const size_t off = ((size_t)sd * 2 + f) * m->face_bytes;
+            e = cudaMemcpyAsync(m->mem + m->off_recv + off, m->mem + m->off_send + off,
+                                m->face_bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    return launch_halo_copy(mtable(m, parity, 1), m->nseg, n16, s);
+}
+
+static cudaError_t multi_rows(lbm_multi_ctx* m, int s, int row0, int nrows, bool out, int from)
+{
+    lbm_ctx* h = m->sub[s];
+    StepParams p = make_params(h);
+    p.row0 = row0;
+    p.nrows = nrows;
+    p.salt_off = (int)((long long)(m->lo[s] - 1) * m->layer);
+    return launch_one(h, p, from, out);
+}
+
+// kernels launched per time step (stream-collide launches + collect + distribute)
+static int multi_launches_per_step(const lbm_multi_ctx* m)
+{
+    int nl = m->direct ? 1 : 2;
+    for (int s = 0; s < m->S; ++s) {
+        const int nloc = m->hi[s] - m->lo[s];
+        nl += m->overlap ? 1 + (nloc > 1) + (nloc > 2) : 1;
+    }
+    return nl;
+}
+
+// one time step of every slab; `from` is the buffer holding the current state
+static cudaError_t multi_step_once(lbm_multi_ctx* m, int from, bool out)
+{
+    cudaError_t e;
+    const int to = from ^ 1;
+    if (!m->overlap) {
+        for (int s = 0; s < m->S; ++s)
+            if ((e = multi_rows(m, s, 1, m->hi[s] - m->lo[s], out, from)) != cudaSuccess) return e;
+        return multi_exchange(m, to, m->stream);
+    }
+    for (int s = 0; s < m->S; ++s) {
+        const int nloc = m->hi[s] - m->lo[s];
+        if ((e = multi_rows(m, s, 1, 1, out, from)) != cudaSuccess) return e;
+        if (nloc > 1 && (e = multi_rows(m, s, nloc, 1, out, from)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(m->ev_bnd, m->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(m->comm, m->ev_bnd, 0)) != cudaSuccess) return e;
+    if ((e = multi_exchange(m, to, m->comm)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(m->ev_halo, m->comm)) != cudaSuccess) return e;
+    for (int s = 0; s < m->S; ++s) {
+        const int nloc = m->hi[s] - m->lo[s];
+        if (nloc > 2 && (e = multi_rows(m, s, 2, nloc - 2, out, from)) != cudaSuccess) return e;
+    }
+    return cudaStreamWaitEvent(m->stream, m->ev_halo, 0);
+}
+
+// Gather rows lo-1 .. hi (periodic) of a field with `ncomp` components of
+// `rowbytes` bytes per row and `nrows_g` rows into dst (device).
+static int gather_rows(lbm_multi_ctx* m, const char* src, char* dst, int lo, int hi, int ncomp,
+                       size_t rowbytes)
+{
+    const int n = m->axis_n, nloc = hi - lo;
+    for (int c = 0; c < ncomp; ++c) {
+        const char* sc = src + (size_t)c * n * rowbytes;
+        char* dc = dst + (size_t)c * (nloc + 2) * rowbytes;
+        const int below = (lo - 1 + n) % n, above = hi % n;
+        MCK(m, cudaMemcpyAsync(dc, sc + (size_t)below * rowbytes, rowbytes, cudaMemcpyDefault,
+                               m->stream), "gather row");
+        MCK(m, cudaMemcpyAsync(dc + rowbytes, sc + (size_t)lo * rowbytes, (size_t)nloc * rowbytes,
+                               cudaMemcpyDefault, m->stream), "gather rows");
+        MCK(m, cudaMemcpyAsync(dc + (size_t)(nloc + 1) * rowbytes, sc + (size_t)above * rowbytes,
+                               rowbytes, cudaMemcpyDefault, m->stream), "gather row");
+    }
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
+                     int nsub, lbm_multi* out)
+{
+    if (!out) return mfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int D = lattice == LBM_D2Q9 ? 2 : 3;
+    const int axis_n = D == 3 ? nz : ny;
+    if (nsub < 1 || nsub > 4096 || axis_n < nsub)
+        return mfail(nullptr, LBM_EINVAL,
+                     "need 1 <= subdomains <= rows of the decomposed axis (%d), got %d", axis_n,
+                     nsub);
+    lbm_multi_ctx* m = new lbm_multi_ctx();
+    m->nx = nx; m->ny = ny; m->nz = nz; m->lattice = lattice; m->D = D; m->S = nsub;
+    m->dtype = dtype; m->axis_n = axis_n;
+    for (int s = 0; s < nsub; ++s) {
+        m->lo.push_back((int)((long long)axis_n * s / nsub));
+        m->hi.push_back((int)((long long)axis_n * (s + 1) / nsub));
+    }
+    for (int s = 0; s < nsub; ++s) {
+        const int nloc = m->hi[s] - m->lo[s];
+        lbm_handle h = nullptr;
+        int r = D == 3 ? lbm_create(nx, ny, nloc + 2, lattice, model, tau, dtype, &h)
+                       : lbm_create(nx, nloc + 2, 1, lattice, model, tau, dtype, &h);
+        if (r) {
+            int code = mfail(nullptr, r, "subdomain %d: %s", s, lbm_last_error(nullptr));
+            multi_free(m);
+            return code;
+        }
+        m->sub.push_back(h);
+    }
+    lbm_ctx* h0 = m->sub[0];
+    m->Q = h0->Q;
+    m->esize = h0->esize;
+    m->layer = D == 3 ? (long long)h0->nxp * ny : h0->nxp;
+    m->layer_dense = D == 3 ? (long long)nx * ny : nx;
+    // directions with a +1 / -1 component along the decomposed axis
+    int ndn = 0;
+    for (int i = 0; i < m->Q; ++i) {
+        const int e = D == 3 ? D3Q19::ez(i) : D2Q9::ey(i);
+        if (e == 1) m->dir_up[m->ndir++] = i;
+        if (e == -1) m->dir_dn[ndn++] = i;
+    }
+    m->face_bytes = (size_t)m->ndir * m->layer * m->esize;
+    m->nseg = 2 * nsub * m->ndir;
+    size_t o = 0;
+    m->off_send = o; o = align256(o + m->face_bytes * 2 * nsub);
+    m->off_recv = o; o = align256(o + m->face_bytes * 2 * nsub);
+    m->off_tab = o; o = align256(o + sizeof(HaloSeg) * 6 * (size_t)m->nseg);
+    int maxloc = 0;
+    for (int s = 0; s < nsub; ++s) maxloc = std::max(maxloc, m->hi[s] - m->lo[s]);
+    m->scr_bytes = (size_t)(maxloc + 2) * m->layer_dense * 8 * (1 + D);
+    m->off_scr = o; o = align256(o + m->scr_bytes);
+    cudaError_t e = cudaMalloc(&m->mem, o);
+    if (e != cudaSuccess) {
+        int code = mfail(nullptr, LBM_ENOMEM, "multi buffers (%zu bytes): %s", o,
+                         cudaGetErrorString(e));
+        multi_free(m);
+        return code;
+    }
+    for (auto* h : m->sub) {
+        int r = ensure_memory(h);
+        if (r) {
+            int code = mfail(nullptr, r, "subdomain memory: %s", h->err.c_str());
+            multi_free(m);
+            return code;
+        }
+    }
+    if ((e = cudaStreamCreateWithFlags(&m->comm, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&m->ev_bnd, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&m->ev_halo, cudaEventDisableTiming)) != cudaSuccess) {
+        int code = mfail(nullptr, LBM_ECUDA, "streams/events: %s", cudaGetErrorString(e));
+        multi_free(m);
+        return code;
+    }
+    int r = multi_build_tables(m);
+    if (r) {
+        int code = mfail(nullptr, r, "%s", m->err.c_str());
+        multi_free(m);
+        return code;
+    }
+    *out = m;
+    return LBM_OK;
+}
+
+int lbm_multi_destroy(lbm_multi m)
+{
+    if (!m) return LBM_OK;
+    cudaStreamSynchronize(m->stream);
+    cudaStreamSynchronize(m->comm);
+    multi_free(m);
+    return LBM_OK;
+}
+
+const char* lbm_multi_last_error(lbm_multi m) { return m ? m->err.c_str() : g_multi_err.c_str(); }
+
+int lbm_multi_set_stream(lbm_multi m, void* stream)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    m->stream = static_cast<cudaStream_t>(stream);
+    for (auto* h : m->sub) lbm_set_stream(h, stream);
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_overlap(lbm_multi m, int on)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    m->overlap = on != 0;
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_transfer(lbm_multi m, int mode)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (mode != LBM_TRANSFER_STAGED && mode != LBM_TRANSFER_DIRECT)
+        return mfail(m, LBM_EINVAL, "unknown transfer mode %d", mode);
+    m->direct = mode == LBM_TRANSFER_DIRECT;
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_graph(lbm_multi m, int on)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    m->use_graph = on != 0;
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_force(lbm_multi m, double fx, double fy, double fz)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    for (auto* h : m->sub) {
+        int r = lbm_set_force(h, fx, fy, fz);
+        if (r) return msub(m, h, r);
+    }
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_rounding(lbm_multi m, int mode)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    for (auto* h : m->sub) {
+        int r = lbm_set_rounding(h, mode);
+        if (r) return msub(m, h, r);
+    }
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_smagorinsky(lbm_multi m, double cs)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    for (auto* h : m->sub) {
+        int r = lbm_set_smagorinsky(h, cs);
+        if (r) return msub(m, h, r);
+    }
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_elbm(lbm_multi m, int alpha_mode, double tol, int max_iter, double skip_eps)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    for (auto* h : m->sub) {
+        int r = lbm_set_elbm(h, alpha_mode, tol, max_iter, skip_eps);
+        if (r) return msub(m, h, r);
+    }
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_geometry(lbm_multi m, const uint8_t* mask)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!mask) return mfail(m, LBM_EINVAL, "mask is NULL");
+    if (m->inited) return mfail(m, LBM_ESTATE, "set the geometry before the initial state");
+    char* scr = m->mem + m->off_scr;
+    for (int s = 0; s < m->S; ++s) {
+        int r = gather_rows(m, reinterpret_cast<const char*>(mask), scr, m->lo[s], m->hi[s], 1,
+                            (size_t)m->layer_dense);
+        if (r) return r;
+        r = lbm_set_geometry(m->sub[s], reinterpret_cast<const uint8_t*>(scr));
+        if (r) return msub(m, m->sub[s], r);
+    }
+    return LBM_OK;
+}
+
+int lbm_multi_init_equilibrium(lbm_multi m, const void* rho, const void* u, int field_dtype)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!rho || !u) return mfail(m, LBM_EINVAL, "rho and u must be non-NULL");
+    if (field_dtype != LBM_FIELD_F64 && field_dtype != LBM_FIELD_F32)
+        return mfail(m, LBM_EINVAL, "unknown field dtype %d", field_dtype);
+    const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
+    const size_t rowb = (size_t)m->layer_dense * fs;
+    for (int s = 0; s < m->S; ++s) {
+        const int nloc = m->hi[s] - m->lo[s];
+        char* sr = m->mem + m->off_scr;
+        char* su = sr + (size_t)(nloc + 2) * rowb;
+        int r = gather_rows(m, static_cast<const char*>(rho), sr, m->lo[s], m->hi[s], 1, rowb);
+        if (r) return r;
+        r = gather_rows(m, static_cast<const char*>(u), su, m->lo[s], m->hi[s], m->D, rowb);
+        if (r) return r;
+        r = lbm_init_equilibrium(m->sub[s], sr, su, field_dtype);
+        if (r) return msub(m, m->sub[s], r);
+    }
+    m->t = 0;
+    m->inited = true;
+    return LBM_OK;
+}
+
+int lbm_multi_step(lbm_multi m, int n)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 1) return mfail(m, LBM_EINVAL, "n must be >= 1 (got %d)", n);
+    if (!m->inited) return mfail(m, LBM_ESTATE, "the initial state must precede stepping");
+    for (auto* h : m->sub) {
+        int r = check_step_ready(h);
+        if (r) return msub(m, h, r);
+    }
+    const int cur = m->sub[0]->cur;
+    if (m->use_graph && m->stream != nullptr) {
+        auto key = std::make_pair(n, cur);
+        auto it = m->graphs.find(key);
+        if (it == m->graphs.end()) {
+            cudaGraph_t g;
+            MCK(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal),
+                "begin capture");
+            int from = cur;
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < n && le == cudaSuccess; ++k) {
+                le = multi_step_once(m, from, k == n - 1);
+                from ^= 1;
+            }
+            cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+            if (le != cudaSuccess)
+                return mfail(m, LBM_ECUDA, "launch during capture: %s", cudaGetErrorString(le));
+            MCK(m, ce, "end capture");
+            cudaGraphExec_t ge;
+            cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            MCK(m, ie, "instantiate graph");
+            it = m->graphs.emplace(key, ge).first;
+        }
+        MCK(m, cudaGraphLaunch(it->second, m->stream), "graph launch");
+    } else {
+        int from = cur;
+        for (int k = 0; k < n; ++k) {
+            MCK(m, multi_step_once(m, from, k == n - 1), "subdomain step");
+            from ^= 1;
+        }
+    }
+    const int nl = n * multi_launches_per_step(m);
+    for (auto* h : m->sub) {
+        h->cur ^= (n & 1);
+        h->t += n;
+        h->have_out = true;
+    }
+    m->t += n;
+    m->launches += nl;
+    return LBM_OK;
+}
+
+int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (field_dtype != LBM_FIELD_F64 && field_dtype != LBM_FIELD_F32)
+        return mfail(m, LBM_EINVAL, "unknown field dtype %d", field_dtype);
+    if (m->t == 0) return mfail(m, LBM_ESTATE, "no step has produced output yet");
+    const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
+    const size_t rowb = (size_t)m->layer_dense * fs;
+    const size_t ntot = (size_t)m->axis_n * rowb;
+    for (int s = 0; s < m->S; ++s) {
+        lbm_ctx* h = m->sub[s];
+        const int nloc = m->hi[s] - m->lo[s];
+        const size_t nb = (size_t)(nloc + 2) * rowb;
+        char* scr = m->mem + m->off_scr;
+        // dense local fields (ghost rows included), then the interior rows
+        for (int fld = 0; fld < 2; ++fld) {
+            void* dst = fld == 0 ? rho : u;
+            if (!dst) continue;
+            const int nc = fld == 0 ? 1 : m->D;
+            MCK(m, launch_pack(h->rsize == 8, h->base + (fld == 0 ? h->off_rho : h->off_u),
+                               field_dtype == LBM_FIELD_F32, scr, nc, h->nx, h->ny, h->nz, h->nxp,
+                               h->sq, m->stream),
+                "pack kernel");
+            m->launches += 1;
+            for (int c = 0; c < nc; ++c)
+                MCK(m, cudaMemcpyAsync(static_cast<char*>(dst) + c * ntot + (size_t)m->lo[s] * rowb,
+                                       scr + c * nb + rowb, (size_t)nloc * rowb, cudaMemcpyDefault,
+                                       m->stream),
+                    "copy rows");
+        }
+    }
+    MCK(m, cudaStreamSynchronize(m->stream), "synchronise");
+    for (auto* h : m->sub) {
+        int r = sync_status(h);
+        if (r) return msub(m, h, r);
+    }
+    return LBM_OK;
+}
+
+int lbm_multi_halo_bytes(lbm_multi m, long long* per_step)
+{
+    if (!m || !per_step) return mfail(m, LBM_EINVAL, "NULL argument");
+    *per_step = (long long)(2 * m->S) * m->ndir * m->layer_dense * (long long)m->esize;
+    return LBM_OK;
+}
+
+long long lbm_multi_launch_count(lbm_multi m) { return m ? m->launches : 0; }
+
+int lbm_multi_sync(lbm_multi m)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    MCK(m, cudaStreamSynchronize(m->stream), "synchronise");
+    MCK(m, cudaStreamSynchronize(m->comm), "synchronise");
+    for (auto* h : m->sub) {
+        int r = sync_status(h);
+        if (r) return msub(m, h, r);
+    }
+    return LBM_OK;
 }
 
 }  // extern "C"

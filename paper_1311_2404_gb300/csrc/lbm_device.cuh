@@ -65,25 +65,36 @@ struct D3Q19 {
 // R; store() takes it back.  *_S codecs keep d itself (Sec. 3.7 round-off
 // minimisation; FP16/BF16 extend it to half-width storage).
 // ---------------------------------------------------------------------------
-// Half-width stores default to dithered rounding: round-to-nearest of a value
-// that is nearly the same at a lattice location from one step to the next
-// commits nearly the same rounding error every step, a bias that grows
+// Half-width stores default to stochastic rounding: round-to-nearest of a
+// value that is nearly the same at a lattice location from one step to the
+// next commits nearly the same rounding error every step, a bias that grows
 // linearly in time (3.2e-3 relative velocity error after 1000 steps of the
-// 256^3 vortex).  Adding to the bits that the narrowing drops an offset drawn
-// from a multiplicative hash of the value's own 32 bits (salted with node and
-// direction) and then truncating rounds up with probability equal to the
-// dropped fraction, like stochastic rounding: the errors lose their bias
-// (6e-4 on the same vortex).  The offset needs no counter, so CUDA-graph
-// replay and the batched kernel see identical results.  FP16 values below its
-// normal range (|d| < 2^-14) are dithered on the fixed subnormal grid 2^-24
-// instead (a stochastic floor of |d| 2^24); a flow started from rest keeps
-// most deviations there for many steps, and truncating them would bias every
-// store toward zero.  Inf and NaN are narrowed unchanged.
+// 256^3 vortex).  The narrowing uses the conversion with stochastic rounding
+// (cvt.rs, sm_100 family): it rounds up with probability equal to the
+// fraction the narrowing drops, subnormals and values below the smallest
+// subnormal included, and passes Inf and NaN through.  Its random bits come
+// from a multiplicative hash of each value's own 32 bits salted with node and
+// direction, so no counter is needed and CUDA-graph replay, the batched
+// kernel and subdomain runs reproduce results exactly.  Two directions of a
+// node share one conversion; each element takes 13 (FP16) or 16 (BF16) high
+// bits of its own hash (the instruction reads bits 16.. of the word for the
+// first element, bits 0.. for the second).
 __device__ __forceinline__ unsigned dither_hash(unsigned bits, unsigned salt)
 {
     return bits * 0x9E3779B1u + salt;
 }
 constexpr unsigned kSaltNode = 0x85EBCA77u, kSaltDir = 0xC2B2AE3Du;
+
+// random word for a pair: high 16 bits of a's hash in the high half, of b's
+// hash in the low half, shifted right by `sh` so that a field of 16 - sh bits
+// starts at each half's bit 0 with the hash's top bits
+template <int sh>
+__device__ __forceinline__ unsigned pair_rbits(float a, float b, unsigned sa, unsigned sb)
+{
+    const unsigned ha = dither_hash(__float_as_uint(a), sa);
+    const unsigned hb = dither_hash(__float_as_uint(b), sb);
+    return __byte_perm(hb, ha, 0x7632) >> sh;
+}
 
 struct StoreF64 {
     using T = double;
@@ -92,7 +103,6 @@ struct StoreF64 {
     __device__ static R load(const T* p, double w) { return __ldg(p) - w; }
     __device__ static void store(T* p, R d, double w) { *p = d + w; }
     __device__ static T encode(R d, double w) { return d + w; }
-    __device__ static T encode_dither(R d, unsigned) { return d; }
 };
 struct StoreF32 {
     using T = float;
@@ -101,7 +111,6 @@ struct StoreF32 {
     __device__ static R load(const T* p, double w) { return __ldg(p) - (float)w; }
     __device__ static void store(T* p, R d, double w) { *p = d + (float)w; }
     __device__ static T encode(R d, double w) { return d + (float)w; }
-    __device__ static T encode_dither(R d, unsigned) { return d; }
 };
 struct StoreF32S {
     using T = float;
@@ -110,7 +119,6 @@ struct StoreF32S {
     __device__ static R load(const T* p, double) { return __ldg(p); }
     __device__ static void store(T* p, R d, double) { *p = d; }
     __device__ static T encode(R d, double) { return d; }
-    __device__ static T encode_dither(R d, unsigned) { return d; }
 };
 struct StoreF16S {
     using T = __half;
@@ -119,19 +127,16 @@ struct StoreF16S {
     __device__ static R load(const T* p, double) { return __half2float(__ldg(p)); }
     __device__ static void store(T* p, R d, double) { *p = __float2half_rn(d); }
     __device__ static T encode(R d, double) { return __float2half_rn(d); }
-    __device__ static T encode_dither(R d, unsigned salt)
+    // a in the high half, b in the low half, stochastic rounding
+    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb)
     {
-        const unsigned b = __float_as_uint(d), a = b & 0x7fffffffu;
-        const unsigned h = dither_hash(b, salt);
-        if (a >= 0x7f800000u) return __float2half_rn(d);                  // Inf, NaN
-        if (a >= 0x38800000u)                                              // normal range
-            return __float2half_rz(__uint_as_float((b + (h >> 19)) & ~0x1fffu));  // 13 bits
-        // subnormal: k = floor(|d| 2^24 + r), r uniform in [0, 1); k <= 1024
-        // is the half's magnitude bit pattern (1024 = 2^-14, the smallest normal)
-        const float r = __uint_as_float(0x3f800000u | (h >> 9)) - 1.0f;
-        const unsigned k = __float2uint_rz(fmaf(__uint_as_float(a), 16777216.0f, r));
-        return __ushort_as_half((unsigned short)(k | ((b >> 16) & 0x8000u)));
+        unsigned out;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
+            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<3>(a, b, sa, sb)));
+        return out;
     }
+    __device__ static T hi(unsigned pk) { return __ushort_as_half((unsigned short)(pk >> 16)); }
+    __device__ static T lo(unsigned pk) { return __ushort_as_half((unsigned short)(pk & 0xffffu)); }
 };
 struct StoreBF16S {
     using T = __nv_bfloat16;
@@ -140,14 +145,40 @@ struct StoreBF16S {
     __device__ static R load(const T* p, double) { return __bfloat162float(__ldg(p)); }
     __device__ static void store(T* p, R d, double) { *p = __float2bfloat16_rn(d); }
     __device__ static T encode(R d, double) { return __float2bfloat16_rn(d); }
-    __device__ static T encode_dither(R d, unsigned salt)
+    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb)
     {
-        const unsigned b = __float_as_uint(d);
-        if ((b & 0x7fffffffu) >= 0x7f800000u) return __float2bfloat16_rn(d);   // Inf, NaN
-        return __float2bfloat16_rz(
-            __uint_as_float((b + (dither_hash(b, salt) >> 16)) & 0xffff0000u));  // 16 bits, exact
+        unsigned out;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;"
+            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<0>(a, b, sa, sb)));
+        return out;
+    }
+    __device__ static T hi(unsigned pk)
+    {
+        return __ushort_as_bfloat16((unsigned short)(pk >> 16));
+    }
+    __device__ static T lo(unsigned pk)
+    {
+        return __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
     }
 };
+
+// Stochastically rounded stores of one node's q deviations (half-width
+// codecs): opposite directions (2k+1, 2k+2) share one conversion, the rest
+// population pairs with itself.  dst(i) is the element index of direction i.
+template <class L, class S, class F>
+__device__ __forceinline__ void store_node_sr(typename S::T* B, const float (&d)[L::Q],
+                                              unsigned salt, F dst)
+{
+    B[dst(0)] = S::hi(S::encode_pair(d[0], d[0], salt, salt ^ 0x5bd1e995u));
+#pragma unroll
+    for (int k = 0; k < (L::Q - 1) / 2; ++k) {
+        const int i = 2 * k + 1, j = i + 1;
+        const unsigned pk = S::encode_pair(d[i], d[j], salt + (unsigned)i * kSaltDir,
+                                           salt + (unsigned)j * kSaltDir);
+        B[dst(i)] = S::hi(pk);
+        B[dst(j)] = S::lo(pk);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Kernel parameters (passed by value).
@@ -178,6 +209,8 @@ struct StepParams {
     int has_force;
     int round_nearest;         // half-width stores: 1 round to nearest, 0 dither
     int aa_pushpull;           // AA pattern: 1 = pull/push step (even t), 0 = in-place step
+    int row0, nrows;           // rows updated: z layers (D3Q19) or y rows (D2Q9)
+    int salt_off;              // node-index offset of the dither salt (subdomains)
     double omega;              // 1/tau
     double F[3];               // body force
     double mrt_c[19];          // s_k / |M_k|^2

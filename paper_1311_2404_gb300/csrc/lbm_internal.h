@@ -14,6 +14,14 @@ cudaError_t launch_step_bgk(int lattice, int store, const StepParams& p, bool ma
                             cudaStream_t s);
 cudaError_t launch_step_mrt(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s);
+// One contiguous run of a ghost-layer exchange (16-byte units).
+struct HaloSeg {
+    const uint4* src;
+    uint4* dst;
+    long long n16;
+};
+cudaError_t launch_halo_copy(const HaloSeg* segs_dev, int nseg, long long max_n16,
+                             cudaStream_t s);
 cudaError_t launch_step_reg(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s);
 cudaError_t launch_step_smag(int lattice, int store, const StepParams& p, bool mask, bool aa,

@@ -44,10 +44,12 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
         __syncthreads();
     }
 
+    // rows row0 .. row0 + nrows - 1 of the slowest axis (z, or y on D2Q9)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    bool active = (x < p.nx) && (y < p.ny);
+    const int yb = blockIdx.y * blockDim.y + threadIdx.y;
+    const int y = (L::D == 2) ? p.row0 + yb : yb;
+    const int z = (L::D == 3) ? p.row0 + (int)blockIdx.z : 0;
+    bool active = (x < p.nx) && ((L::D == 2) ? (yb < p.nrows) : (y < p.ny));
     const int plane = p.ny * p.nxp;
     const int n = z * plane + y * p.nxp + x;
     unsigned fl = 0;
@@ -120,21 +122,22 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
         }
         // destination of population i: own node, slot i (AB); node x + e_i,
         // slot i (AA pull/push); own node, slot opp(i) (AA in place)
-        const bool dith = S::kHalf && !p.round_nearest;
-        const unsigned salt = (unsigned)n * kSaltNode;
+        auto dst = [&](int i) -> size_t {
+            if (!AA) return (size_t)i * p.sq + n;
+            if (pushpull)
+                return (size_t)i * p.sq + (rz[1 + L::ez(i)] + ry[1 + L::ey(i)] + cx[1 + L::ex(i)]);
+            return (size_t)L::opp(i) * p.sq + n;
+        };
+        if constexpr (S::kHalf) {
+            if (!p.round_nearest) {
+                store_node_sr<L, S>(B, d, (unsigned)(n + p.salt_off) * kSaltNode, dst);
+            } else {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            size_t dst;
-            if (!AA)
-                dst = (size_t)i * p.sq + n;
-            else if (pushpull)
-                dst = (size_t)i * p.sq + (rz[1 + L::ez(i)] + ry[1 + L::ey(i)] + cx[1 + L::ex(i)]);
-            else
-                dst = (size_t)L::opp(i) * p.sq + n;
-            if (dith)
-                B[dst] = S::encode_dither(d[i], salt + (unsigned)i * kSaltDir);
-            else
-                S::store(B + dst, d[i], L::w(i));
+                for (int i = 0; i < L::Q; ++i) S::store(B + dst(i), d[i], L::w(i));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) S::store(B + dst(i), d[i], L::w(i));
         }
         if (p.out) {
             static_cast<R*>(p.rho)[n] = rho;
@@ -195,7 +198,10 @@ template <class L, class S, int MODEL>
 cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t s)
 {
     const dim3 block = step_block(p.nxp);
-    const dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y, p.nz);
+    const bool d2 = (L::D == 2);
+    const dim3 grid((p.nx + block.x - 1) / block.x,
+                    ((d2 ? p.nrows : p.ny) + block.y - 1) / block.y, d2 ? 1 : p.nrows);
+    if (p.nrows <= 0) return cudaSuccess;
     if (aa) {
         if (mask)
             k_stream_collide<L, S, MODEL, true, true><<<grid, block, 0, s>>>(p);

@@ -37,6 +37,7 @@ LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
 LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIXED2 = range(4)
 LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
 LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
+LBM_TRANSFER_STAGED, LBM_TRANSFER_DIRECT = 0, 1
 MLP_NPARAM = 1394
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ESTATE", 3: "LBM_ENOMEM",
@@ -56,6 +57,24 @@ _ll = ctypes.c_longlong
 _sz = ctypes.c_size_t
 _PROTOS = {
     "lbm_create": (_i, [_i, _i, _i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
+    "lbm_multi_create": (_i, [_i, _i, _i, _i, _i, _d, _i, _i, ctypes.POINTER(_vp)]),
+    "lbm_multi_destroy": (_i, [_vp]),
+    "lbm_multi_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_multi_set_stream": (_i, [_vp, _vp]),
+    "lbm_multi_set_overlap": (_i, [_vp, _i]),
+    "lbm_multi_set_graph": (_i, [_vp, _i]),
+    "lbm_multi_set_transfer": (_i, [_vp, _i]),
+    "lbm_multi_set_force": (_i, [_vp, _d, _d, _d]),
+    "lbm_multi_set_rounding": (_i, [_vp, _i]),
+    "lbm_multi_set_smagorinsky": (_i, [_vp, _d]),
+    "lbm_multi_set_elbm": (_i, [_vp, _i, _d, _i, _d]),
+    "lbm_multi_set_geometry": (_i, [_vp, _vp]),
+    "lbm_multi_init_equilibrium": (_i, [_vp, _vp, _vp, _i]),
+    "lbm_multi_step": (_i, [_vp, _i]),
+    "lbm_multi_get_macro": (_i, [_vp, _vp, _vp, _i]),
+    "lbm_multi_halo_bytes": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "lbm_multi_launch_count": (_ll, [_vp]),
+    "lbm_multi_sync": (_i, [_vp]),
     "lbm_destroy": (_i, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_required_bytes": (_sz, [_vp]),
@@ -139,10 +158,12 @@ def _ptr(x):
     raise TypeError(f"cannot pass {type(x)} as a pointer")
 
 
-def _check(code, handle=None, batch=False, mlp=False):
+def _check(code, handle=None, batch=False, mlp=False, multi=False):
     if code != LBM_OK:
         if mlp:
             msg = _L.lbm_mlp_last_error()
+        elif multi:
+            msg = _L.lbm_multi_last_error(handle)
         elif batch:
             msg = _L.lbm_batch_last_error(handle)
         else:
@@ -422,6 +443,91 @@ def lbm_batch_launch_count(b):
 
 def lbm_batch_nodes(b):
     return int(_L.lbm_batch_nodes(b))
+
+
+# ---- subdomain decomposition (ghost layers, one GPU) ----------------------------
+def _mcheck(code, m):
+    _check(code, m, multi=True)
+
+
+def lbm_multi_create(nx, ny, nz, lattice, model, tau, dtype, nsub):
+    m = _vp()
+    _mcheck(_L.lbm_multi_create(int(nx), int(ny), int(nz), int(lattice), int(model), float(tau),
+                                int(dtype), int(nsub), ctypes.byref(m)), None)
+    return m.value
+
+
+def lbm_multi_destroy(m):
+    _mcheck(_L.lbm_multi_destroy(m), m)
+
+
+def lbm_multi_set_stream(m, stream):
+    _mcheck(_L.lbm_multi_set_stream(m, _ptr(stream)), m)
+
+
+def lbm_multi_set_overlap(m, on):
+    _mcheck(_L.lbm_multi_set_overlap(m, int(bool(on))), m)
+
+
+def lbm_multi_set_transfer(m, mode):
+    _mcheck(_L.lbm_multi_set_transfer(m, int(mode)), m)
+
+
+def lbm_multi_set_graph(m, on):
+    _mcheck(_L.lbm_multi_set_graph(m, int(bool(on))), m)
+
+
+def lbm_multi_set_force(m, fx, fy, fz=0.0):
+    _mcheck(_L.lbm_multi_set_force(m, float(fx), float(fy), float(fz)), m)
+
+
+def lbm_multi_set_rounding(m, mode):
+    _mcheck(_L.lbm_multi_set_rounding(m, int(mode)), m)
+
+
+def lbm_multi_set_smagorinsky(m, cs):
+    _mcheck(_L.lbm_multi_set_smagorinsky(m, float(cs)), m)
+
+
+def lbm_multi_set_elbm(m, alpha_mode, tol=1e-12, max_iter=20, skip_eps=1e-3):
+    _mcheck(_L.lbm_multi_set_elbm(m, int(alpha_mode), float(tol), int(max_iter),
+                                  float(skip_eps)), m)
+
+
+def lbm_multi_set_geometry(m, mask):
+    if isinstance(mask, np.ndarray):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    _mcheck(_L.lbm_multi_set_geometry(m, _ptr(mask)), m)
+
+
+def lbm_multi_init_equilibrium(m, rho, u):
+    fd = _field_dtype(rho)
+    if _field_dtype(u) != fd:
+        raise TypeError("rho and u must share a dtype")
+    _mcheck(_L.lbm_multi_init_equilibrium(m, _ptr(rho), _ptr(u), fd), m)
+
+
+def lbm_multi_step(m, n=1):
+    _mcheck(_L.lbm_multi_step(m, int(n)), m)
+
+
+def lbm_multi_get_macro(m, rho, u):
+    ref = rho if rho is not None else u
+    _mcheck(_L.lbm_multi_get_macro(m, _ptr(rho), _ptr(u), _field_dtype(ref)), m)
+
+
+def lbm_multi_halo_bytes(m):
+    v = _ll(0)
+    _mcheck(_L.lbm_multi_halo_bytes(m, ctypes.byref(v)), m)
+    return int(v.value)
+
+
+def lbm_multi_launch_count(m):
+    return int(_L.lbm_multi_launch_count(m))
+
+
+def lbm_multi_sync(m):
+    _mcheck(_L.lbm_multi_sync(m), m)
 
 
 # ---- convenience wrapper ------------------------------------------------------

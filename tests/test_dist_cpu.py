@@ -1,0 +1,55 @@
+"""The N > 1 bench path on CPU: two gloo ranks (127.0.0.1) take the maximum
+of their timings, the whole-job throughput counts every rank's updates over
+that time, and the reference arm does its work on rank 0 only."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, lr = bench.dist_env()
+        assert (r, w, lr) == (rank, world, rank)
+        vals = bench.max_over_ranks([10.0 + rank, 5.0 - rank], w, "cpu")
+        out[rank] = vals
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    assert out[0] == [11.0, 5.0] and out[1] == [11.0, 5.0]
+    # 2 ranks x 1e6 nodes x 100 steps in the slowest rank's 11 ms
+    assert abs(bench.job_glups(1_000_000, 100, world, 11.0) - 2e8 / 11e-3 / 1e9) < 1e-9
+
+
+def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    import argparse
+    ns = argparse.Namespace(workload="tg256", dtype="f32s", size=0, model="", steps=1, warmup=0,
+                            impl="reference", gpus=2)
+    bench.run_reference(ns)
+    assert capsys.readouterr().out == ""

@@ -16,27 +16,60 @@ import pytest
 from oracle import BGK, MRT, ELBM, FIXED2, NEWTON, SERIES_GUARDED, AL_CONV, AL_GUARDED
 
 
+def _dim(code):
+    return 2 if code in (2, 9) else 3
+
+
 def _rand_f(oracle_lib, D, rng, u_amp=0.05, noise=0.02, kind=0):
-    u = rng.uniform(-u_amp, u_amp, D)
+    u = rng.uniform(-u_amp, u_amp, _dim(D))
     rho = 1.0 + rng.uniform(-0.05, 0.05)
     fe = oracle_lib.feq(D, rho, u, kind)
     f = fe * (1.0 + noise * rng.standard_normal(len(fe)))
     return f
 
 
-@pytest.mark.parametrize("D", [2, 3])
-def test_polynomial_feq_moments(oracle_lib, D):
-    e, w, _ = oracle_lib.lattice(D)
+@pytest.mark.parametrize("code", [2, 3, 15, 27])
+def test_polynomial_feq_moments(oracle_lib, code):
+    D = _dim(code)
+    e, w, _ = oracle_lib.lattice(code)
     ef = e[:, :D].astype(float)
     rng = np.random.default_rng(1)
     for _ in range(20):
         rho = rng.uniform(0.8, 1.2)
         u = rng.uniform(-0.1, 0.1, D)
-        fe = oracle_lib.feq(D, rho, u, 0)
+        fe = oracle_lib.feq(code, rho, u, 0)
         assert abs(fe.sum() - rho) < 1e-15
         assert np.abs(ef.T @ fe - rho * u).max() < 1e-15
         P = np.einsum("i,ia,ib->ab", fe, ef, ef)
         assert np.abs(P - rho * (np.eye(D) / 3 + np.outer(u, u))).max() < 1e-15
+
+
+def test_entropic_feq_d3q27_is_exact_minimiser(oracle_lib):
+    """D3Q27 is the tensor product of three D1Q3 sets (its weights factor as
+    (2/3, 1/6, 1/6)^3), so the printed product form is the exact constrained
+    H-minimiser there, as on D2Q9: mass and momentum hold without
+    restoration and ln(f_eq / w) is affine in e.  On D3Q15 it is not."""
+    e, w, _ = oracle_lib.lattice(27)
+    ef = e.astype(float)
+    w1 = {0: 2 / 3, 1: 1 / 6}
+    for i in range(27):
+        assert abs(w[i] - np.prod([w1[abs(int(c))] for c in e[i]])) < 1e-17
+    A = np.column_stack([np.ones(27), ef])
+    rng = np.random.default_rng(27)
+    for _ in range(20):
+        rho = rng.uniform(0.9, 1.1)
+        u = rng.uniform(-0.1, 0.1, 3)
+        fe = oracle_lib.feq(27, rho, u, 1)
+        assert abs(fe.sum() - rho) < 1e-15
+        assert np.abs(ef.T @ fe - rho * u).max() < 1e-15
+        lhs = np.log(fe / w)
+        coef, *_ = np.linalg.lstsq(A, lhs, rcond=None)
+        assert np.abs(A @ coef - lhs).max() < 1e-14
+        # restoring changes nothing beyond rounding
+        assert np.abs(oracle_lib.feq(27, rho, u, 2) - fe).max() < 4e-16
+    # on D3Q15 the raw product misses mass by far more than rounding
+    raw15 = oracle_lib.feq(15, 1.0, np.array([0.08, -0.05, 0.03]), 1)
+    assert abs(raw15.sum() - 1.0) > 1e-9
 
 
 def test_entropic_feq_d2q9_is_constrained_minimiser(oracle_lib):
@@ -99,17 +132,19 @@ def test_entropic_feq_d3q19_restored(oracle_lib):
         assert np.abs(fe - fp).max() < 2.0 * np.abs(u).max() ** 3
 
 
-@pytest.mark.parametrize("D,model", [(2, BGK), (3, BGK), (3, MRT), (2, ELBM), (3, ELBM)])
-def test_collision_conserves_mass_and_momentum(oracle_lib, D, model):
+@pytest.mark.parametrize("code,model", [(2, BGK), (3, BGK), (3, MRT), (2, ELBM), (3, ELBM),
+                                        (15, BGK), (27, BGK), (15, ELBM), (27, ELBM)])
+def test_collision_conserves_mass_and_momentum(oracle_lib, code, model):
     """Collision conserves mass; momentum grows by exactly the force F."""
-    e, _, _ = oracle_lib.lattice(D)
+    D = _dim(code)
+    e, _, _ = oracle_lib.lattice(code)
     ef = e[:, :D].astype(float)
     rng = np.random.default_rng(4)
     for force in ((0.0, 0.0, 0.0), (1e-4, -3e-5, 2e-5)):
-        p = oracle_lib.make_params(D=D, model=model, tau=0.57, force=force[:D] + (0.0,) * (3 - D),
-                                   skip_eps=0.0)
+        p = oracle_lib.make_params(D=code, model=model, tau=0.57,
+                                   force=force[:D] + (0.0,) * (3 - D), skip_eps=0.0)
         for _ in range(10):
-            f = _rand_f(oracle_lib, D, rng)
+            f = _rand_f(oracle_lib, code, rng)
             fo, rho, v, info = oracle_lib.collide(p, f)
             assert abs(fo.sum() - f.sum()) < 1e-15
             dj = ef.T @ fo - ef.T @ f
@@ -152,14 +187,15 @@ def test_elbm_alpha2_is_lbgk(oracle_lib):
     entropic equilibrium)."""
     rng = np.random.default_rng(7)
     tau = 0.6
-    for D in (2, 3):
-        p = oracle_lib.make_params(D=D, model=ELBM, tau=tau, alpha_mode=FIXED2)
+    for code in (2, 3, 15, 27):
+        D = _dim(code)
+        p = oracle_lib.make_params(D=code, model=ELBM, tau=tau, alpha_mode=FIXED2)
         for _ in range(5):
-            f = _rand_f(oracle_lib, D, rng)
+            f = _rand_f(oracle_lib, code, rng)
             rho = f.sum()
-            e, _, _ = oracle_lib.lattice(D)
+            e, _, _ = oracle_lib.lattice(code)
             u = (e[:, :D].T @ f) / rho
-            fe = oracle_lib.feq(D, rho, u, 2)
+            fe = oracle_lib.feq(code, rho, u, 2)
             fo, *_ = oracle_lib.collide(p, f)
             assert np.abs(fo - (f + (fe - f) / tau)).max() < 1e-15
 

@@ -23,23 +23,33 @@ def _weights_table():
     return rows
 
 
-@pytest.mark.parametrize("D,name", [(2, "D2Q9"), (3, "D3Q19")])
-def test_weights_match_paper_table(oracle_lib, D, name):
-    e, w, _ = oracle_lib.lattice(D)
+LATTICES = [(2, "D2Q9", 9), (3, "D3Q19", 19), (15, "D3Q15", 15), (27, "D3Q27", 27)]
+
+
+@pytest.mark.parametrize("code,name,Q", LATTICES)
+def test_weights_match_paper_table(oracle_lib, code, name, Q):
+    e, w, _ = oracle_lib.lattice(code)
     table = _weights_table()[name]
-    assert len(w) == (9 if D == 2 else 19)
+    assert len(w) == Q
+    counts = [0, 0, 0, 0]
     for ei, wi in zip(e, w):
         n2 = int((ei * ei).sum())
+        counts[n2] += 1
         assert table[n2] is not None
         assert wi == pytest.approx(float(table[n2]), abs=1e-16)
+    # every link length the table lists is present, with all its links
+    D = 2 if Q == 9 else 3
+    full = {2: [1, 4, 4, 0], 3: [1, 6, 12, 8]}[D]
+    for k in range(4):
+        assert counts[k] == (full[k] if table[k] is not None else 0)
     # the table's rows sum to one over their links (exact rational check)
-    counts = {2: [1, 4, 4], 3: [1, 6, 12]}[D]
-    assert sum(c * table[k] for k, c in enumerate(counts)) == 1
+    assert sum(c * table[k] for k, c in enumerate(counts) if c) == 1
 
 
-@pytest.mark.parametrize("D", [2, 3])
-def test_isotropy(oracle_lib, D):
-    e, w, _ = oracle_lib.lattice(D)
+@pytest.mark.parametrize("code", [2, 3, 15, 27])
+def test_isotropy(oracle_lib, code):
+    e, w, _ = oracle_lib.lattice(code)
+    D = 2 if code == 2 else 3
     e = e[:, :D].astype(np.float64)
     assert abs(w.sum() - 1) < 1e-15
     assert np.abs(w @ e).max() < 1e-16
@@ -63,7 +73,7 @@ def test_opposites_match_listing_pairs(oracle_lib):
         assert opp[i] == j and opp[j] == i
 
 
-@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("D", [2, 3, 15, 27])
 def test_opposite_is_involution(oracle_lib, D):
     e, _, opp = oracle_lib.lattice(D)
     assert (opp[opp] == np.arange(len(opp))).all()
