@@ -57,6 +57,8 @@ class OracleParams(ctypes.Structure):
         ("mlp", ctypes.POINTER(ctypes.c_double)),
         ("smag_cs", ctypes.c_double),
         ("q", ctypes.c_int),
+        ("bc_kind", ctypes.c_int * 15), ("bc_method", ctypes.c_int * 15),
+        ("bc_normal", ctypes.c_int * 15), ("bc_val", (ctypes.c_double * 3) * 15),
     ]
 
 
@@ -95,6 +97,7 @@ def lib():
         L.oracle_mlp_guess.argtypes = [dp, dp]
         L.oracle_mlp_guess.restype = ctypes.c_double
         L.oracle_init.argtypes = [PP, dp, dp, dp]
+        L.oracle_bc_node.argtypes = [PP, ctypes.c_int, dp]
         L.oracle_run.argtypes = [PP, dp, dp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
                                  dp, dp, dp, dp]
         L.oracle_max_threads.argtypes = [ctypes.c_int]
@@ -170,6 +173,28 @@ def make_params(nx=1, ny=1, nz=1, D=3, model=BGK, tau=0.6, force=(0.0, 0.0, 0.0)
         p._mlp_keep = arr  # keep alive with the struct
         p.mlp = _dp(arr)
     return p
+
+
+# boundary-condition codes: kinds, methods, inward normals (+-1 x, +-2 y, +-3 z)
+BC_VELOCITY, BC_PRESSURE = 1, 2
+BC_EQUILIBRIUM, BC_ZOUHE, BC_REGULARIZED = 0, 1, 2
+
+
+def set_bc(p: OracleParams, k: int, kind: int, method: int, normal: int, value) -> None:
+    """Condition k, used by mask code 2 + k: value is the velocity (kind
+    BC_VELOCITY) or [rho] (BC_PRESSURE)."""
+    p.bc_kind[k], p.bc_method[k], p.bc_normal[k] = kind, method, normal
+    val = list(value) + [0.0] * (3 - len(value))
+    for a in range(3):
+        p.bc_val[k][a] = float(val[a])
+
+
+def bc_node(p: OracleParams, k: int, f) -> np.ndarray:
+    """Condition k applied to one node's post-streaming populations."""
+    ff = np.array(f, dtype=np.float64)
+    r = lib().oracle_bc_node(ctypes.byref(p), int(k), _dp(ff))
+    assert r == 0
+    return ff
 
 
 def collide(p: OracleParams, f) -> tuple:

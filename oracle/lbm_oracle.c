@@ -292,6 +292,11 @@ typedef struct {
     const double* mlp;/* MLP parameters for alpha_mode 2 */
     double smag_cs;   /* Smagorinsky constant C_S (model 4) */
     int q;            /* velocity set: 0 = D2Q9 / D3Q19 by D, or 9, 15, 19, 27 */
+    /* velocity / pressure boundary conditions, entry k for mask code 2 + k */
+    int bc_kind[15];      /* 1 velocity, 2 pressure */
+    int bc_method[15];    /* 0 equilibrium, 1 Zou-He, 2 regularized */
+    int bc_normal[15];    /* inward normal: +-1 x, +-2 y, +-3 z */
+    double bc_val[15][3]; /* velocity, or the density in [0] */
 } oracle_params;
 
 /* Per-node ELBM outcome. */
@@ -495,6 +500,105 @@ done:
 /* Collision of one node (post-streaming f in, post-collision f out).   */
 /* info = {alpha, evals, status, |g|/a2} for ELBM.                      */
 /* ------------------------------------------------------------------ */
+/* ------------------------------------------------------------------ */
+/* Velocity and pressure boundary nodes (Sec. 2.3: equilibrium, Zou-He and  */
+/* regularized variants).                                                   */
+/* ------------------------------------------------------------------ */
+/* A boundary node is a fluid node next to the outside of the domain; n is its
+ * inward unit normal along a lattice axis.  After streaming, the populations
+ * with e_i . n > 0 came from outside and are unknown; the others are known.
+ * Mass and normal momentum of the known ones fix the missing moment:
+ *   rho (1 - v_n) = S_0 + 2 S_out - F_n / 2,
+ * S_0 = sum over e_i . n = 0, S_out = sum over e_i . n < 0, with the momentum
+ * j = rho v - F/2 of Guo's scheme (Eq. edm_momentum read backwards), so that
+ * the collision reports exactly the prescribed v.  Velocity condition: v
+ * given, rho from the relation; pressure condition: rho given, v = v_n n with
+ * v_n from the relation (no tangential velocity).  Then, with f_eq at (rho, v):
+ *   equilibrium: f_i = f_eq_i - (3/2) w_i e_i . F (all i);
+ *   Zou-He: unknown f_i = f_opp(i) + f_eq_i - f_eq_opp(i) (bounce-back of the
+ *     non-equilibrium part), then the momentum left over, dJ = j - sum f e,
+ *     goes to the unknown populations: its normal part to the one along n,
+ *     each tangential part t split evenly, with sign e_it, over the unknown
+ *     populations with e_it != 0 of the smallest |e| (D2Q9, D3Q19, D3Q27:
+ *     the two edge links; D3Q15: the four body diagonals);
+ *   regularized: unknown f_i as in Zou-He before the correction, then all
+ *     f_i = f_eq_i + w_i / (2 c_s^4) (e_i e_i - c_s^2 I) : Pi^neq
+ *     - (3/2) w_i e_i . F, Pi^neq = sum (f - f_eq) e e. */
+static void bc_node(const olat* L, const oracle_params* p, int id, double* f)
+{
+    const int Q = L->Q, D = L->D;
+    const int ax = abs(p->bc_normal[id]) - 1, sg = p->bc_normal[id] > 0 ? 1 : -1;
+    const double* F = p->force;
+    double S0 = 0.0, So = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        int en = sg * L->e[i][ax];
+        if (en == 0) S0 += f[i];
+        else if (en < 0) So += f[i];
+    }
+    const double Fn = sg * F[ax];
+    double rho, v[3] = {0.0, 0.0, 0.0};
+    if (p->bc_kind[id] == 1) {
+        for (int a = 0; a < D; ++a) v[a] = p->bc_val[id][a];
+        rho = (S0 + 2.0 * So - 0.5 * Fn) / (1.0 - sg * v[ax]);
+    } else {
+        rho = p->bc_val[id][0];
+        v[ax] = sg * (1.0 - (S0 + 2.0 * So - 0.5 * Fn) / rho);
+    }
+    double feq[OQMAX];
+    feq_poly(L, rho, v, feq);
+    const int method = p->bc_method[id];
+    if (method == 0) {
+        for (int i = 0; i < Q; ++i) f[i] = feq[i] - 1.5 * L->w[i] * edot(L, i, F);
+        return;
+    }
+    for (int i = 0; i < Q; ++i)
+        if (sg * L->e[i][ax] > 0) f[i] = f[L->opp[i]] + feq[i] - feq[L->opp[i]];
+    if (method == 1) {
+        double dJ[3];
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < Q; ++i) s += L->e[i][a] * f[i];
+            dJ[a] = rho * v[a] - 0.5 * F[a] - s;
+        }
+        for (int i = 0; i < Q; ++i) {      /* the link along n */
+            int on = 1;
+            for (int a = 0; a < D; ++a) on &= (L->e[i][a] == (a == ax ? sg : 0));
+            if (on) f[i] += sg * dJ[ax];
+        }
+        for (int t = 0; t < D; ++t) {
+            if (t == ax) continue;
+            int best = 99, cnt = 0;
+            for (int i = 0; i < Q; ++i)
+                if (sg * L->e[i][ax] > 0 && L->e[i][t] != 0) {
+                    int n2 = 0;
+                    for (int a = 0; a < D; ++a) n2 += L->e[i][a] * L->e[i][a];
+                    if (n2 < best) { best = n2; cnt = 0; }
+                    if (n2 == best) ++cnt;
+                }
+            for (int i = 0; i < Q; ++i)
+                if (sg * L->e[i][ax] > 0 && L->e[i][t] != 0) {
+                    int n2 = 0;
+                    for (int a = 0; a < D; ++a) n2 += L->e[i][a] * L->e[i][a];
+                    if (n2 == best) f[i] += L->e[i][t] * dJ[t] / cnt;
+                }
+        }
+        return;
+    }
+    double Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b)
+                Pi[a][b] += (f[i] - feq[i]) *
+                            (L->e[i][a] * L->e[i][b] - (a == b ? 1.0 / 3.0 : 0.0));
+    for (int i = 0; i < Q; ++i) {
+        double pr = 0.0;
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b)
+                pr += (L->e[i][a] * L->e[i][b] - (a == b ? 1.0 / 3.0 : 0.0)) * Pi[a][b];
+        f[i] = feq[i] + 4.5 * L->w[i] * pr - 1.5 * L->w[i] * edot(L, i, F);
+    }
+}
+
 static int collide_node(const olat* L, const oracle_params* p, double* f, double* rho_out,
                         double* v_out, double* info)
 {
@@ -680,6 +784,15 @@ int oracle_collide(const oracle_params* p, double* f, double* rho, double* v, do
     return r;
 }
 
+/* One boundary node's reconstruction (condition id) on post-streaming f. */
+int oracle_bc_node(const oracle_params* p, int id, double* f)
+{
+    const olat* L = PLAT(p);
+    if (!L || id < 0 || id >= 15 || (p->bc_kind[id] != 1 && p->bc_kind[id] != 2)) return -1;
+    bc_node(L, p, id, f);
+    return 0;
+}
+
 /* g(alpha) and g'(alpha) for given f and f_eq (diagnostics / pins). */
 int oracle_elbm_g(int D, const double* f, const double* feq, double alpha, double* g, double* gp)
 {
@@ -746,7 +859,8 @@ int oracle_init(const oracle_params* p, const double* rho, const double* u, doub
 /* nsteps AB steps: F (post-collision state at t) -> F at t + nsteps.
  * Ftmp is scratch of the same size.  rho, u ([D][z][y][x]) receive the
  * macroscopic fields of the last step; alpha (may be NULL) the last step's
- * per-node alpha.  mask (may be NULL): 0 fluid, nonzero solid.  Solid nodes
+ * per-node alpha.  mask (may be NULL): 0 fluid, 1 solid, 2 + k a boundary
+ * node of condition k (bc_* entries of the parameters).  Solid nodes
  * get F = 0, rho = 0, u = 0.  stats (may be NULL, 6 doubles): total g
  * evaluations, skipped, clamped, not converged, guarded-accepted, nodes. */
 int oracle_run(const oracle_params* p, double* F, double* Ftmp, const uint8_t* mask,
@@ -774,7 +888,7 @@ int oracle_run(const oracle_params* p, double* F, double* Ftmp, const uint8_t* m
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
                     size_t n = ((size_t)z * ny + y) * nx + x;
-                    if (mask && mask[n]) {
+                    if (mask && mask[n] == 1) {
                         for (int i = 0; i < Q; ++i) B[i * N + n] = 0.0;
                         if (last) {
                             rho[n] = 0.0;
@@ -791,9 +905,10 @@ int oracle_run(const oracle_params* p, double* F, double* Ftmp, const uint8_t* m
                         int sy = ((y - L->e[i][1]) % ny + ny) % ny;
                         int sz = ((z - L->e[i][2]) % nz + nz) % nz;
                         size_t src = ((size_t)sz * ny + sy) * nx + sx;
-                        if (mask && mask[src]) f[i] = A[L->opp[i] * N + n];
+                        if (mask && mask[src] == 1) f[i] = A[L->opp[i] * N + n];
                         else f[i] = A[i * N + src];
                     }
+                    if (mask && mask[n] >= 2) bc_node(L, p, mask[n] - 2, f);
                     double r, v[3], info[4] = {0, 0, 0, 0};
                     collide_node(L, p, f, &r, v, info);
                     for (int i = 0; i < Q; ++i) B[i * N + n] = f[i];
