@@ -7,7 +7,7 @@ u0 0.05.  One bench step = one lattice Boltzmann time step over all nodes
 (one fused stream-collide launch).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tg256|duct|elbm|kida|batch] [--dtype f32s|f16s|bf16s|f32]
+                  [--workload tg256|duct|elbm|kida|ldc|batch] [--dtype f32s|f16s|bf16s|f32]
 
 For N > 1 (torchrun) every rank runs an independent replica of the workload
 (the domains do not exchange data; weak scaling) and rank 0 reports the
@@ -33,7 +33,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-B_PER_NODE = {"f32s": 152, "f32": 152, "f16s": 76, "bf16s": 76, "f64": 304}
+B_PER_NODE = {"f32s": 152, "f32": 152, "f16s": 76, "bf16s": 76, "f64": 304}   # D3Q19
+ESIZE = {"f32s": 4, "f32": 4, "f16s": 2, "bf16s": 2, "f64": 8}
+LATTICE_NAME = {0: "D2Q9", 1: "D3Q19", 2: "D3Q15", 3: "D3Q27"}
+LATTICE_Q = {0: 9, 1: 19, 2: 15, 3: 27}
+
+
+def bytes_per_node(dtype, lattice=1):
+    """Algorithmic bytes of one node update: q values read and q written."""
+    return 2 * LATTICE_Q[lattice] * ESIZE[dtype]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -44,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tg256",
-                    choices=["tg256", "duct", "elbm", "kida", "batch"])
+                    choices=["tg256", "duct", "elbm", "kida", "ldc", "batch"])
     ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
                     help="ELBM alpha solve for --workload elbm")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
@@ -55,6 +63,8 @@ def parse():
     ap.add_argument("--dtype", default="f32s", choices=["f32s", "f32", "f16s", "bf16s"])
     ap.add_argument("--model", default="", choices=["", "bgk", "mrt", "reg", "smag"],
                     help="override the collision model of the tg256 / duct / kida workloads")
+    ap.add_argument("--lattice", default="", choices=["", "q15", "q19", "q27"],
+                    help="override the 3-D velocity set of the workload")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--size", type=int, default=0,
                     help="override the cube edge of the 256^3 workloads (profiling runs)")
@@ -175,16 +185,25 @@ def job_glups(nodes_per_rank, steps, world, ms_max):
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def workload_spec(name, dtype, size=0, model=""):
+def workload_spec(name, dtype, size=0, model="", lattice=""):
     spec = _workload_spec(name, dtype)
+    if lattice and name != "batch":
+        from paper_1311_2404_gb300 import lbm
+        spec["lattice"] = {"q15": lbm.LBM_D3Q15, "q19": lbm.LBM_D3Q19,
+                           "q27": lbm.LBM_D3Q27}[lattice]
+        spec["name"] = spec["name"].replace("d3q19", "d3" + lattice)
     if model:
         spec["model"] = {"bgk": 0, "mrt": 1, "reg": 3, "smag": 4}[model]
         for m in ("lbgk", "mrt", "smag"):
             if f"_{m}_" in spec["name"]:
                 spec["name"] = spec["name"].replace(f"_{m}_", f"_{model}_")
-    if size and name in ("tg256", "elbm", "kida"):
+    if size and name in ("tg256", "elbm", "kida", "ldc"):
         spec["n"] = (size, size, size)
-        spec["name"] = spec["name"].replace("256^3", f"{size}^3").replace("350^3", f"{size}^3")
+        for tag in ("256^3", "350^3", "254^3"):
+            spec["name"] = spec["name"].replace(tag, f"{size}^3")
+        if name == "ldc":
+            from paper_1311_2404_gb300 import workloads as wl
+            spec["tau"] = wl.ldc_tau(size)
     if size and name == "duct":
         spec["n"] = (2 * size, size, size)
         spec["name"] = spec["name"].replace("512x256x256", f"{2 * size}x{size}x{size}")
@@ -207,6 +226,13 @@ def _workload_spec(name, dtype):
         return dict(kind="turb", name="d3q19_elbm_decaying_turbulence_256^3", n=(256, 256, 256),
                     lattice=lbm.LBM_D3Q19, model=lbm.LBM_ELBM, tau=0.5005, dtype=dmap[dtype],
                     mask=None, force=(0, 0, 0))
+    if name == "ldc":
+        # the paper's benchmark cavity, Re = 1000 with a lid at 0.05, regularized lid
+        from paper_1311_2404_gb300 import workloads as wl
+        return dict(kind="ldc", name="d3q19_lbgk_lid_driven_cavity_254^3", n=(254, 254, 254),
+                    lattice=lbm.LBM_D3Q19, model=lbm.LBM_BGK, tau=wl.ldc_tau(254),
+                    dtype=dmap[dtype], mask="ldc", force=(0, 0, 0),
+                    bcs=[(0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_REGULARIZED, -2, [0.05, 0.0, 0.0])])
     if name == "kida":
         # Re = N u0 / nu = 4000 at N = 350, u0 = 0.05 (the paper's smaller Kida case)
         return dict(kind="kida", name="d3q19_smag_kida_vortex_350^3", n=(350, 350, 350),
@@ -228,6 +254,10 @@ def workload_inputs(spec):
     elif spec["kind"] == "kida":
         rho, u = wl.kida(nx, 0.05)
         mask = None
+    elif spec["kind"] == "ldc":
+        mask = wl.ldc_mask(nx)
+        rho = np.ones((nz, ny, nx))
+        u = np.zeros((3, nz, ny, nx))
     else:
         rho, u = wl.turbulence(nx)
         mask = None
@@ -242,7 +272,7 @@ def run_multi(args):
     import torch
     torch.cuda.set_device(0)
     from paper_1311_2404_gb300 import lbm
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
@@ -255,6 +285,8 @@ def run_multi(args):
         lbm.lbm_multi_set_graph(m, True)
         if args.direct:
             lbm.lbm_multi_set_transfer(m, lbm.LBM_TRANSFER_DIRECT)
+        for b in spec.get("bcs", ()):
+            lbm.lbm_multi_set_boundary(m, *b)
         if mask is not None:
             lbm.lbm_multi_set_geometry(m, mask)
         if any(spec["force"]):
@@ -295,7 +327,7 @@ def run_multi(args):
         e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
         lbm.lbm_multi_destroy(m)
     glups = nodes * args.steps / (ms * 1e-3) / 1e9
-    bpn = B_PER_NODE[args.dtype] + (1 if mask is not None else 0)
+    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (1 if mask is not None else 0)
     per_launch_s = ms / 1e3 / args.steps
     achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_kind = peaks()
@@ -305,7 +337,7 @@ def run_multi(args):
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 6),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded analytic/random initial fields; no dataset)",
-        "config": {"workload": spec["name"], "lattice": "D3Q19",
+        "config": {"workload": spec["name"], "lattice": LATTICE_NAME[spec["lattice"]],
                    "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG", 4: "SMAG"}[spec["model"]],
                    "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
                    "subdomains": args.subdomains, "overlap": not args.no_overlap,
@@ -337,7 +369,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1311_2404_gb300 import lbm
 
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
@@ -347,6 +379,8 @@ def run_ours(args):
                              spec["dtype"], stream=stream.cuda_stream,
                              pattern=lbm.LBM_PATTERN_AA if args.pattern == "aa"
                              else lbm.LBM_PATTERN_AB)
+        for b in spec.get("bcs", ()):
+            lbm.lbm_set_boundary(sim.h, *b)
         if mask is not None:
             sim.set_geometry(mask)
         if any(spec["force"]):
@@ -427,7 +461,7 @@ def run_ours(args):
         return
     glups = job_glups(nodes, args.steps, world, ms_max)
     per_launch_s = ms / 1e3 / args.steps
-    bpn = B_PER_NODE[args.dtype] + (1 if mask is not None else 0)
+    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (1 if mask is not None else 0)
     achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_kind = peaks()
     traffic = traffic_for(args.workload, args.dtype)
@@ -444,7 +478,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"f32s": "f32", "f32": "f32", "f16s": "f32", "bf16s": "f32"}[args.dtype],
         "data": "synthetic (seeded analytic/random initial fields; no dataset)",
-        "config": {"workload": spec["name"], "lattice": "D3Q19",
+        "config": {"workload": spec["name"], "lattice": LATTICE_NAME[spec["lattice"]],
                    "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG",
                              4: "SMAG"}[spec["model"]],
                    **({"smagorinsky_cs": 0.1} if spec["model"] == 4 else {}),
@@ -454,7 +488,7 @@ def run_ours(args):
                    **({"pattern": "AA"} if args.pattern == "aa" else {}),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
-                         % (B_PER_NODE[args.dtype] * nodes / 1e9)},
+                         % (bytes_per_node(args.dtype, spec["lattice"]) * nodes / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": peak_kind, "bytes_per_node": bpn},
@@ -485,15 +519,19 @@ def _oracle_sample(spec, nz_s, ny_s=None):
     ny_s = ny_s or ny
     model = {0: oracle.BGK, 1: oracle.MRT, 2: oracle.ELBM, 3: oracle.REG,
              4: oracle.SMAG}[spec["model"]]
-    p = oracle.make_params(nx, ny_s, nz_s, D=3, model=model, tau=spec["tau"],
-                           force=spec["force"])
+    p = oracle.make_params(nx, ny_s, nz_s, D={1: 3, 2: 15, 3: 27}[spec["lattice"]], model=model,
+                           tau=spec["tau"], force=spec["force"])
+    for b in spec.get("bcs", ()):
+        oracle.set_bc(p, *b)
     if spec["kind"] == "tg":
         rho, u = wl.taylor_green(nx, 0.05, nz=nz_s, D=3)
         rho, u = rho[:, :ny_s].copy(), u[:, :, :ny_s].copy()
         mask = None
-    elif spec["kind"] == "duct":
-        m, _ = wl.duct_with_spheres(nx, ny, nz)
-        mask = np.ascontiguousarray(m[:nz_s, :ny_s])
+    elif spec["kind"] in ("duct", "ldc"):
+        m = wl.duct_with_spheres(nx, ny, nz)[0] if spec["kind"] == "duct" else wl.ldc_mask(nx)
+        # interior planes of the cavity (its first plane is a wall)
+        z0 = 0 if spec["kind"] == "duct" else min(1, nz - nz_s)
+        mask = np.ascontiguousarray(m[z0:z0 + nz_s, :ny_s])
         rho = np.ones((nz_s, ny_s, nx))
         u = np.zeros((3, nz_s, ny_s, nx))
     else:
@@ -529,7 +567,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
     import oracle
     oracle.build()
     cores = oracle.max_threads(0)
@@ -560,7 +598,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded analytic/random initial fields; no dataset)",
-        "config": {"workload": spec["name"], "lattice": "D3Q19",
+        "config": {"workload": spec["name"], "lattice": LATTICE_NAME[spec["lattice"]],
                    "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG",
                              4: "SMAG"}[spec["model"]],
                    **({"smagorinsky_cs": 0.1} if spec["model"] == 4 else {}),

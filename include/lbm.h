@@ -59,7 +59,9 @@ enum {
 };
 
 /* ---- lattices, collision models, storage types ------------------------ */
-enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };          /* Sec. 2, Fig. lattices, Table bgkweights */
+/* Velocity sets (Sec. 2, Fig. lattices, Table bgkweights).  MRT is defined
+ * on D3Q19 only; every other model runs on all four. */
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q15 = 2, LBM_D3Q27 = 3 };
 /* Collision models: LBGK (Eq. lbgk, Guo forcing), MRT (Eq. mrt_collision,
  * D3Q19), ELBM (Eqs. elbm and alpha_cond, exact-difference forcing),
  * regularized LBGK (Sec. 2.1.1: the non-equilibrium part is replaced by its
@@ -142,12 +144,13 @@ LBM_API int lbm_set_stream(lbm_handle h, void* cuda_stream);
 
 /* ---- geometry and parameters ------------------------------------------ */
 
-/* Node types (Sec. 3.4, simplified to one boundary kind): mask[n] = 0 fluid,
- * nonzero solid, nx*ny*nz bytes, dense.  Solid nodes are walls for half-way
- * bounce-back (Sec. 2.3): a population that would stream out of a solid node
- * is replaced by the opposite population of the receiving node.  Solid nodes
- * are not updated and report rho = 0, v = 0.  The data are copied.
- * Must precede lbm_init_equilibrium.  Default: no solid nodes. */
+/* Node types (Sec. 3.4): mask[n] = 0 fluid, 1 solid, 2 + k a boundary node
+ * of condition k (lbm_set_boundary, k = 0..14); nx*ny*nz bytes, dense, host
+ * or device.  Solid nodes are walls for half-way bounce-back (Sec. 2.3): a
+ * population that would stream out of a solid node is replaced by the
+ * opposite population of the receiving node.  Solid nodes are not updated
+ * and report rho = 0, v = 0.  The data are copied.  Values above 16 return
+ * LBM_EINVAL.  Must precede lbm_init_equilibrium.  Default: all fluid. */
 LBM_API int lbm_set_geometry(lbm_handle h, const uint8_t* mask);
 
 /* Uniform body force density F (lattice units), Sec. 2.4.  LBGK and MRT use
@@ -161,6 +164,30 @@ LBM_API int lbm_set_force(lbm_handle h, double fx, double fy, double fz);
  * my, mz.  q must be 19.  Default: 0 for conserved moments, 1/tau for the
  * five stress moments, 1.19, 1.4, 1.2, 1.4, 1.98 for the others. */
 LBM_API int lbm_set_mrt_rates(lbm_handle h, const double* s, int q);
+
+/* Velocity / pressure boundary condition `id` (0..14), used by the nodes
+ * whose mask value is 2 + id (Sec. 2.3 lists equilibrium, Zou-He and
+ * regularized conditions).  A boundary node is a fluid node; after
+ * streaming, its populations with e_i . n > 0 (n the inward normal: +-1 x,
+ * +-2 y, +-3 z) came from outside and are replaced before the collision:
+ *   rho (1 - v_n) = S_0 + 2 S_out - F_n / 2 gives the missing moment (S_0 and
+ *     S_out sum the populations with e.n = 0 and e.n < 0; the momentum is
+ *     j = rho v - F/2, so the node reports exactly v);
+ *   LBM_BC_VELOCITY: value = v (D components), rho from the relation;
+ *   LBM_BC_PRESSURE: value[0] = rho, v = v_n n from the relation;
+ *   LBM_BC_EQUILIBRIUM: f_i = f_eq_i(rho, v) - 3/2 w_i e_i . F;
+ *   LBM_BC_ZOUHE: unknown f_i = f_opp(i) + f_eq_i - f_eq_opp(i), the
+ *     remaining momentum to the normal link and, per tangential axis, evenly
+ *     to the shortest unknown links with that component (Zou & He on D2Q9,
+ *     its D3Q19 extension; the body diagonals on D3Q15);
+ *   LBM_BC_REGULARIZED: the same unknown f_i, then every population rebuilt
+ *     as f_eq + w_i 9/2 (e_i e_i - I/3) : Pi^neq - 3/2 w_i e_i . F.
+ * Set before lbm_step; LBM_EINVAL for a bad id, kind, method, normal or a
+ * non-finite value (rho must be > 0). */
+enum { LBM_BC_VELOCITY = 1, LBM_BC_PRESSURE = 2 };
+enum { LBM_BC_EQUILIBRIUM = 0, LBM_BC_ZOUHE = 1, LBM_BC_REGULARIZED = 2 };
+LBM_API int lbm_set_boundary(lbm_handle h, int id, int kind, int method, int normal,
+                             const double* value);
 
 /* Smagorinsky constant C_S of an LBM_SMAG handle (Eq. taut; default 0.1,
  * the value Sec. 2.1.4 gives for LB models).  C_S = 0 is plain LBGK.
@@ -406,13 +433,15 @@ enum { LBM_TRANSFER_STAGED = 0, LBM_TRANSFER_DIRECT = 1 };
 LBM_API int lbm_multi_set_transfer(lbm_multi m, int mode);
 /* Capture lbm_multi_step(n) as one CUDA graph (both streams) and replay it. */
 LBM_API int lbm_multi_set_graph(lbm_multi m, int on);
-/* As lbm_set_force / lbm_set_rounding / lbm_set_smagorinsky / lbm_set_elbm,
- * applied to every slab. */
+/* As lbm_set_force / lbm_set_rounding / lbm_set_smagorinsky / lbm_set_elbm /
+ * lbm_set_boundary, applied to every slab. */
 LBM_API int lbm_multi_set_force(lbm_multi m, double fx, double fy, double fz);
 LBM_API int lbm_multi_set_rounding(lbm_multi m, int mode);
 LBM_API int lbm_multi_set_smagorinsky(lbm_multi m, double cs);
 LBM_API int lbm_multi_set_elbm(lbm_multi m, int alpha_mode, double tol, int max_iter,
                                double skip_eps);
+LBM_API int lbm_multi_set_boundary(lbm_multi m, int id, int kind, int method, int normal,
+                                   const double* value);
 /* Whole-domain mask and initial fields, laid out as for lbm_set_geometry and
  * lbm_init_equilibrium (host or device); each slab takes its rows plus the
  * neighbouring row on each side. */

@@ -12,6 +12,7 @@ import glob
 import os
 import shutil
 import subprocess
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -19,17 +20,23 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# The single-domain LBGK kernels and the batched ensemble must evaluate the
-# same sequence of IEEE operations so that a batched domain is bitwise equal
-# to the same domain run alone: no multiply-add contraction in those units
-# (both are HBM-bound; the extra ALU work is free).
 # Every translation unit holding a stream-and-collide kernel is compiled
 # without multiply-add contraction: the kernels write their fused operations
-# explicitly, so the AB and AA instances, the batched kernel and the
-# single-domain kernel apply the same operation sequence and agree bitwise.
+# explicitly, so the AB and AA instances, the batched kernel, subdomain runs
+# and the single-domain kernel apply the same operation sequence and agree
+# bitwise.
 NO_CONTRACT = ["-fmad=false"]
-PER_FILE = {f: NO_CONTRACT for f in ("k_bgk.cu", "k_mrt.cu", "k_elbm2.cu", "k_elbm3.cu",
-                                      "k_les.cu", "k_batch.cu")}
+PER_FILE = {f: NO_CONTRACT for f in ("k_bgk.cu", "k_bgk_q15q27.cu", "k_mrt.cu", "k_elbm.cu",
+                                      "k_les.cu", "k_les_q15q27.cu", "k_batch.cu")}
+# Sources compiled into several objects, each with its own defines: the ELBM
+# kernels, once per lattice code (0 D2Q9, 1 D3Q19, 2 D3Q15, 3 D3Q27) and
+# storage group ({F64}, {F32, F32S}, {F16S, BF16S}), so that they build in
+# parallel.
+VARIANTS = {"k_elbm.cu": [(f"_l{lat}_s{st}", [f"-DELBM_LAT={lat}", f"-DELBM_STORES={st}u"])
+                          for lat in (3, 1, 2, 0) for st in (1, 6, 24)]}
+# compile the slowest units first
+COST = {"k_elbm.cu": 9, "k_les_q15q27.cu": 5, "k_les.cu": 4, "k_bgk_q15q27.cu": 3,
+        "k_mrt.cu": 3, "k_bgk.cu": 2, "k_support.cu": 2}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-fvisibility=hidden", "--ftz=false", "--prec-div=true",
          "--prec-sqrt=true", "-I", INCLUDE, "-I", CSRC]
@@ -56,28 +63,30 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     objs = []
     todo = []
     for src in srcs:
-        obj = os.path.join(LIBDIR, "obj", os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
-            todo.append((src, obj))
+        base = os.path.basename(src)[:-3]
+        for suffix, defs in VARIANTS.get(os.path.basename(src), [("", [])]):
+            obj = os.path.join(LIBDIR, "obj", base + suffix + ".o")
+            objs.append(obj)
+            if not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
+                todo.append((src, obj, defs))
 
     def compile_one(item):
-        src, obj = item
-        cmd = [nvcc, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), "-c", src, "-o",
-               obj + ".tmp"]
+        src, obj, defs = item
+        t0 = time.time()
+        cmd = [nvcc, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), *defs, "-c", src,
+               "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
         os.replace(obj + ".tmp", obj)
-        return src
+        return obj, time.time() - t0
 
     if todo:
-        # biggest translation units first
-        todo.sort(key=lambda it: -os.path.getsize(it[0]))
+        todo.sort(key=lambda it: -COST.get(os.path.basename(it[0]), 0))
         with cf.ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
-            for src in ex.map(compile_one, todo):
+            for obj, dt in ex.map(compile_one, todo):
                 if verbose:
-                    print("compiled", os.path.basename(src))
+                    print(f"compiled {os.path.basename(obj)} in {dt:.0f} s")
     if todo or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl",

@@ -25,7 +25,10 @@ namespace lbm {
 // time (1.2e-5 relative after 1000 steps of the 256^3 vortex); with exact
 // sums only incoherent per-element rounding is left.  The pairs used are
 // exactly representable: on D3Q19 b_diag = fl(1/12), b_axis = (1 - 8 b_diag)/2;
-// on D2Q9 b_axis = fl(1/3), b_diag = (1 - 2 b_axis)/4 (Sterbenz subtractions).
+// on D2Q9 b_axis = fl(1/3), b_diag = (1 - 2 b_axis)/4 (Sterbenz subtractions);
+// on D3Q15 b_axis = fl(1/3), b_corner = (1 - 2 b_axis)/8; on D3Q27
+// b_axis = fl(2/9), b_edge = fl(1/18), b_corner = (1 - (2 b_axis + 8 b_edge))/8
+// (in that order of evaluation, exact in FP32 and FP64).
 // ---------------------------------------------------------------------------
 template <class L, class R>
 __host__ __device__ constexpr R first_order_coef(int i)
@@ -34,6 +37,14 @@ __host__ __device__ constexpr R first_order_coef(int i)
     if (L::Q == 19) {
         constexpr R bd = R(1.0 / 12.0);
         return i < 7 ? (R(1) - R(8) * bd) / R(2) : bd;
+    }
+    if (L::Q == 15) {                       // 2 b_axis + 8 b_corner = 1
+        constexpr R ba = R(1.0 / 3.0);
+        return i < 7 ? ba : (R(1) - R(2) * ba) / R(8);
+    }
+    if (L::Q == 27) {                       // 2 b_axis + 8 b_edge + 8 b_corner = 1
+        constexpr R ba = R(2.0 / 9.0), be = R(1.0 / 18.0);
+        return i < 7 ? ba : (i < 19 ? be : (R(1) - (R(2) * ba + R(8) * be)) / R(8));
     }
     constexpr R ba = R(1.0 / 3.0);
     return i < 5 ? ba : (R(1) - R(2) * ba) / R(4);
@@ -289,6 +300,145 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
         }
     }
     rho_out = rho;
+}
+
+// ---------------------------------------------------------------------------
+// Velocity and pressure boundary nodes (Sec. 2.3: equilibrium, Zou-He and
+// regularized conditions).  Applied to the post-streaming deviations of a
+// node marked with a condition, before its collision.  With n the inward
+// normal, the populations with e_i . n > 0 came from outside and are unknown.
+// The known ones fix the missing moment through
+//   rho (1 - v_n) = S_0 + 2 S_out - F_n / 2
+// (S_0: e.n = 0, S_out: e.n < 0; momentum j = rho v - F/2 as in Guo's scheme,
+// so the collision reports exactly v).  Velocity condition: v given; pressure
+// condition: rho given, v = v_n n.  Then, with f_eq at (rho, v):
+//  equilibrium: f_i = f_eq_i - 3/2 w_i e_i . F;
+//  Zou-He: unknown f_i = f_opp(i) + f_eq_i - f_eq_opp(i), and the momentum
+//    still missing goes to the link along n (normal part) and, per tangential
+//    axis t, evenly with sign e_it to the unknown links of smallest length
+//    with e_it != 0 (two edge links; the four body diagonals on D3Q15);
+//  regularized: unknown f_i as Zou-He before the correction, then
+//    f_i = f_eq_i + w_i 9/2 (e_i e_i - I/3) : Pi^neq - 3/2 w_i e_i . F.
+// Rare nodes: plain f-form arithmetic in the compute type.
+// ---------------------------------------------------------------------------
+template <class L, class R>
+__device__ __forceinline__ void bc_apply(R (&d)[L::Q], const BCEntry& b, R F0, R F1, R F2)
+{
+    constexpr int Q = L::Q, D = L::D;
+    // the normal's axis is a run-time value: components are picked with
+    // selects (no run-time indexed arrays, which would live in local memory)
+    const int ax = b.axis, sg = b.sign;
+    auto pick = [ax](R c0, R c1, R c2) { return ax == 0 ? c0 : (ax == 1 ? c1 : c2); };
+    R f[Q];
+    R S0 = R(0), So = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        f[i] = (R)L::w(i) + d[i];
+        const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
+        if (en == 0) S0 += f[i];
+        else if (en < 0) So += f[i];
+    }
+    const R Fax = pick(F0, F1, F2);
+    const R Fn = sg > 0 ? Fax : -Fax;
+    const R known = fma(R(2), So, S0) - R(0.5) * Fn;
+    R rho, v0, v1, v2;
+    if (b.kind == 1) {
+        v0 = sel<R>(b.val_f[0], b.val[0]);
+        v1 = sel<R>(b.val_f[1], b.val[1]);
+        v2 = D == 3 ? sel<R>(b.val_f[2], b.val[2]) : R(0);
+        const R vax = pick(v0, v1, v2);
+        rho = known / (R(1) - (sg > 0 ? vax : -vax));
+    } else {
+        rho = sel<R>(b.val_f[0], b.val[0]);
+        const R vn = R(1) - known / rho;
+        const R va = sg > 0 ? vn : -vn;
+        v0 = ax == 0 ? va : R(0);
+        v1 = ax == 1 ? va : R(0);
+        v2 = ax == 2 ? va : R(0);
+    }
+    const R usq = fma(v0, v0, fma(v1, v1, v2 * v2));
+    R feq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R eu = edot<L, R>(i, v0, v1, v2);
+        feq[i] = (R)L::w(i) * rho *
+                 fma(R(3), eu, fma(R(4.5) * eu, eu, fma(R(-1.5), usq, R(1))));
+    }
+    if (b.method == 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            f[i] = fma(R(-1.5) * (R)L::w(i), edot<L, R>(i, F0, F1, F2), feq[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
+            if (en > 0) f[i] = f[L::opp(i)] + (feq[i] - feq[L::opp(i)]);
+        }
+        if (b.method == 1) {
+            R J0 = R(0), J1 = R(0), J2 = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (L::ex(i)) J0 = L::ex(i) > 0 ? J0 + f[i] : J0 - f[i];
+                if (L::ey(i)) J1 = L::ey(i) > 0 ? J1 + f[i] : J1 - f[i];
+                if (L::ez(i)) J2 = L::ez(i) > 0 ? J2 + f[i] : J2 - f[i];
+            }
+            const R dJ0 = fma(rho, v0, R(-0.5) * F0) - J0;
+            const R dJ1 = fma(rho, v1, R(-0.5) * F1) - J1;
+            const R dJ2 = D == 3 ? fma(rho, v2, R(-0.5) * F2) - J2 : R(0);
+            const R dJn = pick(dJ0, dJ1, dJ2);
+            constexpr int tlen = (Q == 15) ? 3 : 2;      // shortest unknown links with e_t != 0
+            constexpr R tshare = (Q == 15) ? R(0.25) : R(0.5);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
+                if (en <= 0) continue;
+                const int l2 = L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
+                if (l2 == 1) f[i] += sg > 0 ? dJn : -dJn;      // the link along n
+                if (l2 == tlen) {
+                    if (L::ex(i) && ax != 0) f[i] = fma(L::ex(i) > 0 ? tshare : -tshare, dJ0, f[i]);
+                    if (L::ey(i) && ax != 1) f[i] = fma(L::ey(i) > 0 ? tshare : -tshare, dJ1, f[i]);
+                    if (L::ez(i) && ax != 2) f[i] = fma(L::ez(i) > 0 ? tshare : -tshare, dJ2, f[i]);
+                }
+            }
+        } else {
+            // Hermite coefficient a2 = sum (f - f_eq)(e e - I/3): the node's
+            // mass defect m = sum (f - f_eq) (F_n/2 under a force) enters the
+            // diagonal
+            R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const R nq = f[i] - feq[i];
+                const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+                m += nq;
+                if (ex) P[0] += nq;
+                if (ey) P[1] += nq;
+                if (ez) P[2] += nq;
+                if (ex && ey) P[3] = (ex * ey > 0) ? P[3] + nq : P[3] - nq;
+                if (ex && ez) P[4] = (ex * ez > 0) ? P[4] + nq : P[4] - nq;
+                if (ey && ez) P[5] = (ey * ez > 0) ? P[5] + nq : P[5] - nq;
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) P[a] = fma(R(-1.0 / 3.0), m, P[a]);
+            const R tr3 = (P[0] + P[1] + P[2]) * R(1.0 / 3.0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+                R ePe = R(0);
+                if (ex) ePe += P[0];
+                if (ey) ePe += P[1];
+                if (ez) ePe += P[2];
+                if (ex && ey) ePe = (ex * ey > 0) ? fma(R(2), P[3], ePe) : fma(R(-2), P[3], ePe);
+                if (ex && ez) ePe = (ex * ez > 0) ? fma(R(2), P[4], ePe) : fma(R(-2), P[4], ePe);
+                if (ey && ez) ePe = (ey * ez > 0) ? fma(R(2), P[5], ePe) : fma(R(-2), P[5], ePe);
+                const R wi = (R)L::w(i);
+                f[i] = fma(R(4.5) * wi, ePe - tr3,
+                           fma(R(-1.5) * wi, edot<L, R>(i, F0, F1, F2), feq[i]));
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = f[i] - (R)L::w(i);
 }
 
 // ---------------------------------------------------------------------------

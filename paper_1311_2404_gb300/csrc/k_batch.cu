@@ -130,8 +130,8 @@ __device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams&
     bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
     if constexpr (S::kHalf) {
         if (!bp.round_nearest) {
-            store_node_sr<L, S>(B, d, (unsigned)n * kSaltNode,
-                                [&](int i) -> size_t { return (size_t)i * D.sq + n; });
+            store_node_sr<L, S>(d, (unsigned)n * kSaltNode,
+                                [&](int i) { return B + (size_t)i * D.sq + n; });
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
@@ -450,11 +450,17 @@ int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask)
     BCK(b, cudaMemcpyAsync(stage, mask, n, dev_ptr(mask) ? cudaMemcpyDeviceToDevice
                                                          : cudaMemcpyHostToDevice, b->stream),
         "copy mask");
-    BCK(b, launch_flags(0, stage, reinterpret_cast<uint8_t*>(b->base + D.offF), D.nx, D.ny, 1,
-                        D.nxp, b->stream),
+    int* bad = reinterpret_cast<int*>(b->base + b->off_bar + 32);
+    BCK(b, cudaMemsetAsync(bad, 0, sizeof(int), b->stream), "clear mask check");
+    BCK(b, launch_flags(0, stage, reinterpret_cast<uint8_t*>(b->base + D.offF), nullptr, D.nx,
+                        D.ny, 1, D.nxp, 1, bad, b->stream),
         "node-type map kernel");
     b->launches += 1;
+    int hbad = 0;
+    BCK(b, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+        "read mask check");
     BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
+    if (hbad) return bfail(b, LBM_EINVAL, "batch masks take 0 (fluid) and 1 (solid) only");
     b->has_mask[d] = 1;
     return LBM_OK;
 }

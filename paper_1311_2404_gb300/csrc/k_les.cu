@@ -6,11 +6,11 @@ namespace lbm {
 cudaError_t launch_step_reg(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s)
 {
-    return launch_step_model<MODEL_REG>(lattice, store, p, mask, aa, s);
+    return launch_step_model<MODEL_REG, 3u>(lattice, store, p, mask, aa, s);
 }
 cudaError_t launch_step_smag(int lattice, int store, const StepParams& p, bool mask, bool aa,
                              cudaStream_t s)
 {
-    return launch_step_model<MODEL_SMAG>(lattice, store, p, mask, aa, s);
+    return launch_step_model<MODEL_SMAG, 3u>(lattice, store, p, mask, aa, s);
 }
 }  // namespace lbm

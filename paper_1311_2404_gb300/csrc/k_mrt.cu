@@ -5,6 +5,6 @@ namespace lbm {
 cudaError_t launch_step_mrt(int lattice, int store, const StepParams& p, bool mask, bool aa,
                            cudaStream_t s)
 {
-    return launch_step_model<MODEL_MRT>(lattice, store, p, mask, aa, s);
+    return launch_step_model<MODEL_MRT, 2u>(lattice, store, p, mask, aa, s);
 }
 }  // namespace lbm

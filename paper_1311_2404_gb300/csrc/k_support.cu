@@ -6,13 +6,18 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------
-// Node-type map (Sec. 3.4, reduced to fluid / solid): bit 0 solid, bit 1 a
+// Node-type map (Sec. 3.4): from the caller's mask (0 fluid, 1 solid, 2 + k a
+// boundary node of condition k) to one byte per node: bit 0 solid, bit 1 a
 // fluid node with at least one solid upstream neighbour (the only nodes that
-// need the bounce-back check).  dense: [nz][ny][nx]; flags: padded rows.
+// need the bounce-back check), bits 2..5 condition id + 1; and for every node
+// a link mask, bit i set when the upstream node x - e_i is solid (links may be
+// NULL).  A mask value above max_code sets *bad.  dense: [nz][ny][nx];
+// flags and links: padded rows.
 // ---------------------------------------------------------------------------
 template <class L>
-__global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__ flags, int nx,
-                        int ny, int nz, int nxp)
+__global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__ flags,
+                        uint32_t* __restrict__ links, int nx, int ny, int nz, int nxp,
+                        int max_code, int* __restrict__ bad)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -21,29 +26,44 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__
     const size_t out = ((size_t)z * ny + y) * nxp + x;
     if (x >= nx) {
         flags[out] = FLAG_SOLID;  // padding never updates
+        if (links) links[out] = 0;
         return;
     }
     auto at = [&](int xx, int yy, int zz) {
         xx = (xx + nx) % nx;
         yy = (yy + ny) % ny;
         zz = (zz + nz) % nz;
-        return dense[((size_t)zz * ny + yy) * nx + xx] != 0;
+        return dense[((size_t)zz * ny + yy) * nx + xx];
     };
-    const bool solid = at(x, y, z);
-    bool near = false;
+    const int code = at(x, y, z);
+    if (code > max_code) {
+        atomicOr(bad, 1);
+        flags[out] = FLAG_SOLID;
+        if (links) links[out] = 0;
+        return;
+    }
+    const bool solid = code == 1;
+    uint32_t lk = 0;
     if (!solid)
-        for (int i = 1; i < L::Q; ++i) near |= at(x - L::ex(i), y - L::ey(i), z - L::ez(i));
-    flags[out] = (solid ? FLAG_SOLID : 0) | (near ? FLAG_NEAR_WALL : 0);
+        for (int i = 1; i < L::Q; ++i)
+            if (at(x - L::ex(i), y - L::ey(i), z - L::ez(i)) == 1) lk |= 1u << i;
+    const bool near = lk != 0;
+    if (links) links[out] = lk;
+    flags[out] = (solid ? FLAG_SOLID : 0) | (near ? FLAG_NEAR_WALL : 0) |
+                 (code >= 2 ? ((code - 1) << FLAG_BC_SHIFT) : 0);
 }
 
-cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, int nx, int ny,
-                         int nz, int nxp, cudaStream_t s)
+cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, uint32_t* links,
+                         int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s)
 {
     dim3 block(128), grid((nxp + 127) / 128, ny, nz);
-    if (lattice == 0)
-        k_flags<D2Q9><<<grid, block, 0, s>>>(dense, flags, nx, ny, nz, nxp);
-    else
-        k_flags<D3Q19><<<grid, block, 0, s>>>(dense, flags, nx, ny, nz, nxp);
+    switch (lattice) {
+    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
+    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
+    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
+    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -128,11 +148,17 @@ cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, 
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s)
 {
-    if (lattice == 0)
-        return init_l<D2Q9>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
-                            feq_variant, opposite_slots, s);
-    return init_l<D3Q19>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic, feq_variant,
-                         opposite_slots, s);
+    switch (lattice) {
+    case 0: return init_l<D2Q9>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
+                                feq_variant, opposite_slots, s);
+    case 1: return init_l<D3Q19>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
+                                 feq_variant, opposite_slots, s);
+    case 2: return init_l<D3Q15>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
+                                 feq_variant, opposite_slots, s);
+    case 3: return init_l<D3Q27>(store, rho, u, field_f32, A, nx, ny, nz, nxp, sq, entropic,
+                                 feq_variant, opposite_slots, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------

@@ -41,7 +41,8 @@ struct lbm_ctx {
     size_t bytes = 0;
     bool owned = false;
     size_t off_A = 0, off_B = 0, off_flags = 0, off_rho = 0, off_u = 0, off_alpha = 0,
-           off_misc = 0, off_part = 0, off_mlp = 0, off_stage = 0, stage_bytes = 0;
+           off_misc = 0, off_part = 0, off_mlp = 0, off_stage = 0, stage_bytes = 0,
+           off_links = 0;
     int cur = 0;            // 0: state in A, 1: state in B
     bool has_mask = false, inited = false, have_out = false;
     cudaStream_t stream = nullptr;
@@ -50,6 +51,7 @@ struct lbm_ctx {
     int alpha_mode = LBM_ALPHA_NEWTON, max_iter = 20, guard_steps = 2, feq_variant = 0;
     double tol = 1e-12, skip_eps = 1e-3, guard_tol = 1e-6;
     double smag_cs = 0.1;   // Smagorinsky constant C_S
+    BCEntry bc[kMaxBC] = {};  // velocity / pressure boundary conditions by id
     bool mlp_loaded = false, alpha_out = false, use_graph = false, round_nearest = false;
     bool aa = false;        // AA access pattern (one distribution array)
     long long t = 0, launches = 0;
@@ -61,6 +63,7 @@ struct lbm_ctx {
 enum : size_t {
     MISC_STATUS = 0,        // uint32 status bits
     MISC_PAIRS = 8,         // int pairs counter
+    MISC_BAD = 16,          // int: mask value out of range
     MISC_RED = 64,          // 5 doubles reduction result
     MISC_CTR_OUT = 128,     // 6 doubles summed counters
     MISC_CTR = 256,         // 64 x 8 unsigned long long counter replicas
@@ -131,6 +134,7 @@ static void layout(lbm_ctx* h)
     h->off_B = o;
     if (!h->aa) o = align256(o + dist);   // AA: a single array
     h->off_flags = o; o = align256(o + (size_t)h->sq);
+    h->off_links = o; o = align256(o + (size_t)h->sq * 4);
     h->off_rho = o; o = align256(o + (size_t)h->sq * h->rsize);
     h->off_u = o; o = align256(o + (size_t)h->D * h->sq * h->rsize);
     h->off_alpha = o;
@@ -185,6 +189,17 @@ static int sync_status(lbm_ctx* h)
     return LBM_OK;
 }
 
+template <int LAT>
+static cudaError_t elbm_dispatch(int store, const StepParams& p, bool mask, bool aa,
+                                 cudaStream_t s)
+{
+    switch (kElbmStoreGroup[store]) {
+    case 1u: return launch_step_elbm_part<LAT, 1u>(store, p, mask, aa, s);
+    case 6u: return launch_step_elbm_part<LAT, 6u>(store, p, mask, aa, s);
+    default: return launch_step_elbm_part<LAT, 24u>(store, p, mask, aa, s);
+    }
+}
+
 extern "C" {
 
 int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
@@ -194,7 +209,8 @@ int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int d
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1)
         return fail(nullptr, LBM_EINVAL, "sizes must be >= 1 (got %d x %d x %d)", nx, ny, nz);
-    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q15 &&
+        lattice != LBM_D3Q27)
         return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lattice);
     if (lattice == LBM_D2Q9 && nz != 1)
         return fail(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1 (got %d)", nz);
@@ -216,7 +232,7 @@ int lbm_create(int nx, int ny, int nz, int lattice, int model, double tau, int d
     h->nx = nx; h->ny = ny; h->nz = nz;
     h->lattice = lattice; h->model = model; h->dtype = dtype; h->tau = tau;
     h->D = lattice == LBM_D2Q9 ? 2 : 3;
-    h->Q = lattice == LBM_D2Q9 ? 9 : 19;
+    h->Q = lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : (lattice == LBM_D3Q15 ? 15 : 27));
     h->nxp = (int)nxp;
     h->sq = sq;
     h->N = (long long)nx * ny * nz;
@@ -277,11 +293,17 @@ int lbm_set_geometry(lbm_handle h, const uint8_t* mask)
     CK(h, cudaMemcpyAsync(stage, mask, (size_t)h->N,
                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
        "copy mask");
-    CK(h, launch_flags(h->lattice, stage, at<uint8_t>(h, h->off_flags), h->nx, h->ny, h->nz,
-                       h->nxp, h->stream),
+    int* bad = at<int>(h, h->off_misc + MISC_BAD);
+    CK(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream), "clear mask check");
+    CK(h, launch_flags(h->lattice, stage, at<uint8_t>(h, h->off_flags), at<uint32_t>(h, h->off_links),
+                       h->nx, h->ny, h->nz, h->nxp, 1 + kMaxBC, bad, h->stream),
        "node-type map kernel");
     h->launches += 1;
+    int hbad = 0;
+    CK(h, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+       "read mask check");
     CK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    if (hbad) return fail(h, LBM_EINVAL, "mask values are 0, 1 or 2..%d", 1 + kMaxBC);
     h->has_mask = true;
     return LBM_OK;
 }
@@ -305,6 +327,36 @@ int lbm_set_mrt_rates(lbm_handle h, const double* s, int q)
     for (int k = 0; k < 19; ++k) {
         if (!std::isfinite(s[k])) return fail(h, LBM_EINVAL, "rate %d not finite", k);
         h->s[k] = s[k];
+    }
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_set_boundary(lbm_handle h, int id, int kind, int method, int normal,
+                     const double* value)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (id < 0 || id >= kMaxBC) return fail(h, LBM_EINVAL, "condition id must be 0..%d", kMaxBC - 1);
+    if (kind != LBM_BC_VELOCITY && kind != LBM_BC_PRESSURE)
+        return fail(h, LBM_EINVAL, "unknown condition kind %d", kind);
+    if (method != LBM_BC_EQUILIBRIUM && method != LBM_BC_ZOUHE && method != LBM_BC_REGULARIZED)
+        return fail(h, LBM_EINVAL, "unknown condition method %d", method);
+    const int ax = normal < 0 ? -normal - 1 : normal - 1;
+    if (normal == 0 || ax >= h->D)
+        return fail(h, LBM_EINVAL, "normal must be +-1..+-%d (got %d)", h->D, normal);
+    if (!value) return fail(h, LBM_EINVAL, "value is NULL");
+    const int nv = kind == LBM_BC_VELOCITY ? h->D : 1;
+    for (int a = 0; a < nv; ++a)
+        if (!std::isfinite(value[a])) return fail(h, LBM_EINVAL, "value must be finite");
+    if (kind == LBM_BC_PRESSURE && !(value[0] > 0)) return fail(h, LBM_EINVAL, "rho must be > 0");
+    BCEntry& b = h->bc[id];
+    b.kind = kind;
+    b.method = method;
+    b.axis = ax;
+    b.sign = normal > 0 ? 1 : -1;
+    for (int a = 0; a < 3; ++a) {
+        b.val[a] = a < nv ? value[a] : 0.0;
+        b.val_f[a] = (float)b.val[a];
     }
     drop_graphs(h);
     return LBM_OK;
@@ -454,6 +506,7 @@ static StepParams make_params(lbm_ctx* h)
     StepParams p;
     std::memset(&p, 0, sizeof p);
     p.flags = h->has_mask ? at<uint8_t>(h, h->off_flags) : nullptr;
+    p.links = h->has_mask ? at<uint32_t>(h, h->off_links) : nullptr;
     p.rho = h->base + h->off_rho;
     p.u = h->base + h->off_u;
     p.alpha_out = (h->model == LBM_ELBM && h->alpha_out) ? at<double>(h, h->off_alpha) : nullptr;
@@ -478,6 +531,7 @@ static StepParams make_params(lbm_ctx* h)
     }
     p.omega_f = (float)p.omega;
     p.tau = h->tau;
+    for (int k = 0; k < kMaxBC; ++k) p.bc[k] = h->bc[k];
     p.smag_cs2 = h->smag_cs * h->smag_cs;
     p.tau_f = (float)p.tau;
     p.smag_cs2_f = (float)p.smag_cs2;
@@ -503,15 +557,33 @@ static cudaError_t launch_one(lbm_ctx* h, StepParams& p, int from, bool out)
         p.B = h->base + (from == 0 ? h->off_B : h->off_A);
         p.aa_pushpull = 0;
     }
+    for (int i = 0; i < h->Q; ++i) {
+        p.Ap[i] = static_cast<const char*>(p.A) + (size_t)i * h->sq * h->esize;
+        p.Bp[i] = static_cast<char*>(p.B) + (size_t)i * h->sq * h->esize;
+    }
     p.out = out ? 1 : 0;
     const bool mask = h->has_mask;
     const bool aa = h->aa;
-    if (h->model == LBM_BGK) return launch_step_bgk(h->lattice, h->dtype, p, mask, aa, h->stream);
-    if (h->model == LBM_MRT) return launch_step_mrt(h->lattice, h->dtype, p, mask, aa, h->stream);
-    if (h->model == LBM_REG) return launch_step_reg(h->lattice, h->dtype, p, mask, aa, h->stream);
-    if (h->model == LBM_SMAG) return launch_step_smag(h->lattice, h->dtype, p, mask, aa, h->stream);
-    if (h->lattice == LBM_D2Q9) return launch_step_elbm2(h->dtype, p, mask, aa, h->stream);
-    return launch_step_elbm3(h->dtype, p, mask, aa, h->stream);
+    const int lat = h->lattice;
+    const bool ext = lat == LBM_D3Q15 || lat == LBM_D3Q27;   // built in separate units
+    switch (h->model) {
+    case LBM_BGK:
+        return ext ? launch_step_bgk_q15q27(lat, h->dtype, p, mask, aa, h->stream)
+                   : launch_step_bgk(lat, h->dtype, p, mask, aa, h->stream);
+    case LBM_MRT: return launch_step_mrt(lat, h->dtype, p, mask, aa, h->stream);
+    case LBM_REG:
+        return ext ? launch_step_reg_q15q27(lat, h->dtype, p, mask, aa, h->stream)
+                   : launch_step_reg(lat, h->dtype, p, mask, aa, h->stream);
+    case LBM_SMAG:
+        return ext ? launch_step_smag_q15q27(lat, h->dtype, p, mask, aa, h->stream)
+                   : launch_step_smag(lat, h->dtype, p, mask, aa, h->stream);
+    }
+    switch (lat) {
+    case LBM_D2Q9: return elbm_dispatch<0>(h->dtype, p, mask, aa, h->stream);
+    case LBM_D3Q19: return elbm_dispatch<1>(h->dtype, p, mask, aa, h->stream);
+    case LBM_D3Q15: return elbm_dispatch<2>(h->dtype, p, mask, aa, h->stream);
+    default: return elbm_dispatch<3>(h->dtype, p, mask, aa, h->stream);
+    }
 }
 
 static int check_step_ready(lbm_ctx* h)
@@ -772,7 +844,7 @@ struct lbm_multi_ctx {
     std::vector<int> lo, hi;
     std::vector<lbm_ctx*> sub;
     int ndir = 0;
-    int dir_up[9], dir_dn[9];    // directions with +1 / -1 along the decomposed axis
+    int dir_up[9], dir_dn[9];    // directions with +1 / -1 along the decomposed axis (<= 9)
     bool overlap = true, use_graph = false, inited = false;
     bool direct = false;         // one kernel stores into the neighbour's ghost row
     cudaStream_t stream = nullptr, comm = nullptr;
@@ -1003,7 +1075,10 @@ int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau,
     // directions with a +1 / -1 component along the decomposed axis
     int ndn = 0;
     for (int i = 0; i < m->Q; ++i) {
-        const int e = D == 3 ? D3Q19::ez(i) : D2Q9::ey(i);
+        const int e = lattice == LBM_D2Q9    ? D2Q9::ey(i)
+                      : lattice == LBM_D3Q19 ? D3Q19::ez(i)
+                      : lattice == LBM_D3Q15 ? D3Q15::ez(i)
+                                             : D3Q27::ez(i);
         if (e == 1) m->dir_up[m->ndir++] = i;
         if (e == -1) m->dir_dn[ndn++] = i;
     }
@@ -1122,6 +1197,18 @@ int lbm_multi_set_smagorinsky(lbm_multi m, double cs)
     if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
     for (auto* h : m->sub) {
         int r = lbm_set_smagorinsky(h, cs);
+        if (r) return msub(m, h, r);
+    }
+    mdrop_graphs(m);
+    return LBM_OK;
+}
+
+int lbm_multi_set_boundary(lbm_multi m, int id, int kind, int method, int normal,
+                           const double* value)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    for (auto* h : m->sub) {
+        int r = lbm_set_boundary(h, id, kind, method, normal, value);
         if (r) return msub(m, h, r);
     }
     mdrop_graphs(m);

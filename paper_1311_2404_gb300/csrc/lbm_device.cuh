@@ -60,6 +60,77 @@ struct D3Q19 {
     }
 };
 
+// D3Q15: rest, three axis pairs, four body-diagonal pairs.
+struct D3Q15 {
+    static constexpr int D = 3, Q = 15;
+    __host__ __device__ static constexpr int ex(int i) {
+        constexpr int t[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        constexpr int t[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        constexpr int t[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+// D3Q27: the D3Q19 set (same order) followed by four body-diagonal pairs.
+struct D3Q27 {
+    static constexpr int D = 3, Q = 27;
+    __host__ __device__ static constexpr int ex(int i) {
+        constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0,
+                               1, -1, 1, -1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1,
+                               1, -1, 1, -1, -1, 1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1,
+                               1, -1, -1, 1, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 8.0 / 27.0 : (i < 7 ? 2.0 / 27.0 : (i < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+};
+
+// Compile-time checks of a velocity set: rest first, opposite pairs
+// (2k+1, 2k+2), zero mean velocity, links of each length counted.
+template <class L>
+__host__ __device__ constexpr bool lattice_ok(int n1, int n2, int n3)
+{
+    if (L::ex(0) || L::ey(0) || L::ez(0)) return false;
+    int c[4] = {1, 0, 0, 0}, sx = 0, sy = 0, sz = 0;
+    for (int i = 1; i < L::Q; ++i) {
+        const int o = L::opp(i);
+        if (L::ex(o) != -L::ex(i) || L::ey(o) != -L::ey(i) || L::ez(o) != -L::ez(i)) return false;
+        c[L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i)] += 1;
+        sx += L::ex(i); sy += L::ey(i); sz += L::ez(i);
+        for (int k = 1; k < i; ++k)
+            if (L::ex(k) == L::ex(i) && L::ey(k) == L::ey(i) && L::ez(k) == L::ez(i)) return false;
+    }
+    return sx == 0 && sy == 0 && sz == 0 && c[1] == n1 && c[2] == n2 && c[3] == n3;
+}
+static_assert(lattice_ok<D2Q9>(4, 4, 0), "D2Q9 table");
+static_assert(lattice_ok<D3Q15>(6, 0, 8), "D3Q15 table");
+static_assert(lattice_ok<D3Q19>(6, 12, 0), "D3Q19 table");
+static_assert(lattice_ok<D3Q27>(6, 12, 8), "D3Q27 table");
+
 // ---------------------------------------------------------------------------
 // Storage codecs.  load() returns the deviation d = f - w in the compute type
 // R; store() takes it back.  *_S codecs keep d itself (Sec. 3.7 round-off
@@ -137,6 +208,13 @@ struct StoreF16S {
     }
     __device__ static T hi(unsigned pk) { return __ushort_as_half((unsigned short)(pk >> 16)); }
     __device__ static T lo(unsigned pk) { return __ushort_as_half((unsigned short)(pk & 0xffffu)); }
+    // two x-adjacent nodes (p 4-byte aligned): the lower address first
+    __device__ static void load2(const T* p, R& a, R& b)
+    {
+        const __half2 h = __ldg(reinterpret_cast<const __half2*>(p));
+        a = __low2float(h);
+        b = __high2float(h);
+    }
 };
 struct StoreBF16S {
     using T = __nv_bfloat16;
@@ -160,23 +238,30 @@ struct StoreBF16S {
     {
         return __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
     }
+    __device__ static void load2(const T* p, R& a, R& b)
+    {
+        const __nv_bfloat162 h = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+        a = __low2float(h);
+        b = __high2float(h);
+    }
 };
 
 // Stochastically rounded stores of one node's q deviations (half-width
 // codecs): opposite directions (2k+1, 2k+2) share one conversion, the rest
-// population pairs with itself.  dst(i) is the element index of direction i.
+// population pairs with itself.  dst(i) is the address of direction i.  Each
+// value's random field comes from its own hash, so the rounding of a value
+// does not depend on which value it is paired with or in which half it sits.
 template <class L, class S, class F>
-__device__ __forceinline__ void store_node_sr(typename S::T* B, const float (&d)[L::Q],
-                                              unsigned salt, F dst)
+__device__ __forceinline__ void store_node_sr(const float (&d)[L::Q], unsigned salt, F dst)
 {
-    B[dst(0)] = S::hi(S::encode_pair(d[0], d[0], salt, salt ^ 0x5bd1e995u));
+    *dst(0) = S::hi(S::encode_pair(d[0], d[0], salt, salt ^ 0x5bd1e995u));
 #pragma unroll
     for (int k = 0; k < (L::Q - 1) / 2; ++k) {
         const int i = 2 * k + 1, j = i + 1;
         const unsigned pk = S::encode_pair(d[i], d[j], salt + (unsigned)i * kSaltDir,
                                            salt + (unsigned)j * kSaltDir);
-        B[dst(i)] = S::hi(pk);
-        B[dst(j)] = S::lo(pk);
+        *dst(i) = S::hi(pk);
+        *dst(j) = S::lo(pk);
     }
 }
 
@@ -184,7 +269,20 @@ __device__ __forceinline__ void store_node_sr(typename S::T* B, const float (&d)
 // Kernel parameters (passed by value).
 // ---------------------------------------------------------------------------
 enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2, MODEL_REG = 3, MODEL_SMAG = 4 };
-enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2 };
+// node-type byte: bit 0 solid, bit 1 fluid with a solid upstream neighbour,
+// bits 2..5 boundary condition id + 1 (0: none)
+enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2, FLAG_BC_SHIFT = 2, FLAG_BC_MASK = 0x3c };
+constexpr int kMaxBC = 15;
+
+// One velocity or pressure boundary condition (Sec. 2.3's list).
+struct BCEntry {
+    int kind;          // 1 velocity, 2 pressure
+    int method;        // 0 equilibrium, 1 Zou-He, 2 regularized
+    int axis, sign;    // inward normal: sign times the unit vector of axis (0 x, 1 y, 2 z)
+    double val[3];     // prescribed velocity, or the density in val[0]
+    float val_f[3];
+    float pad_;
+};
 enum { STATUS_NAN = 1u, STATUS_NOCONV = 2u, STATUS_TIMEOUT = 4u };
 // ELBM per-node outcome, shared meaning with the counters of the ABI
 enum { ALPHA_CONV = 0, ALPHA_SKIP = 1, ALPHA_CLAMP = 2, ALPHA_NOCONV = 3, ALPHA_GUARDED = 5 };
@@ -193,7 +291,13 @@ enum { MLP_NPARAM = 1394 };
 struct StepParams {
     const void* A;             // post-collision distributions at t (read)
     void* B;                   // post-collision distributions at t+1 (written)
-    const uint8_t* flags;      // node-type map (FLAG_*) or nullptr
+    const uint8_t* flags;
+    const uint32_t* links;     // near-wall nodes: bit i set when node x - e_i is solid
+    // plane i of A and B (A + i sq, B + i sq): the kernels address each
+    // direction's plane through these, so a load is one 32-bit offset from a
+    // parameter-bank pointer instead of a 64-bit plane product per access
+    const void* Ap[27];
+    void* Bp[27];      // node-type map (FLAG_*) or nullptr
     void* rho;                 // output fields (compute type), padded layout
     void* u;                   // [D][sq]
     double* alpha_out;         // ELBM per-node alpha or nullptr
@@ -209,7 +313,7 @@ struct StepParams {
     int has_force;
     int round_nearest;         // half-width stores: 1 round to nearest, 0 dither
     int aa_pushpull;           // AA pattern: 1 = pull/push step (even t), 0 = in-place step
-    int row0, nrows;           // rows updated: z layers (D3Q19) or y rows (D2Q9)
+    int row0, nrows;           // rows updated: z layers (3-D lattices) or y rows (D2Q9)
     int salt_off;              // node-index offset of the dither salt (subdomains)
     double omega;              // 1/tau
     double F[3];               // body force
@@ -223,6 +327,7 @@ struct StepParams {
     float tau_f, smag_cs2_f;
     float mrt_c_f[19];
     float mrt_cf_f[19];
+    BCEntry bc[kMaxBC];        // boundary conditions by id
     // ELBM
     int alpha_mode, max_iter, guard_steps, feq_variant;
     double tol, skip_eps, guard_tol;

@@ -24,15 +24,25 @@ cudaError_t launch_halo_copy(const HaloSeg* segs_dev, int nseg, long long max_n1
                              cudaStream_t s);
 cudaError_t launch_step_reg(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s);
+cudaError_t launch_step_bgk_q15q27(int lattice, int store, const StepParams& p, bool mask,
+                                   bool aa, cudaStream_t s);
+cudaError_t launch_step_reg_q15q27(int lattice, int store, const StepParams& p, bool mask,
+                                   bool aa, cudaStream_t s);
+cudaError_t launch_step_smag_q15q27(int lattice, int store, const StepParams& p, bool mask,
+                                    bool aa, cudaStream_t s);
 cudaError_t launch_step_smag(int lattice, int store, const StepParams& p, bool mask, bool aa,
                              cudaStream_t s);
 cudaError_t launch_diagnostics(int f64, const void* u, int D, int nx, int ny, int nz, int nxp,
                                long long sq, double* partials, double* out, cudaStream_t s);
-cudaError_t launch_step_elbm2(int store, const StepParams& p, bool mask, bool aa, cudaStream_t s);
-cudaError_t launch_step_elbm3(int store, const StepParams& p, bool mask, bool aa, cudaStream_t s);
+// ELBM: one object per (lattice code LAT, storage mask STORES); see k_elbm.cu
+template <int LAT, unsigned STORES>
+cudaError_t launch_step_elbm_part(int store, const StepParams& p, bool mask, bool aa,
+                                  cudaStream_t s);
+// storage groups of the ELBM objects: {F64}, {F32, F32S}, {F16S, BF16S}
+constexpr unsigned kElbmStoreGroup[5] = {1u, 6u, 6u, 24u, 24u};
 
-cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, int nx, int ny,
-                         int nz, int nxp, cudaStream_t s);
+cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, uint32_t* links,
+                         int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s);
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s);

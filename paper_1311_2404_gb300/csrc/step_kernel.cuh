@@ -30,7 +30,8 @@ namespace lbm {
 constexpr int kStepThreads = 128;
 
 template <class L, class S, int MODEL, bool MASK, bool AA>
-__global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParams p)
+__global__ void __launch_bounds__(kStepThreads)
+    k_stream_collide(const StepParams p)
 {
     using R = typename S::R;
     using T = typename S::T;
@@ -52,8 +53,35 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
     bool active = (x < p.nx) && ((L::D == 2) ? (yb < p.nrows) : (y < p.ny));
     const int plane = p.ny * p.nxp;
     const int n = z * plane + y * p.nxp + x;
+    // The node-type byte and the q populations are loaded independently: the
+    // loads do not wait for the flag (a solid node's populations are read and
+    // dropped), so a masked domain keeps the unmasked kernel's memory-level
+    // parallelism.
     unsigned fl = 0;
-    if (MASK && active) fl = p.flags[n];
+    if (MASK && active) fl = __ldg(p.flags + n);
+    auto Ai = [&](int i) { return static_cast<const T*>(p.Ap[i]); };
+    auto Bi = [&](int i) { return static_cast<T*>(p.Bp[i]); };
+    // neighbour coordinates (periodic)
+    const int cx[3] = {x == 0 ? p.nx - 1 : x - 1, x, x == p.nx - 1 ? 0 : x + 1};
+    const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nxp, y * p.nxp,
+                       (y == p.ny - 1 ? 0 : y + 1) * p.nxp};
+    const int zm = (L::D == 3) ? (z == 0 ? p.nz - 1 : z - 1) : z;
+    const int zp = (L::D == 3) ? (z == p.nz - 1 ? 0 : z + 1) : z;
+    const int rz[3] = {zm * plane, z * plane, zp * plane};
+    const bool pushpull = AA && p.aa_pushpull;
+    R d[L::Q];
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+            if (!AA)
+                d[i] = S::load(Ai(i) + src, L::w(i));
+            else if (pushpull)
+                d[i] = S::load(Ai(L::opp(i)) + src, L::w(i));
+            else
+                d[i] = S::load(Ai(i) + n, L::w(i));
+        }
+    }
     if (active && (fl & FLAG_SOLID)) {
         if (p.out) {
             static_cast<R*>(p.rho)[n] = R(0);
@@ -65,41 +93,25 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
     }
     int evals = 0, astat = -1;
     if (active) {
-        const T* A = static_cast<const T*>(p.A);
-        T* B = static_cast<T*>(p.B);
-        // neighbour coordinates (periodic)
-        const int cx[3] = {x == 0 ? p.nx - 1 : x - 1, x, x == p.nx - 1 ? 0 : x + 1};
-        const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nxp, y * p.nxp,
-                           (y == p.ny - 1 ? 0 : y + 1) * p.nxp};
-        const int zm = (L::D == 3) ? (z == 0 ? p.nz - 1 : z - 1) : z;
-        const int zp = (L::D == 3) ? (z == p.nz - 1 ? 0 : z + 1) : z;
-        const int rz[3] = {zm * plane, z * plane, zp * plane};
-        const bool pushpull = AA && p.aa_pushpull;
-        R d[L::Q];
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-            if (!AA)
-                d[i] = S::load(A + (size_t)i * p.sq + src, L::w(i));
-            else if (pushpull)
-                d[i] = S::load(A + (size_t)L::opp(i) * p.sq + src, L::w(i));
-            else
-                d[i] = S::load(A + (size_t)i * p.sq + n, L::w(i));
-        }
         if (MASK && (fl & FLAG_NEAR_WALL)) {
+            const uint32_t lk = __ldg(p.links + n);
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-                if (p.flags[src] & FLAG_SOLID) {
+                if ((lk >> i) & 1u) {
                     if (!AA)
-                        d[i] = S::load(A + (size_t)L::opp(i) * p.sq + n, L::w(i));
+                        d[i] = S::load(Ai(L::opp(i)) + n, L::w(i));
                     else if (pushpull)
-                        d[i] = S::load(A + (size_t)i * p.sq + n, L::w(i));
+                        d[i] = S::load(Ai(i) + n, L::w(i));
                     else
-                        d[i] = S::load(A + (size_t)L::opp(i) * p.sq + src, L::w(i));
+                        d[i] = S::load(Ai(L::opp(i)) + src, L::w(i));
                 }
             }
         }
+        if (MASK && (fl & FLAG_BC_MASK))
+            bc_apply<L, R>(d, p.bc[((fl & FLAG_BC_MASK) >> FLAG_BC_SHIFT) - 1],
+                           sel<R>(p.F_f[0], p.F[0]), sel<R>(p.F_f[1], p.F[1]),
+                           sel<R>(p.F_f[2], p.F[2]));
         R rho, v[3];
         double feat[8];
         bool have_feat = false;
@@ -122,22 +134,22 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
         }
         // destination of population i: own node, slot i (AB); node x + e_i,
         // slot i (AA pull/push); own node, slot opp(i) (AA in place)
-        auto dst = [&](int i) -> size_t {
-            if (!AA) return (size_t)i * p.sq + n;
+        auto dst = [&](int i) -> T* {
+            if (!AA) return Bi(i) + n;
             if (pushpull)
-                return (size_t)i * p.sq + (rz[1 + L::ez(i)] + ry[1 + L::ey(i)] + cx[1 + L::ex(i)]);
-            return (size_t)L::opp(i) * p.sq + n;
+                return Bi(i) + (rz[1 + L::ez(i)] + ry[1 + L::ey(i)] + cx[1 + L::ex(i)]);
+            return Bi(L::opp(i)) + n;
         };
         if constexpr (S::kHalf) {
             if (!p.round_nearest) {
-                store_node_sr<L, S>(B, d, (unsigned)(n + p.salt_off) * kSaltNode, dst);
+                store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode, dst);
             } else {
 #pragma unroll
-                for (int i = 0; i < L::Q; ++i) S::store(B + dst(i), d[i], L::w(i));
+                for (int i = 0; i < L::Q; ++i) S::store(dst(i), d[i], L::w(i));
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) S::store(B + dst(i), d[i], L::w(i));
+            for (int i = 0; i < L::Q; ++i) S::store(dst(i), d[i], L::w(i));
         }
         if (p.out) {
             static_cast<R*>(p.rho)[n] = rho;
@@ -187,6 +199,140 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParam
     }
 }
 
+// ---------------------------------------------------------------------------
+// Half-width storage, AB pattern: two x-adjacent nodes (x0 even, x0 + 1) per
+// thread.  The directions without an x component are read as one 32-bit pair,
+// each direction's plane address is formed once for both nodes, and a pair of
+// active nodes is narrowed by one stochastic-rounding conversion and written
+// with one 32-bit store.  The rounding of every value depends only on the
+// value and its (node, direction) salt, so the results are bitwise those of
+// the one-node kernel.  A pair with a solid or padding node writes only the
+// active node, leaving solid slots untouched as the one-node kernel does.
+// ---------------------------------------------------------------------------
+template <class L, class S, int MODEL, bool MASK>
+__global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepParams p)
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    static_assert(S::kHalf && MODEL != MODEL_ELBM, "two-node kernel: half-width, non-entropic");
+    const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int yb = blockIdx.y * blockDim.y + threadIdx.y;
+    const int y = (L::D == 2) ? p.row0 + yb : yb;
+    const int z = (L::D == 3) ? p.row0 + (int)blockIdx.z : 0;
+    if (!(x0 < p.nx && ((L::D == 2) ? (yb < p.nrows) : (y < p.ny)))) return;
+    const int nx = p.nx, x1 = x0 + 1;
+    const int plane = p.ny * p.nxp;
+    const int n0 = z * plane + y * p.nxp + x0;
+    bool act[2] = {true, x1 < nx};
+    unsigned fl[2] = {0u, 0u};
+    if (MASK) {   // the two flag bytes in one load (padding flags are solid)
+        const unsigned f2 = __ldg(reinterpret_cast<const unsigned short*>(p.flags + n0));
+        fl[0] = f2 & 0xffu;
+        fl[1] = f2 >> 8;
+    }
+    auto Ai = [&](int i) { return static_cast<const T*>(p.Ap[i]); };
+    auto Bi = [&](int i) { return static_cast<T*>(p.Bp[i]); };
+    // source x of each node for e_x = +1, 0, -1 (index 1 - e_x), periodic;
+    // node x0 + 1 may be padding (x1 = nx), whose reads stay inside the row
+    const int cx[2][3] = {{x0 == 0 ? nx - 1 : x0 - 1, x0, x1 >= nx ? x1 - nx : x1},
+                          {x0, x1, x1 + 1 >= nx ? x1 + 1 - nx : x1 + 1}};
+    const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nxp, y * p.nxp,
+                       (y == p.ny - 1 ? 0 : y + 1) * p.nxp};
+    const int zm = (L::D == 3) ? (z == 0 ? p.nz - 1 : z - 1) : z;
+    const int zp = (L::D == 3) ? (z == p.nz - 1 ? 0 : z + 1) : z;
+    const int rz[3] = {zm * plane, z * plane, zp * plane};
+    R d[2][L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int rs = rz[1 - L::ez(i)] + ry[1 - L::ey(i)];
+        if (L::ex(i) == 0) {
+            S::load2(Ai(i) + rs + x0, d[0][i], d[1][i]);
+        } else {
+            d[0][i] = S::load(Ai(i) + rs + cx[0][1 - L::ex(i)], L::w(i));
+            d[1][i] = S::load(Ai(i) + rs + cx[1][1 - L::ex(i)], L::w(i));
+        }
+    }
+    R rho[2], v[2][3];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int n = n0 + k;
+        if (MASK && (fl[k] & FLAG_SOLID)) act[k] = false;
+        if (!act[k]) continue;
+        if (MASK && (fl[k] & FLAG_NEAR_WALL)) {
+            const uint32_t lk = __ldg(p.links + n);
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i)
+                if ((lk >> i) & 1u) d[k][i] = S::load(Ai(L::opp(i)) + n, L::w(i));
+        }
+        if (MASK && (fl[k] & FLAG_BC_MASK))
+            bc_apply<L, R>(d[k], p.bc[((fl[k] & FLAG_BC_MASK) >> FLAG_BC_SHIFT) - 1],
+                           p.F_f[0], p.F_f[1], p.F_f[2]);
+        if (MODEL == MODEL_BGK) {
+            bgk_collide<L, R>(d[k], p.omega_f, p.F_f[0], p.F_f[1], p.F_f[2], p.has_force != 0,
+                              rho[k], v[k]);
+        } else if (MODEL == MODEL_MRT) {
+            if constexpr (L::Q == 19) mrt_collide<R>(d[k], p, rho[k], v[k]);
+        } else {
+            les_collide<L, R, MODEL == MODEL_SMAG>(d[k], p.omega_f, p.tau_f, p.smag_cs2_f,
+                                                   p.F_f[0], p.F_f[1], p.F_f[2],
+                                                   p.has_force != 0, rho[k], v[k]);
+        }
+    }
+    const unsigned s0 = (unsigned)(n0 + p.salt_off) * kSaltNode, s1 = s0 + kSaltNode;
+    if (act[0] && act[1]) {
+        if (!p.round_nearest) {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const unsigned pk = S::encode_pair(d[1][i], d[0][i], s1 + (unsigned)i * kSaltDir,
+                                                   s0 + (unsigned)i * kSaltDir);
+                *reinterpret_cast<unsigned*>(Bi(i) + n0) = pk;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                S::store(Bi(i) + n0, d[0][i], L::w(i));
+                S::store(Bi(i) + n0 + 1, d[1][i], L::w(i));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!act[k]) continue;
+            const int n = n0 + k;
+            if (!p.round_nearest)
+                store_node_sr<L, S>(d[k], k ? s1 : s0, [&](int i) { return Bi(i) + n; });
+            else
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[k][i], L::w(i));
+        }
+    }
+    if (p.out) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int n = n0 + k;
+            if (k == 1 && x1 >= nx) continue;
+            const bool a = act[k];
+            static_cast<R*>(p.rho)[n] = a ? rho[k] : R(0);
+#pragma unroll
+            for (int c = 0; c < L::D; ++c) static_cast<R*>(p.u)[c * p.sq + n] = a ? v[k][c] : R(0);
+            if (a) {
+                bad |= !isfinite(rho[k]);
+#pragma unroll
+                for (int c = 0; c < L::D; ++c) bad |= !isfinite(v[k][c]);
+            }
+        }
+        if (bad) atomicOr(p.status, STATUS_NAN);
+    }
+}
+
+inline dim3 step_block_x2(int nxp)
+{
+    const int pairs = nxp / 2;   // a multiple of 16
+    const int bx = pairs >= kStepThreads ? kStepThreads : (pairs + 31) / 32 * 32;
+    return dim3(bx, kStepThreads / bx, 1);
+}
+
 // Block shape: BX along x (a multiple of 32, at most kStepThreads), BY rows.
 inline dim3 step_block(int nxp)
 {
@@ -197,6 +343,22 @@ inline dim3 step_block(int nxp)
 template <class L, class S, int MODEL>
 cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t s)
 {
+    if constexpr (S::kHalf && MODEL != MODEL_ELBM) {
+        // masked MRT keeps the one-node kernel: two MRT nodes need ~96
+        // registers and solid neighbours split the pairs (20% slower measured)
+        if (!aa && !(MODEL == MODEL_MRT && mask)) {
+            if (p.nrows <= 0) return cudaSuccess;
+            const bool d2 = (L::D == 2);
+            const dim3 block = step_block_x2(p.nxp);
+            const dim3 grid(((p.nx + 1) / 2 + block.x - 1) / block.x,
+                            ((d2 ? p.nrows : p.ny) + block.y - 1) / block.y, d2 ? 1 : p.nrows);
+            if (mask)
+                k_stream_collide_x2<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
+            else
+                k_stream_collide_x2<L, S, MODEL, false><<<grid, block, 0, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
     const dim3 block = step_block(p.nxp);
     const bool d2 = (L::D == 2);
     const dim3 grid((p.nx + block.x - 1) / block.x,
@@ -216,33 +378,41 @@ cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t 
     return cudaGetLastError();
 }
 
-// lattice: 0 D2Q9, 1 D3Q19; LAT restricts a translation unit to one lattice
-// (-1: both).
-template <int MODEL, int LAT = -1>
+// storage codes 0 F64, 1 F32, 2 F32S, 3 F16S, 4 BF16S; bit k of STORES
+// compiles storage k
+template <class L, int MODEL, unsigned STORES = 31u>
+cudaError_t launch_store(int store, const StepParams& p, bool mask, bool aa, cudaStream_t s)
+{
+    switch (store) {
+    case 0: if constexpr ((STORES & 1u) != 0) return launch_step_t<L, StoreF64, MODEL>(p, mask, aa, s);
+            break;
+    case 1: if constexpr ((STORES & 2u) != 0) return launch_step_t<L, StoreF32, MODEL>(p, mask, aa, s);
+            break;
+    case 2: if constexpr ((STORES & 4u) != 0) return launch_step_t<L, StoreF32S, MODEL>(p, mask, aa, s);
+            break;
+    case 3: if constexpr ((STORES & 8u) != 0) return launch_step_t<L, StoreF16S, MODEL>(p, mask, aa, s);
+            break;
+    case 4: if constexpr ((STORES & 16u) != 0) return launch_step_t<L, StoreBF16S, MODEL>(p, mask, aa, s);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+// lattice codes: 0 D2Q9, 1 D3Q19, 2 D3Q15, 3 D3Q27.  Bit l of LATS compiles
+// lattice l into the calling translation unit (each unit holds a few
+// lattices so that the build compiles them in parallel).
+template <int MODEL, unsigned LATS, unsigned STORES = 31u>
 cudaError_t launch_step_model(int lattice, int store, const StepParams& p, bool mask, bool aa,
                               cudaStream_t s)
 {
-    if (lattice == 0) {
-        if constexpr (MODEL != MODEL_MRT && LAT != 1) {
-            switch (store) {
-            case 0: return launch_step_t<D2Q9, StoreF64, MODEL>(p, mask, aa, s);
-            case 1: return launch_step_t<D2Q9, StoreF32, MODEL>(p, mask, aa, s);
-            case 2: return launch_step_t<D2Q9, StoreF32S, MODEL>(p, mask, aa, s);
-            case 3: return launch_step_t<D2Q9, StoreF16S, MODEL>(p, mask, aa, s);
-            case 4: return launch_step_t<D2Q9, StoreBF16S, MODEL>(p, mask, aa, s);
-            }
-        }
-        return cudaErrorInvalidValue;
-    }
-    if constexpr (LAT != 0) {
-        switch (store) {
-        case 0: return launch_step_t<D3Q19, StoreF64, MODEL>(p, mask, aa, s);
-        case 1: return launch_step_t<D3Q19, StoreF32, MODEL>(p, mask, aa, s);
-        case 2: return launch_step_t<D3Q19, StoreF32S, MODEL>(p, mask, aa, s);
-        case 3: return launch_step_t<D3Q19, StoreF16S, MODEL>(p, mask, aa, s);
-        case 4: return launch_step_t<D3Q19, StoreBF16S, MODEL>(p, mask, aa, s);
-        }
-    }
+    if constexpr ((LATS & 1u) != 0 && MODEL != MODEL_MRT)
+        if (lattice == 0) return launch_store<D2Q9, MODEL, STORES>(store, p, mask, aa, s);
+    if constexpr ((LATS & 2u) != 0)
+        if (lattice == 1) return launch_store<D3Q19, MODEL, STORES>(store, p, mask, aa, s);
+    if constexpr ((LATS & 4u) != 0 && MODEL != MODEL_MRT)
+        if (lattice == 2) return launch_store<D3Q15, MODEL, STORES>(store, p, mask, aa, s);
+    if constexpr ((LATS & 8u) != 0 && MODEL != MODEL_MRT)
+        if (lattice == 3) return launch_store<D3Q27, MODEL, STORES>(store, p, mask, aa, s);
     return cudaErrorInvalidValue;
 }
 

@@ -30,7 +30,7 @@ _L = ctypes.CDLL(LIB_PATH)
 
 # ---- constants (mirror include/lbm.h) -------------------------------------
 LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ENOCONV = range(8)
-LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q15, LBM_D3Q27 = 0, 1, 2, 3
 LBM_BGK, LBM_MRT, LBM_ELBM, LBM_REG, LBM_SMAG = 0, 1, 2, 3, 4
 LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S = range(5)
 LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
@@ -38,6 +38,8 @@ LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIX
 LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
 LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
 LBM_TRANSFER_STAGED, LBM_TRANSFER_DIRECT = 0, 1
+LBM_BC_VELOCITY, LBM_BC_PRESSURE = 1, 2
+LBM_BC_EQUILIBRIUM, LBM_BC_ZOUHE, LBM_BC_REGULARIZED = 0, 1, 2
 MLP_NPARAM = 1394
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ESTATE", 3: "LBM_ENOMEM",
@@ -68,6 +70,7 @@ _PROTOS = {
     "lbm_multi_set_rounding": (_i, [_vp, _i]),
     "lbm_multi_set_smagorinsky": (_i, [_vp, _d]),
     "lbm_multi_set_elbm": (_i, [_vp, _i, _d, _i, _d]),
+    "lbm_multi_set_boundary": (_i, [_vp, _i, _i, _i, _i, _vp]),
     "lbm_multi_set_geometry": (_i, [_vp, _vp]),
     "lbm_multi_init_equilibrium": (_i, [_vp, _vp, _vp, _i]),
     "lbm_multi_step": (_i, [_vp, _i]),
@@ -85,6 +88,7 @@ _PROTOS = {
     "lbm_set_force": (_i, [_vp, _d, _d, _d]),
     "lbm_set_mrt_rates": (_i, [_vp, _vp, _i]),
     "lbm_set_smagorinsky": (_i, [_vp, _d]),
+    "lbm_set_boundary": (_i, [_vp, _i, _i, _i, _i, _vp]),
     "lbm_set_elbm": (_i, [_vp, _i, _d, _i, _d]),
     "lbm_set_elbm_guard": (_i, [_vp, _i, _d]),
     "lbm_set_elbm_feq": (_i, [_vp, _i]),
@@ -223,6 +227,19 @@ def lbm_set_force(h, fx, fy, fz=0.0):
 def lbm_set_mrt_rates(h, s):
     s = np.ascontiguousarray(s, dtype=np.float64)
     _check(_L.lbm_set_mrt_rates(h, _ptr(s), int(s.size)), h)
+
+
+def _bc_value(value):
+    v = np.zeros(3)
+    vals = np.atleast_1d(np.asarray(value, dtype=np.float64))
+    v[:len(vals)] = vals
+    return v
+
+
+def lbm_set_boundary(h, cid, kind, method, normal, value):
+    """Condition cid (mask code 2 + cid): value = velocity or [rho]."""
+    v = _bc_value(value)
+    _check(_L.lbm_set_boundary(h, int(cid), int(kind), int(method), int(normal), _ptr(v)), h)
 
 
 def lbm_set_smagorinsky(h, cs):
@@ -487,6 +504,12 @@ def lbm_multi_set_rounding(m, mode):
 
 def lbm_multi_set_smagorinsky(m, cs):
     _mcheck(_L.lbm_multi_set_smagorinsky(m, float(cs)), m)
+
+
+def lbm_multi_set_boundary(m, cid, kind, method, normal, value):
+    v = _bc_value(value)
+    _mcheck(_L.lbm_multi_set_boundary(m, int(cid), int(kind), int(method), int(normal),
+                                      _ptr(v)), m)
 
 
 def lbm_multi_set_elbm(m, alpha_mode, tol=1e-12, max_iter=20, skip_eps=1e-3):

@@ -140,6 +140,32 @@ def turbulence(n: int = 256, k0: float = 4.0, u_rms: float = 0.04, seed: int = 2
 
 
 # --------------------------------------------------------------------------
+# Lid-driven cavity (Sec. 5.1 validation; the benchmark shape of Sec. 4)
+# --------------------------------------------------------------------------
+def ldc_mask(n: int = 254, D: int = 3) -> np.ndarray:
+    """Cubic (square for D = 2) cavity of n nodes per side: solid walls
+    (mask 1) on every face except the top (y = n - 1), whose interior nodes
+    are boundary nodes of condition 0 (mask 2), the moving lid; the lid's
+    edge nodes belong to the side walls.  [nz, ny, nx] uint8."""
+    nz = n if D == 3 else 1
+    m = np.zeros((nz, n, n), dtype=np.uint8)
+    m[:, :, 0] = 1
+    m[:, :, n - 1] = 1
+    m[:, 0, :] = 1
+    if D == 3:
+        m[0] = 1
+        m[n - 1] = 1
+    lid = m[:, n - 1, :]
+    lid[lid == 0] = 2
+    return m
+
+
+def ldc_tau(n: int, re: float = 1000.0, u_lid: float = 0.05) -> float:
+    """Relaxation time for Re = u_lid L / nu, L = n - 2 fluid nodes across."""
+    return 0.5 + 3.0 * u_lid * (n - 2) / re
+
+
+# --------------------------------------------------------------------------
 # Kida vortex (Sec. 5.2)
 # --------------------------------------------------------------------------
 def kida(n: int = 256, u0: float = 0.05, rho0: float = 1.0):

@@ -1,0 +1,217 @@
+"""D3Q15 / D3Q27 lattices and velocity / pressure boundary nodes on the GPU
+against the FP64 oracle: ragged domains with walls and forcing on the new
+lattices for every model; channels with a velocity inlet and a pressure
+outlet for every condition method on all four lattices; a reduced
+lid-driven cavity; the exact Couette profile; AA = AB and subdomains =
+single domain with boundary nodes; mask validation.
+"""
+import numpy as np
+import pytest
+
+import analytic as an
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1311_2404_gb300 import lbm  # noqa: E402
+from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
+
+LAT = {2: lbm.LBM_D2Q9, 3: lbm.LBM_D3Q19, 15: lbm.LBM_D3Q15, 27: lbm.LBM_D3Q27}
+OMODEL = {lbm.LBM_BGK: oracle.BGK, lbm.LBM_REG: oracle.REG, lbm.LBM_SMAG: oracle.SMAG,
+          lbm.LBM_ELBM: oracle.ELBM, lbm.LBM_MRT: oracle.MRT}
+TOL = {lbm.LBM_F64: 1e-11, lbm.LBM_F32S: 2e-5, lbm.LBM_F32: 2e-4, lbm.LBM_F16S: 5e-3,
+       lbm.LBM_BF16S: 5e-2}
+
+
+def _dim(code):
+    return 2 if code == 2 else 3
+
+
+def _gpu(code, model, dtype, shape, steps, rho, u, mask=None, force=(0, 0, 0), tau=0.6,
+         bcs=(), pattern=lbm.LBM_PATTERN_AB, elbm_skip=0.0):
+    nz, ny, nx = shape
+    sim = lbm.Simulation(nx, ny, nz, LAT[code], model, tau, dtype, pattern=pattern)
+    if model == lbm.LBM_SMAG:
+        lbm.lbm_set_smagorinsky(sim.h, 0.15)
+    if model == lbm.LBM_ELBM:
+        lbm.lbm_set_elbm(sim.h, lbm.LBM_ALPHA_NEWTON, 1e-12, 20, elbm_skip)
+    for cid, kind, method, normal, value in bcs:
+        lbm.lbm_set_boundary(sim.h, cid, kind, method, normal, value)
+    if mask is not None:
+        sim.set_geometry(mask)
+    if any(force):
+        sim.set_force(*force)
+    sim.init(rho, u)
+    sim.step(steps)
+    r, v = sim.macro()
+    sim.close()
+    return r, v
+
+
+def _oracle(code, model, shape, steps, rho, u, mask=None, force=(0, 0, 0), tau=0.6, bcs=(),
+            elbm_skip=0.0):
+    nz, ny, nx = shape
+    p = oracle.make_params(nx, ny, nz, D=code if code in (15, 27) else _dim(code),
+                           model=OMODEL[model], tau=tau, force=force, smag_cs=0.15,
+                           skip_eps=elbm_skip)
+    for cid, kind, method, normal, value in bcs:
+        oracle.set_bc(p, cid, kind, method, normal, value)
+    F = oracle.init(p, rho, u)
+    ro, uo, _, _ = oracle.run(p, F, steps, mask)
+    return ro, uo
+
+
+@pytest.mark.parametrize("code", [15, 27])
+@pytest.mark.parametrize("model", [lbm.LBM_BGK, lbm.LBM_REG, lbm.LBM_SMAG, lbm.LBM_ELBM])
+@pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32S, lbm.LBM_F16S])
+def test_new_lattices_vs_oracle(code, model, dtype):
+    shape = (9, 14, 37)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(code + 3 * model)
+    mask = (rng.random(shape) < 0.1).astype(np.uint8)
+    mask[:, 0, :] = 1
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=code, u_amp=0.06, rho_amp=0.01)
+    force = (2e-5, -1e-5, 3e-6)
+    tau = 0.52 if model == lbm.LBM_ELBM else 0.56
+    T = 10
+    rg, ug = _gpu(code, model, dtype, shape, T, rho, u, mask, force, tau)
+    ro, uo = _oracle(code, model, shape, T, rho, u, mask, force, tau)
+    fl = mask == 0
+    eu = an.rel_l2(ug[:, fl], uo[:, fl])
+    print(f"D3Q{code} model {model} dtype {dtype}: rel-L2 u {eu:.3e}")
+    assert eu < TOL[dtype]
+    assert np.abs(rg[fl] - ro[fl]).max() < max(TOL[dtype], 1e-12) * 10
+
+
+def _channel(code, nx=40, ny=18, nz=6):
+    """Walls at y = 0 and ny - 1; velocity inlet (condition 0) at x = 0 and
+    pressure outlet (condition 1) at x = nx - 1 on the fluid rows."""
+    D = _dim(code)
+    nz = 1 if D == 2 else nz
+    m = np.zeros((nz, ny, nx), dtype=np.uint8)
+    m[:, 0, :] = 1
+    m[:, ny - 1, :] = 1
+    m[:, 1:ny - 1, 0] = 2
+    m[:, 1:ny - 1, nx - 1] = 3
+    return m
+
+
+@pytest.mark.parametrize("code", [2, 3, 15, 27])
+@pytest.mark.parametrize("method", [lbm.LBM_BC_EQUILIBRIUM, lbm.LBM_BC_ZOUHE,
+                                    lbm.LBM_BC_REGULARIZED])
+@pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32S])
+def test_inlet_outlet_channel_vs_oracle(code, method, dtype):
+    D = _dim(code)
+    mask = _channel(code)
+    nz, ny, nx = mask.shape
+    rho = np.ones(mask.shape)
+    u = np.zeros((D,) + mask.shape)
+    u[0] = 0.02
+    bcs = [(0, lbm.LBM_BC_VELOCITY, method, 1, [0.03, 0.0, 0.0]),
+           (1, lbm.LBM_BC_PRESSURE, method, -1, [1.0])]
+    force = (0.0, 1e-6, 0.0)
+    T = 60
+    rg, ug = _gpu(code, lbm.LBM_BGK, dtype, mask.shape, T, rho, u, mask, force, 0.7, bcs)
+    ro, uo = _oracle(code, lbm.LBM_BGK, mask.shape, T, rho, u, mask, force, 0.7, bcs)
+    fl = mask != 1
+    eu = an.rel_l2(ug[:, fl], uo[:, fl])
+    print(f"channel D{code} method {method} dtype {dtype}: rel-L2 u {eu:.3e}")
+    assert eu < TOL[dtype]
+    # the inlet nodes report the prescribed velocity
+    inlet = mask == 2
+    assert np.abs(ug[0][inlet] - 0.03).max() < (1e-13 if dtype == lbm.LBM_F64 else 1e-6)
+    assert np.abs(rg[mask == 3] - 1.0).max() < (1e-13 if dtype == lbm.LBM_F64 else 1e-6)
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32S])
+@pytest.mark.parametrize("model", [lbm.LBM_BGK, lbm.LBM_MRT, lbm.LBM_ELBM])
+def test_lid_driven_cavity_reduced_copy(dtype, model):
+    """20^3 cavity, regularized lid at 0.05, 150 steps vs the oracle."""
+    n = 20
+    mask = wl.ldc_mask(n)
+    rho = np.ones(mask.shape)
+    u = np.zeros((3,) + mask.shape)
+    tau = 0.56
+    bcs = [(0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_REGULARIZED, -2, [0.05, 0.0, 0.0])]
+    T = 150
+    rg, ug = _gpu(3, model, dtype, mask.shape, T, rho, u, mask, (0, 0, 0), tau, bcs,
+                  elbm_skip=1e-4)
+    ro, uo = _oracle(3, model, mask.shape, T, rho, u, mask, (0, 0, 0), tau, bcs, elbm_skip=1e-4)
+    fl = mask != 1
+    eu = an.rel_l2(ug[:, fl], uo[:, fl])
+    print(f"LDC model {model} dtype {dtype}: rel-L2 u {eu:.3e}")
+    assert eu < TOL[dtype] * (10 if model == lbm.LBM_ELBM else 1)
+
+
+def test_couette_exact_profile_on_gpu():
+    ny, U = 12, 0.05
+    mask = np.zeros((2, ny, 3), dtype=np.uint8)
+    mask[:, 0, :] = 1
+    mask[:, ny - 1, :] = 2
+    rho = np.ones(mask.shape)
+    u = np.zeros((3,) + mask.shape)
+    bcs = [(0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_ZOUHE, -2, [U, 0.0, 0.0])]
+    _, ug = _gpu(3, lbm.LBM_BGK, lbm.LBM_F64, mask.shape, 6000, rho, u, mask, (0, 0, 0), 0.8,
+                 bcs)
+    y = np.arange(1, ny)
+    ref = U * (y - 0.5) / (ny - 1.5)
+    assert np.abs(ug[0, :, 1:, :] - ref[None, :, None]).max() < 1e-10 * U
+
+
+@pytest.mark.parametrize("code,model,dtype", [(27, lbm.LBM_BGK, lbm.LBM_F32S),
+                                              (15, lbm.LBM_ELBM, lbm.LBM_F64),
+                                              (3, lbm.LBM_REG, lbm.LBM_F16S)])
+def test_aa_equals_ab_with_boundary_nodes(code, model, dtype):
+    mask = _channel(code, nx=37, ny=13, nz=9)
+    nz, ny, nx = mask.shape
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=2, u_amp=0.03, rho_amp=0.01)
+    bcs = [(0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_ZOUHE, 1, [0.03, 0.0, 0.0]),
+           (1, lbm.LBM_BC_PRESSURE, lbm.LBM_BC_REGULARIZED, -1, [1.0])]
+    for steps in (7, 8):
+        ra, va = _gpu(code, model, dtype, mask.shape, steps, rho, u, mask, (1e-6, 0, 0), 0.6,
+                      bcs)
+        rb, vb = _gpu(code, model, dtype, mask.shape, steps, rho, u, mask, (1e-6, 0, 0), 0.6,
+                      bcs, pattern=lbm.LBM_PATTERN_AA)
+        assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+
+
+@pytest.mark.parametrize("code", [3, 27])
+def test_subdomains_with_boundary_nodes_equal_single(code):
+    mask = _channel(code, nx=40, ny=12, nz=10)
+    nz, ny, nx = mask.shape
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=4, u_amp=0.03, rho_amp=0.01)
+    bcs = [(0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_REGULARIZED, 1, [0.03, 0.0, 0.0]),
+           (1, lbm.LBM_BC_PRESSURE, lbm.LBM_BC_ZOUHE, -1, [1.0])]
+    r1, v1 = _gpu(code, lbm.LBM_BGK, lbm.LBM_F32S, mask.shape, 9, rho, u, mask, (0, 0, 0), 0.6,
+                  bcs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m = lbm.lbm_multi_create(nx, ny, nz, LAT[code], lbm.LBM_BGK, 0.6, lbm.LBM_F32S, 3)
+        lbm.lbm_multi_set_stream(m, s.cuda_stream)
+        for b in bcs:
+            lbm.lbm_multi_set_boundary(m, *b)
+        lbm.lbm_multi_set_geometry(m, mask)
+        lbm.lbm_multi_init_equilibrium(m, rho, u)
+        lbm.lbm_multi_step(m, 9)
+        r2, v2 = np.empty(rho.shape), np.empty(u.shape)
+        lbm.lbm_multi_get_macro(m, r2, v2)
+        lbm.lbm_multi_destroy(m)
+    assert np.array_equal(r1, r2) and np.array_equal(v1, v2)
+
+
+def test_mask_values_are_checked():
+    sim = lbm.Simulation(16, 8, 4, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+    bad = np.zeros((4, 8, 16), dtype=np.uint8)
+    bad[1, 2, 3] = 17
+    with pytest.raises(lbm.LBMError):
+        sim.set_geometry(bad)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_boundary(sim.h, 15, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_ZOUHE, 1, [0, 0, 0])
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_boundary(sim.h, 0, lbm.LBM_BC_VELOCITY, lbm.LBM_BC_ZOUHE, 4, [0, 0, 0])
+    sim.close()
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_create(8, 8, 8, lbm.LBM_D3Q27, lbm.LBM_MRT, 0.6, lbm.LBM_F32S)
