@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--lattice", default="", choices=["", "q15", "q19", "q27"],
                     help="override the 3-D velocity set of the workload")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--shape", default="",
+                    help="override the domain as NX,NY,NZ (e.g. the paper's duct 254,127,512)")
     ap.add_argument("--size", type=int, default=0,
                     help="override the cube edge of the 256^3 workloads (profiling runs)")
     ap.add_argument("--subdomains", type=int, default=0,
@@ -87,10 +89,17 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources of the headline kernel (LBGK stream-collide): its translation
+# unit and the headers it includes
+KERNEL_SOURCES = ("k_bgk.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh")
+
+
 def source_sha():
+    """Hash of the headline kernel's sources; a recorded DRAM traffic figure
+    is reported only while they are unchanged."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1311_2404_gb300", "csrc", "*"))):
-        with open(p, "rb") as fh:
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1311_2404_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -185,8 +194,13 @@ def job_glups(nodes_per_rank, steps, world, ms_max):
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def workload_spec(name, dtype, size=0, model="", lattice=""):
+def workload_spec(name, dtype, size=0, model="", lattice="", shape=""):
     spec = _workload_spec(name, dtype)
+    if shape and name in ("duct", "tg256", "kida"):
+        nxs, nys, nzs = (int(v) for v in shape.split(","))
+        old = "x".join(str(v) for v in spec["n"]) if name == "duct" else f"{spec['n'][0]}^3"
+        spec["n"] = (nxs, nys, nzs)
+        spec["name"] = spec["name"].replace(old, f"{nxs}x{nys}x{nzs}")
     if lattice and name != "batch":
         from paper_1311_2404_gb300 import lbm
         spec["lattice"] = {"q15": lbm.LBM_D3Q15, "q19": lbm.LBM_D3Q19,
@@ -272,7 +286,7 @@ def run_multi(args):
     import torch
     torch.cuda.set_device(0)
     from paper_1311_2404_gb300 import lbm
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice, args.shape)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
@@ -358,6 +372,36 @@ def run_multi(args):
     print(json.dumps(line), flush=True)
 
 
+def elbm_compare(lbm, sim, spec, rho, u, args, stream):
+    """After the timed steps: kinetic energy of this run against a Newton run
+    of the same steps from the same state, and the entropy-condition residual
+    |g(alpha)| / a_2 over one more (untimed) step in diagnostic mode."""
+    t = lbm.lbm_get_time(sim.h)
+    E, _ = lbm.lbm_kinetic_energy_enstrophy(sim.h)
+    out = {"t": int(t), "E": E}
+    nx, ny, nz = spec["n"]
+    if args.alpha != "newton":
+        ref = lbm.Simulation(nx, ny, nz, spec["lattice"], spec["model"], spec["tau"],
+                             spec["dtype"], stream=stream.cuda_stream)
+        lbm.lbm_set_elbm(ref.h, lbm.LBM_ALPHA_NEWTON, 1e-12, 20, 1e-3)
+        lbm.lbm_init_equilibrium(ref.h, torch_from(rho), torch_from(u))
+        lbm.lbm_step(ref.h, int(t))
+        Er, _ = lbm.lbm_kinetic_energy_enstrophy(ref.h)
+        ref.close()
+        out["E_rel_diff_vs_newton"] = abs(E - Er) / Er
+    lbm.lbm_set_elbm_diagnostics(sim.h, 1)
+    lbm.lbm_step(sim.h, 1)
+    mean, mx, cnt = lbm.lbm_get_elbm_entropy_error(sim.h)
+    lbm.lbm_set_elbm_diagnostics(sim.h, 0)
+    out.update({"entropy_resid_mean": mean, "entropy_resid_max": mx, "entropy_resid_nodes": cnt})
+    return out
+
+
+def torch_from(a):
+    import torch
+    return torch.from_numpy(a).cuda()
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -369,7 +413,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1311_2404_gb300 import lbm
 
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice, args.shape)
     nx, ny, nz = spec["n"]
     nodes = nx * ny * nz
     rho, u, mask = workload_inputs(spec)
@@ -425,6 +469,7 @@ def run_ours(args):
         lbm.lbm_sync(sim.h)
         elbm_stats = None
         diag = None
+        elbm_cmp = None
         if spec["kind"] == "kida":
             E, Om = lbm.lbm_kinetic_energy_enstrophy(sim.h)
             diag = {"t": int(lbm.lbm_get_time(sim.h)), "E": E, "Omega": Om,
@@ -435,6 +480,8 @@ def run_ours(args):
                           "skipped_frac": round(st[1] / max(st[5], 1), 4),
                           "guess_accepted_frac": round(st[4] / max(st[5], 1), 4),
                           "at_cap": int(st[3])}
+            if spec["kind"] == "turb":
+                elbm_cmp = elbm_compare(lbm, sim, spec, rho, u, args, stream)
 
         # end to end through the public API with host buffers
         pin_r = torch.from_numpy(rho).pin_memory()
@@ -460,6 +507,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     glups = job_glups(nodes, args.steps, world, ms_max)
+    fluid = int((mask != 1).sum()) if mask is not None else nodes
     per_launch_s = ms / 1e3 / args.steps
     bpn = bytes_per_node(args.dtype, spec["lattice"]) + (1 if mask is not None else 0)
     achieved = bpn * nodes / per_launch_s / 1e9
@@ -498,12 +546,18 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if mask is not None:
+        line["config"]["fluid_nodes"] = fluid
+        line["fluid_glups"] = round(job_glups(fluid, args.steps, world, ms_max), 4)
     if elbm_stats:
         line["elbm"] = elbm_stats
+        if elbm_cmp:
+            line["elbm"].update(elbm_cmp)
     if diag:
         line["kida"] = diag
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=12.0)
+        line["cpu_baseline"]["single_thread"] = cpu_baseline(spec, budget_s=6.0, threads=1)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -543,16 +597,18 @@ def _oracle_sample(spec, nz_s, ny_s=None):
     return p, F, mask, nx * ny_s * nz_s
 
 
-def cpu_baseline(spec, budget_s=12.0, steps=None):
+def cpu_baseline(spec, budget_s=12.0, steps=None, threads=0):
     import oracle
     oracle.build()
-    cores = oracle.max_threads(0)
+    cores = oracle.max_threads(threads)
     p, F, mask, n = _oracle_sample(spec, 1)
+    p.nthreads = threads
     t0 = time.perf_counter()
     oracle.run(p, F, 1, mask)
     dt1 = time.perf_counter() - t0
     nz_s = max(1, min(spec["n"][2], int(budget_s / 4 / max(dt1, 1e-6))))
     p, F, mask, n = _oracle_sample(spec, nz_s)
+    p.nthreads = threads
     nsteps = max(1, min(50, int(budget_s / max(dt1 * nz_s, 1e-6))))
     t0 = time.perf_counter()
     oracle.run(p, F, nsteps, mask)
@@ -563,11 +619,38 @@ def cpu_baseline(spec, budget_s=12.0, steps=None):
                       f"{nsteps} steps, FP64 C oracle, {dt:.1f} s"}
 
 
+def batch_cpu_baseline(specs, budget_s=10.0):
+    """The FP64 oracle on a sample of the ensemble's channels, one after the
+    other, each for a few steps."""
+    import oracle
+    from paper_1311_2404_gb300 import workloads as wl
+    oracle.build()
+    cores = oracle.max_threads(0)
+    done, t_used, nsamp = 0, 0.0, 0
+    for sp in specs:
+        p = oracle.make_params(sp["nx"], sp["ny"], 1, D=2, model=oracle.BGK, tau=sp["tau"],
+                               force=(sp["gx"], 0.0, 0.0))
+        rho = np.ones((1, sp["ny"], sp["nx"]))
+        u = np.zeros((2, 1, sp["ny"], sp["nx"]))
+        F = oracle.init(p, rho, u)
+        t0 = time.perf_counter()
+        oracle.run(p, F, 10, wl.batch_channel_mask(sp))
+        t_used += time.perf_counter() - t0
+        done += sp["nx"] * sp["ny"] * 10
+        nsamp += 1
+        if t_used > budget_s:
+            break
+    return {"value": round(done / t_used / 1e9, 6), "unit": "GLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"first {nsamp} of {len(specs)} channels, 10 steps each, FP64 C oracle, "
+                      f"{t_used:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice)
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice, args.shape)
     import oracle
     oracle.build()
     cores = oracle.max_threads(0)
@@ -634,8 +717,11 @@ def run_batch(args):
     lbm.lbm_batch_set_rounding(b, lbm.LBM_ROUND_NEAREST if args.round == "nearest"
                                else lbm.LBM_ROUND_DITHER)
     rho_bytes = 0
+    fluid = 0
     for d, sp in enumerate(specs):
-        lbm.lbm_batch_set_geometry(b, d, wl.batch_channel_mask(sp))
+        bm = wl.batch_channel_mask(sp)
+        fluid += int((bm == 0).sum())
+        lbm.lbm_batch_set_geometry(b, d, bm)
         lbm.lbm_batch_set_force(b, d, sp["gx"], 0.0)
         r = np.ones((1, sp["ny"], sp["nx"]), dtype=np.float32)
         u = np.zeros((2, 1, sp["ny"], sp["nx"]), dtype=np.float32)
@@ -665,6 +751,25 @@ def run_batch(args):
     launches = lbm.lbm_batch_launch_count(b) - l0
     clocks = sampler.stop() if sampler else None
     lbm.lbm_batch_sync(b)
+    # end to end: every domain's rho, u from pinned host memory, one step, every
+    # domain's rho, v back to pinned host memory
+    pins = []
+    for sp in specs:
+        r = torch.ones((1, sp["ny"], sp["nx"]), dtype=torch.float32).pin_memory()
+        u = torch.zeros((2, 1, sp["ny"], sp["nx"]), dtype=torch.float32).pin_memory()
+        pins.append((r, u, torch.empty_like(r).pin_memory(), torch.empty_like(u).pin_memory()))
+    e2e_steps = max(1, min(args.e2e_steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for d, (r, u, _, _) in enumerate(pins):
+            lbm.lbm_batch_init_equilibrium(b, d, r, u)
+        lbm.lbm_batch_step(b, 1)
+        for d, (_, _, ro, uo) in enumerate(pins):
+            lbm.lbm_batch_get_macro(b, d, ro, uo)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    io_bytes = sum(int(r.numel() + u.numel()) * 4 for r, u, _, _ in pins)
     lbm.lbm_batch_destroy(b)
     ms_max, = max_over_ranks([ms], world, "cuda")
     if rank != 0:
@@ -689,8 +794,14 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": peak_kind, "bytes_per_node": bpn},
+        "fluid_glups": round(job_glups(fluid, args.steps, world, ms_max), 4),
+        "e2e": {"value": round(nodes * world / e2e_s / 1e9, 4), "unit": "GLUPS",
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": int(launches), "clocks": clocks,
     }
+    line["config"]["fluid_nodes"] = fluid
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(specs, budget_s=10.0)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -232,7 +232,11 @@ LBM_API int lbm_set_graph(lbm_handle h, int on);
 
 /* F = f_eq(rho, u) at every node (polynomial Eq. equilibrium for LBGK/MRT,
  * the model's own equilibrium for ELBM) and t = 0.  rho [nz][ny][nx], u
- * [D][nz][ny][nx], element type field_dtype.  Errors: LBM_EINVAL,
+ * [D][nz][ny][nx], element type field_dtype.  Device memory is read
+ * asynchronously on the stream.  Host memory: pinned (page-locked) buffers
+ * are read in place by the kernel over the CPU-GPU link, pageable ones
+ * through a staging copy; either way the call returns after the data have
+ * been read, so the caller may reuse the buffers.  Errors: LBM_EINVAL,
  * LBM_ENOMEM, LBM_ECUDA. */
 LBM_API int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field_dtype);
 
@@ -248,8 +252,10 @@ LBM_API int lbm_get_time(lbm_handle h, long long* t);
 /* ---- readback ---------------------------------------------------------- */
 
 /* rho [nz][ny][nx] and v [D][nz][ny][nx] of the last step (either pointer
- * may be NULL).  Solid nodes give 0.  Synchronises the stream; returns
- * LBM_ENAN if a non-finite value was found, LBM_ESTATE before any step. */
+ * may be NULL; device, pinned host or pageable host memory; pinned host
+ * memory is written in place by the packing kernel).  Solid nodes give 0.
+ * Synchronises the stream; returns LBM_ENAN if a non-finite value was found,
+ * LBM_ESTATE before any step. */
 LBM_API int lbm_get_macro(lbm_handle h, void* rho, void* u, int field_dtype);
 
 /* Per-node alpha of the last output step (FP64, [nz][ny][nx]); requires
@@ -261,6 +267,18 @@ LBM_API int lbm_get_alpha(lbm_handle h, double* alpha);
  * out[1..D] = sum rho v_a, out[D+1] = sum rho |v|^2 / 2.  out is host
  * memory of D + 2 doubles.  Synchronises. */
 LBM_API int lbm_reduce(lbm_handle h, double* out);
+
+/* ELBM diagnostic mode (on = 1): every node whose alpha converged or was
+ * accepted from the guess also evaluates the entropy condition at that alpha
+ * by its definition (Eq. alpha_cond with per-direction logarithms, one more
+ * g evaluation per node) and accumulates the residual |g(alpha)| / a_2,
+ * a_2 = sum_i f_i x_i^2.  Clears all ELBM counters.  Off by default. */
+LBM_API int lbm_set_elbm_diagnostics(lbm_handle h, int on);
+
+/* Residual statistics of the steps run in diagnostic mode since it was set:
+ * out[0] mean, out[1] max of |g(alpha)| / a_2, out[2] nodes sampled (host
+ * memory, 3 doubles).  Synchronises. */
+LBM_API int lbm_get_elbm_entropy_error(lbm_handle h, double* out);
 
 /* Kinetic energy and enstrophy of the last step's velocity field (the
  * decaying-turbulence diagnostics of Sec. 5.2): out[0] = E = (1/2N) sum |v|^2,
@@ -310,7 +328,9 @@ LBM_API int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask);
 /* Guo body force of domain d. */
 LBM_API int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy);
 /* f = f_eq(rho, u) for domain d; rho [ny][nx], u [2][ny][nx].  Every domain
- * must be initialised before the first lbm_batch_step; afterwards LBM_ESTATE. */
+ * must be initialised before the first lbm_batch_step.  Called again later,
+ * it replaces domain d's state at the current step (the other domains and
+ * the batch's time are unchanged). */
 LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
                                int field_dtype);
 /* Choose block size, tile shape, rows per thread and CTAs per SM by timing a

@@ -762,6 +762,7 @@ struct AlphaResult {
     double alpha;
     int evals;
     int status;
+    double resid;   // |g(alpha)| / a_2 with the logarithm form (diagnostic mode), else 0
 };
 constexpr int ALPHA_NEEDS_LOG = 100;   // internal: series range left, redo with logs
 
@@ -1009,6 +1010,17 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             }
             LogEval<L> ev{f, x, A};
             ar = elbm_solve(ev, amax, p, guess, ar.evals);
+        }
+        if (p.elbm_diag && (ar.status == ALPHA_CONV || ar.status == ALPHA_GUARDED)) {
+            // entropy condition at the accepted alpha, by the definition
+            // (per-direction logarithms): also measures the series truncation
+            double Al = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) Al = fma(f[i] * x[i], log(f[i] / L::w(i)), Al);
+            LogEval<L> evd{f, x, Al};
+            double g, gp;
+            evd(ar.alpha, g, gp);
+            ar.resid = fabs(g) / ak[2];
         }
     }
     const double ab = ar.alpha * 0.5 * p.omega;     // alpha * beta, beta = 1/(2 tau)

@@ -487,8 +487,6 @@ int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* 
     if (d < 0 || d >= b->ndom || !rho || !u) return bfail(b, LBM_EINVAL, "bad arguments");
     if (field_dtype != LBM_FIELD_F32 && field_dtype != LBM_FIELD_F64)
         return bfail(b, LBM_EINVAL, "unknown field dtype");
-    if (b->t != 0)
-        return bfail(b, LBM_ESTATE, "initialise every domain before the first step");
     const DomDev& D = b->dom[d];
     const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
     const size_t nb = (size_t)D.nx * D.ny * fs;
@@ -504,14 +502,15 @@ int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* 
             "copy u");
         du = stage + nb;
     }
-    BCK(b, launch_init(0, b->dtype, dr, du, field_dtype == LBM_FIELD_F32, b->base + D.offA, D.nx,
-                       D.ny, 1, D.nxp, D.sq, 0, 0, 0, b->stream),
+    // the buffer that holds the current state (A before any step); the other
+    // domains and the batch's step parity and time are unchanged
+    BCK(b, launch_init(0, b->dtype, dr, du, field_dtype == LBM_FIELD_F32,
+                       b->base + (b->cur ? D.offB : D.offA), D.nx, D.ny, 1, D.nxp, D.sq, 0, 0, 0,
+                       b->stream),
         "init kernel");
     b->launches += 1;
     BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
     b->inited[d] = 1;
-    b->cur = 0;
-    b->t = 0;
     return LBM_OK;
 }
 

@@ -367,13 +367,26 @@ cudaError_t launch_diagnostics(int f64, const void* u, int D, int nx, int ny, in
 }
 
 // Sum the 64 replicas of the ELBM counters into 6 values.
+// Combine the counter replicas: out[0..5] counts, out[6] residual sum,
+// out[7] residual max, out[8] residual samples.
 __global__ void k_sum_ctr(const unsigned long long* __restrict__ rep, double* __restrict__ out)
 {
     const int k = threadIdx.x;
-    if (k >= 6) return;
-    unsigned long long s = 0;
-    for (int r = 0; r < 64; ++r) s += rep[r * 8 + k];
-    out[k] = (double)s;
+    if (k >= 9) return;
+    if (k == 6) {
+        double s = 0;
+        for (int r = 0; r < kCtrReplicas; ++r) s += __longlong_as_double(rep[r * kCtrStride + 6]);
+        out[6] = s;
+    } else if (k == 7) {
+        double m = 0;
+        for (int r = 0; r < kCtrReplicas; ++r)
+            m = fmax(m, __longlong_as_double(rep[r * kCtrStride + 7]));
+        out[7] = m;
+    } else {
+        unsigned long long s = 0;
+        for (int r = 0; r < kCtrReplicas; ++r) s += rep[r * kCtrStride + k];
+        out[k] = (double)s;
+    }
 }
 
 cudaError_t launch_sum_ctr(const unsigned long long* rep, double* out, cudaStream_t s)

@@ -54,6 +54,7 @@ struct lbm_ctx {
     BCEntry bc[kMaxBC] = {};  // velocity / pressure boundary conditions by id
     bool mlp_loaded = false, alpha_out = false, use_graph = false, round_nearest = false;
     bool aa = false;        // AA access pattern (one distribution array)
+    bool elbm_diag = false; // ELBM entropy-condition residual accumulation
     long long t = 0, launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -65,9 +66,9 @@ enum : size_t {
     MISC_PAIRS = 8,         // int pairs counter
     MISC_BAD = 16,          // int: mask value out of range
     MISC_RED = 64,          // 5 doubles reduction result
-    MISC_CTR_OUT = 128,     // 6 doubles summed counters
-    MISC_CTR = 256,         // 64 x 8 unsigned long long counter replicas
-    MISC_BYTES = 256 + 64 * 8 * 8
+    MISC_CTR_OUT = 128,     // 9 doubles: combined counters
+    MISC_CTR = 256,         // kCtrReplicas x kCtrStride unsigned long long counter replicas
+    MISC_BYTES = 256 + kCtrReplicas * kCtrStride * 8
 };
 
 static thread_local std::string g_err;
@@ -112,6 +113,23 @@ static bool is_device_ptr(const void* p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// An address the kernels can use for p: p itself for device or managed
+// memory, the mapped device address of pinned host memory (read or written
+// in place over the CPU-GPU link, no staging copy), or nullptr for pageable
+// host memory, which goes through the staging area.
+static const void* kernel_view(const void* p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
 }
 
 static void default_rates(double tau, double* s)
@@ -472,20 +490,20 @@ int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field
     if (r) return r;
     const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
     const size_t nb = (size_t)h->N * fs;
-    const void* drho = rho;
-    const void* du = u;
+    const void* drho = kernel_view(rho);
+    const void* du = kernel_view(u);
     char* stage = at<char>(h, h->off_stage);
-    bool host_in = false;
-    if (!is_device_ptr(rho)) {
+    // host memory (pinned: read in place; pageable: staged) is released to the
+    // caller only after the init kernel has read it
+    const bool host_in = !is_device_ptr(rho) || !is_device_ptr(u);
+    if (!drho) {
         CK(h, cudaMemcpyAsync(stage, rho, nb, cudaMemcpyHostToDevice, h->stream), "copy rho");
         drho = stage;
-        host_in = true;
     }
-    if (!is_device_ptr(u)) {
+    if (!du) {
         CK(h, cudaMemcpyAsync(stage + nb, u, nb * h->D, cudaMemcpyHostToDevice, h->stream),
            "copy u");
         du = stage + nb;
-        host_in = true;
     }
     CK(h, launch_init(h->lattice, h->dtype, drho, du, field_dtype == LBM_FIELD_F32,
                       h->base + h->off_A, h->nx, h->ny, h->nz, h->nxp, h->sq,
@@ -537,6 +555,7 @@ static StepParams make_params(lbm_ctx* h)
     p.smag_cs2_f = (float)p.smag_cs2;
     for (int a = 0; a < 3; ++a) p.F_f[a] = (float)p.F[a];
     p.alpha_mode = h->alpha_mode; p.max_iter = h->max_iter;
+    p.elbm_diag = h->elbm_diag ? 1 : 0;
     p.guard_steps = h->guard_steps; p.feq_variant = h->feq_variant;
     p.tol = h->tol; p.skip_eps = h->skip_eps; p.guard_tol = h->guard_tol;
     p.mlp = at<float>(h, h->off_mlp);
@@ -649,13 +668,14 @@ static int get_field(lbm_ctx* h, size_t src_off, int nfields, void* dst, int fie
     const int dst_f32 = field_dtype == LBM_FIELD_F32;
     const size_t fs = dst_f32 ? 4 : 8;
     const size_t nb = (size_t)h->N * fs * nfields;
-    const bool dev = is_device_ptr(dst);
-    void* out = dev ? dst : h->base + h->off_stage;
+    // device or pinned host memory is written in place; pageable memory is staged
+    void* view = const_cast<void*>(kernel_view(dst));
+    void* out = view ? view : h->base + h->off_stage;
     CK(h, launch_pack(h->rsize == 8, h->base + src_off, dst_f32, out, nfields, h->nx, h->ny,
                       h->nz, h->nxp, h->sq, h->stream),
        "pack kernel");
     h->launches += 1;
-    if (!dev)
+    if (!view)
         CK(h, cudaMemcpyAsync(dst, out, nb, cudaMemcpyDeviceToHost, h->stream), "copy out");
     return LBM_OK;
 }
@@ -705,6 +725,40 @@ int lbm_reduce(lbm_handle h, double* out)
     CK(h, cudaMemcpyAsync(tmp, dres, sizeof tmp, cudaMemcpyDeviceToHost, h->stream), "copy sums");
     int r = sync_status(h);
     for (int k = 0; k < h->D + 2; ++k) out[k] = tmp[k];
+    return r;
+}
+
+int lbm_set_elbm_diagnostics(lbm_handle h, int on)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
+    int r = ensure_memory(h);
+    if (r) return r;
+    CK(h, cudaMemsetAsync(h->base + h->off_misc + MISC_CTR, 0,
+                          (size_t)kCtrReplicas * kCtrStride * 8, h->stream),
+       "clear counters");
+    h->elbm_diag = on != 0;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_get_elbm_entropy_error(lbm_handle h, double* out)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
+    int r = ensure_memory(h);
+    if (r) return r;
+    double* d = at<double>(h, h->off_misc + MISC_CTR_OUT);
+    CK(h, launch_sum_ctr(at<unsigned long long>(h, h->off_misc + MISC_CTR), d, h->stream),
+       "counter kernel");
+    h->launches += 1;
+    double tmp[9];
+    CK(h, cudaMemcpyAsync(tmp, d, sizeof tmp, cudaMemcpyDeviceToHost, h->stream), "copy");
+    r = sync_status(h);
+    out[0] = tmp[8] > 0 ? tmp[6] / tmp[8] : 0.0;
+    out[1] = tmp[7];
+    out[2] = tmp[8];
     return r;
 }
 

@@ -273,6 +273,10 @@ enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2, MODEL_REG = 3, MODEL_SMAG =
 // bits 2..5 boundary condition id + 1 (0: none)
 enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2, FLAG_BC_SHIFT = 2, FLAG_BC_MASK = 0x3c };
 constexpr int kMaxBC = 15;
+// ELBM counter replicas: slots 0..5 evals, skipped, clamped, at cap, guarded,
+// updated; 6 sum of |g(alpha)|/a2 (double bits), 7 its max (double bits),
+// 8 residual samples
+constexpr int kCtrReplicas = 64, kCtrStride = 16;
 
 // One velocity or pressure boundary condition (Sec. 2.3's list).
 struct BCEntry {
@@ -302,7 +306,7 @@ struct StepParams {
     void* u;                   // [D][sq]
     double* alpha_out;         // ELBM per-node alpha or nullptr
     unsigned int* status;      // STATUS_* bits
-    unsigned long long* elbm_ctr;  // 6 counters or nullptr
+    unsigned long long* elbm_ctr;  // counter replicas (kCtrStride slots each) or nullptr
     float* pairs_X;            // ELBM training-pair capture (nullptr = off)
     double* pairs_y;
     int* pairs_count;
@@ -330,6 +334,7 @@ struct StepParams {
     BCEntry bc[kMaxBC];        // boundary conditions by id
     // ELBM
     int alpha_mode, max_iter, guard_steps, feq_variant;
+    int elbm_diag;             // 1: accumulate the entropy-condition residual
     double tol, skip_eps, guard_tol;
     const float* mlp;          // MLP_NPARAM floats (BF16-rounded weights)
 };

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kStepThreads)
     using T = typename S::T;
     constexpr bool ELBM = (MODEL == MODEL_ELBM);
     __shared__ float smlp[ELBM ? MLP_NPARAM : 1];
-    __shared__ unsigned long long sctr[ELBM ? (kStepThreads / 32) * 6 : 1];
+    __shared__ unsigned long long sctr[ELBM ? (kStepThreads / 32) * 9 : 1];
     if (ELBM && p.alpha_mode == 2) {
         for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < MLP_NPARAM;
              k += blockDim.x * blockDim.y)
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kStepThreads)
         active = false;
     }
     int evals = 0, astat = -1;
+    double resid = 0.0;
     if (active) {
         if (MASK && (fl & FLAG_NEAR_WALL)) {
             const uint32_t lk = __ldg(p.links + n);
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(kStepThreads)
             ar = elbm_collide<L, R>(d, p, smlp, rho, v, feat, have_feat);
             evals = ar.evals;
             astat = ar.status;
+            resid = ar.resid;
         }
         // destination of population i: own node, slot i (AB); node x + e_i,
         // slot i (AA pull/push); own node, slot opp(i) (AA in place)
@@ -172,29 +174,51 @@ __global__ void __launch_bounds__(kStepThreads)
         }
     }
     if (ELBM && p.elbm_ctr) {
-        // counters: evals, skipped, clamped, at cap, guarded, updated nodes
-        unsigned long long c[6] = {(unsigned long long)evals, astat == ALPHA_SKIP,
+        // counters: evals, skipped, clamped, at cap, guarded, updated nodes,
+        // and in diagnostic mode the residual sum, max and sample count
+        const bool hr = p.elbm_diag && (astat == ALPHA_CONV || astat == ALPHA_GUARDED);
+        unsigned long long c[7] = {(unsigned long long)evals, astat == ALPHA_SKIP,
                                    astat == ALPHA_CLAMP, astat == ALPHA_NOCONV,
-                                   astat == ALPHA_GUARDED, astat >= 0};
+                                   astat == ALPHA_GUARDED, astat >= 0, hr};
+        double rs = hr ? resid : 0.0, rm = rs;
         const int lane = threadIdx.x & 31;
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
         const int warp = tid >> 5;
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_down_sync(0xffffffffu, c[k], o);
-        if (lane == 0)
+            for (int k = 0; k < 7; ++k) c[k] += __shfl_down_sync(0xffffffffu, c[k], o);
+            rs += __shfl_down_sync(0xffffffffu, rs, o);
+            rm = fmax(rm, __shfl_down_sync(0xffffffffu, rm, o));
+        }
+        if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) sctr[warp * 6 + k] = c[k];
+            for (int k = 0; k < 7; ++k) sctr[warp * 9 + k] = c[k];
+            sctr[warp * 9 + 7] = __double_as_longlong(rs);
+            sctr[warp * 9 + 8] = __double_as_longlong(rm);
+        }
         __syncthreads();
-        if (tid < 6) {
-            unsigned long long s = 0;
+        if (tid < 9) {
             const int nw = (blockDim.x * blockDim.y) >> 5;
-            for (int w = 0; w < nw; ++w) s += sctr[w * 6 + tid];
-            // spread over 64 replicas to limit contention on one address
-            const int rep = (blockIdx.x + blockIdx.y * 7 + blockIdx.z * 13) & 63;
-            if (s) atomicAdd(&p.elbm_ctr[rep * 8 + tid], s);
-            if (tid == 3 && s) atomicOr(p.status, STATUS_NOCONV);
+            // spread over the replicas to limit contention on one address
+            const int rep = (blockIdx.x + blockIdx.y * 7 + blockIdx.z * 13) & (kCtrReplicas - 1);
+            unsigned long long* slot = p.elbm_ctr + (size_t)rep * kCtrStride;
+            if (tid < 7) {
+                unsigned long long s = 0;
+                for (int w = 0; w < nw; ++w) s += sctr[w * 9 + tid];
+                // slots 0..5, and the sample count in slot 8
+                if (s) atomicAdd(&slot[tid < 6 ? tid : 8], s);
+                if (tid == 3 && s) atomicOr(p.status, STATUS_NOCONV);
+            } else if (tid == 7) {
+                double s = 0;
+                for (int w = 0; w < nw; ++w) s += __longlong_as_double(sctr[w * 9 + 7]);
+                if (s > 0) atomicAdd(reinterpret_cast<double*>(&slot[6]), s);
+            } else {
+                double m = 0;
+                for (int w = 0; w < nw; ++w) m = fmax(m, __longlong_as_double(sctr[w * 9 + 8]));
+                // non-negative doubles order like their bit patterns
+                if (m > 0) atomicMax(&slot[7], (unsigned long long)__double_as_longlong(m));
+            }
         }
     }
 }

@@ -104,6 +104,8 @@ _PROTOS = {
     "lbm_reduce": (_i, [_vp, _vp]),
     "lbm_kinetic_energy_enstrophy": (_i, [_vp, _vp]),
     "lbm_get_elbm_stats": (_i, [_vp, _vp]),
+    "lbm_set_elbm_diagnostics": (_i, [_vp, _i]),
+    "lbm_get_elbm_entropy_error": (_i, [_vp, _vp]),
     "lbm_state_bytes": (_sz, [_vp]),
     "lbm_get_state": (_i, [_vp, _vp, ctypes.POINTER(_ll)]),
     "lbm_set_state": (_i, [_vp, _vp, _ll]),
@@ -313,6 +315,17 @@ def lbm_kinetic_energy_enstrophy(h):
     out = np.zeros(2)
     _check(_L.lbm_kinetic_energy_enstrophy(h, _ptr(out)), h)
     return float(out[0]), float(out[1])
+
+
+def lbm_set_elbm_diagnostics(h, on):
+    _check(_L.lbm_set_elbm_diagnostics(h, int(bool(on))), h)
+
+
+def lbm_get_elbm_entropy_error(h):
+    """(mean, max, samples) of |g(alpha)| / a_2 since diagnostics were set."""
+    out = np.zeros(3)
+    _check(_L.lbm_get_elbm_entropy_error(h, _ptr(out)), h)
+    return float(out[0]), float(out[1]), int(out[2])
 
 
 def lbm_get_elbm_stats(h):

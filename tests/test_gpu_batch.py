@@ -145,3 +145,36 @@ def test_batch_errors():
         lbm.lbm_batch_step(b, 1)                  # domains not initialised
     assert ei.value.code == lbm.LBM_ESTATE
     lbm.lbm_batch_destroy(b)
+
+
+def _single(spec, rho, u, steps, dtype):
+    sim = lbm.Simulation(spec["nx"], spec["ny"], 1, lbm.LBM_D2Q9, lbm.LBM_BGK, spec["tau"], dtype)
+    sim.set_geometry(wl.batch_channel_mask(spec))
+    sim.set_force(spec["gx"], 0.0)
+    sim.init(rho, u)
+    sim.step(steps)
+    r, v = sim.macro()
+    sim.close()
+    return r, v
+
+
+@pytest.mark.parametrize("t_reinit", [5, 6])
+def test_batch_reinit_one_domain_mid_run(t_reinit):
+    """Re-initialising domain 1 after t steps (odd and even t: the state is in
+    either buffer) restarts that domain only: after 4 more steps it equals a
+    fresh single-domain run of 4 steps, and the other domains equal
+    uninterrupted runs of t + 4 steps (bitwise)."""
+    specs = _specs(3, seed=7)
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_step(b, t_reinit)
+    rho1, u1 = _init_state(specs[1], 555)
+    lbm.lbm_batch_init_equilibrium(b, 1, rho1, u1)
+    lbm.lbm_batch_step(b, 4)
+    got = _batch_fields(b, specs)
+    lbm.lbm_batch_destroy(b)
+    r, v = _single(specs[1], rho1, u1, 4, lbm.LBM_F32S)
+    assert np.array_equal(got[1][0], r) and np.array_equal(got[1][1], v)
+    for d in (0, 2):
+        rho, u = _init_state(specs[d], 100 + d)
+        r, v = _single(specs[d], rho, u, t_reinit + 4, lbm.LBM_F32S)
+        assert np.array_equal(got[d][0], r) and np.array_equal(got[d][1], v)

@@ -148,3 +148,28 @@ def test_mlp_guarded_oracle_parity(trained):
     ro, uo, _, _ = oracle.run(p, F, steps)
     import analytic as an
     assert an.rel_l2(ug, uo) < 1e-5 and an.rel_l2(rg, ro) < 1e-5
+
+
+def test_entropy_condition_error_newton_vs_guesses(trained):
+    """Diagnostic mode measures |g(alpha)| / a_2 at the accepted alpha with the
+    logarithm form: tiny for Newton (tolerance 1e-12 on alpha), bounded by the
+    guard tolerance for guesses accepted after two guarded steps."""
+    P, n, tau = trained["P"], trained["n"], trained["tau"]
+    res = {}
+    for mode in (lbm.LBM_ALPHA_NEWTON, lbm.LBM_ALPHA_SERIES_GUARDED, lbm.LBM_ALPHA_MLP_GUARDED):
+        sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
+        lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-4)
+        lbm.lbm_load_alpha_mlp(sim.h, P)
+        sim.set_state(trained["state"], trained["t"])
+        lbm.lbm_set_elbm_diagnostics(sim.h, 1)
+        sim.step(2)
+        mean, mx, cnt = lbm.lbm_get_elbm_entropy_error(sim.h)
+        st = lbm.lbm_get_elbm_stats(sim.h)
+        sim.close()
+        res[mode] = (mean, mx, cnt, st)
+    for mode, (mean, mx, cnt, st) in res.items():
+        print(f"mode {mode}: |g|/a2 mean {mean:.3e} max {mx:.3e} over {cnt} nodes")
+        assert cnt > 0.5 * st[5]
+    assert res[lbm.LBM_ALPHA_NEWTON][1] < 1e-8
+    assert res[lbm.LBM_ALPHA_MLP_GUARDED][1] < 1e-4
+    assert res[lbm.LBM_ALPHA_SERIES_GUARDED][1] < 1e-4
