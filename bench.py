@@ -341,7 +341,7 @@ def run_multi(args):
         e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
         lbm.lbm_multi_destroy(m)
     glups = nodes * args.steps / (ms * 1e-3) / 1e9
-    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (1 if mask is not None else 0)
+    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (4 if mask is not None else 0)
     per_launch_s = ms / 1e3 / args.steps
     achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_kind = peaks()
@@ -509,7 +509,7 @@ def run_ours(args):
     glups = job_glups(nodes, args.steps, world, ms_max)
     fluid = int((mask != 1).sum()) if mask is not None else nodes
     per_launch_s = ms / 1e3 / args.steps
-    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (1 if mask is not None else 0)
+    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (4 if mask is not None else 0)
     achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_kind = peaks()
     traffic = traffic_for(args.workload, args.dtype)

@@ -337,8 +337,15 @@ LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, cons
  * few steps of each candidate (CUDA events); restores the state afterwards. */
 LBM_API int lbm_batch_autotune(lbm_batch b);
 /* Current launch configuration (5 ints): threads per CTA, CTAs, tile width,
- * tile rows, rows per thread and pass (1 or 2). */
+ * tile rows, rows per thread and pass (1, 2 or 4). */
 LBM_API int lbm_batch_get_config(lbm_batch b, int* out5);
+/* Set the launch configuration (5 ints, as lbm_batch_get_config returns
+ * them), e.g. one found by an earlier lbm_batch_autotune.  Threads per CTA
+ * at most 512 and a multiple of the tile width, itself a multiple of 32;
+ * rows per thread and pass 1, 2 or 4; CTAs between 1 and the number that can
+ * be co-resident (the launch is cooperative).  LBM_EINVAL otherwise, with
+ * the configuration unchanged. */
+LBM_API int lbm_batch_set_config(lbm_batch b, const int* in5);
 /* Advance every domain n steps in one persistent launch.  The per-step
  * grid barrier spins a bounded number of times; if it gives up, the kernel
  * exits and the next synchronising call returns LBM_ETIMEOUT. */

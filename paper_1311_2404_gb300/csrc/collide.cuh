@@ -157,22 +157,18 @@ __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R
 //        tau = tau0 + tau_t, tau_t = (sqrt(tau0^2 + 4 C_S^2 |Q| / c_s^4) - tau0)/2,
 //        |Q| = (Q_ab Q_ab)^(1/2); then LBGK with that tau.
 // ---------------------------------------------------------------------------
+// Even and odd parts of one opposite pair's equilibrium deviation at
+// velocity u (m15 = -3/2 u^2), computed where they are used: the operators
+// below recompute them in their update pass instead of keeping per-pair
+// arrays alive across passes (registers, not FLOPs, limit these kernels).
 template <class L, class R>
-__host__ __device__ __forceinline__ void eq_pairs(R rho, R drho, R u0, R u1, R u2,
-                                                  R (&ev)[(L::Q - 1) / 2],
-                                                  R (&od)[(L::Q - 1) / 2], R& e0)
+__host__ __device__ __forceinline__ void eq_pair(int i, R rho, R drho, R u0, R u1, R u2, R m15,
+                                                 R& ev, R& od)
 {
-    const R m15 = R(-1.5) * fma(u0, u0, fma(u1, u1, u2 * u2));
-    const R w0 = (R)L::w(0);
-    e0 = fma(w0 * rho, m15, w0 * drho);
-#pragma unroll
-    for (int q = 0; q < (L::Q - 1) / 2; ++q) {
-        const int i = 2 * q + 1;
-        const R wi = (R)L::w(i);
-        const R eu = edot<L, R>(i, u0, u1, u2);
-        ev[q] = fma(wi * rho, fma(R(4.5) * eu, eu, m15), wi * drho);
-        od[q] = (first_order_coef<L, R>(i) * rho) * eu;
-    }
+    const R wi = (R)L::w(i);
+    const R eu = edot<L, R>(i, u0, u1, u2);
+    ev = fma(wi * rho, fma(R(4.5) * eu, eu, m15), wi * drho);
+    od = (first_order_coef<L, R>(i) * rho) * eu;
 }
 
 template <class L, class R, bool SMAG>
@@ -181,41 +177,34 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
                                                      R& rho_out, R (&v)[3])
 {
     constexpr int NP = (L::Q - 1) / 2;
-    R S[NP], A[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        S[q] = d[2 * q + 1] + d[2 * q + 2];
-        A[q] = d[2 * q + 1] - d[2 * q + 2];
-    }
-    R drho = d[0];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) drho += S[q];
-    R j[3] = {R(0), R(0), R(0)};
+    // pass 1: mass, momentum, and the flux about fe
+    R drho = d[0], j0 = R(0), j1 = R(0), j2 = R(0);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const int i = 2 * q + 1;
-        if (L::ex(i)) j[0] = L::ex(i) > 0 ? j[0] + A[q] : j[0] - A[q];
-        if (L::ey(i)) j[1] = L::ey(i) > 0 ? j[1] + A[q] : j[1] - A[q];
-        if (L::ez(i)) j[2] = L::ez(i) > 0 ? j[2] + A[q] : j[2] - A[q];
+        drho += d[i] + d[i + 1];
+        const R A = d[i] - d[i + 1];
+        if (L::ex(i)) j0 = L::ex(i) > 0 ? j0 + A : j0 - A;
+        if (L::ey(i)) j1 = L::ey(i) > 0 ? j1 + A : j1 - A;
+        if (L::ez(i)) j2 = L::ez(i) > 0 ? j2 + A : j2 - A;
     }
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
-    v[0] = fma(R(0.5), F0, j[0]) * irho;
-    v[1] = fma(R(0.5), F1, j[1]) * irho;
-    v[2] = (L::D == 3) ? fma(R(0.5), F2, j[2]) * irho : R(0);
+    v[0] = fma(R(0.5), F0, j0) * irho;
+    v[1] = fma(R(0.5), F1, j1) * irho;
+    v[2] = (L::D == 3) ? fma(R(0.5), F2, j2) * irho : R(0);
     const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
-    // equilibrium the flux is taken about (even/odd pair parts, rest value)
-    R ev[NP], od[NP], e0;
-    if (SMAG)
-        eq_pairs<L, R>(rho, drho, v[0], v[1], v[2], ev, od, e0);
-    else
-        eq_pairs<L, R>(rho, drho, j[0] * irho, j[1] * irho, (L::D == 3) ? j[2] * irho : R(0),
-                       ev, od, e0);
+    // the velocity fe is taken at: v (SMAG), u = j / rho (REG)
+    const R e0 = SMAG ? v[0] : j0 * irho, e1 = SMAG ? v[1] : j1 * irho,
+            e2 = SMAG ? v[2] : ((L::D == 3) ? j2 * irho : R(0));
+    const R m15e = R(-1.5) * fma(e0, e0, fma(e1, e1, e2 * e2));
     R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const int i = 2 * q + 1;
-        const R ns = fma(R(-2), ev[q], S[q]);        // pair sum of f - fe
+        R ev, od;
+        eq_pair<L, R>(i, rho, drho, e0, e1, e2, m15e, ev, od);
+        const R ns = fma(R(-2), ev, d[i] + d[i + 1]);   // pair sum of f - fe
         const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
         if (ex) P[0] += ns;
         if (ey) P[1] += ns;
@@ -232,15 +221,21 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
         om = R(1) / (tau0 + tau_t);
     }
     const R cf = fma(R(-0.5), om, R(1));
+    const R w0 = (R)L::w(0);
+    const R m15v = R(-1.5) * fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2]));
+    const R e0v = fma(w0 * rho, m15v, w0 * drho);       // rest equilibrium at v
+    // pass 2: relax, pair by pair
     if (SMAG) {
-        R d0 = fma(om, e0 - d[0], d[0]);
-        if (has_force) d0 = fma(cf, R(-3) * (R)L::w(0) * vF, d0);
+        R d0 = fma(om, e0v - d[0], d[0]);
+        if (has_force) d0 = fma(cf, R(-3) * w0 * vF, d0);
         d[0] = d0;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const int i = 2 * q + 1;
-            R dp = fma(om, (ev[q] + od[q]) - d[i], d[i]);
-            R dm = fma(om, (ev[q] - od[q]) - d[i + 1], d[i + 1]);
+            R ev, od;
+            eq_pair<L, R>(i, rho, drho, v[0], v[1], v[2], m15v, ev, od);
+            R dp = fma(om, (ev + od) - d[i], d[i]);
+            R dm = fma(om, (ev - od) - d[i + 1], d[i + 1]);
             if (has_force) {
                 const R wi = (R)L::w(i);
                 const R eu = edot<L, R>(i, v[0], v[1], v[2]);
@@ -254,20 +249,13 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
             d[i + 1] = dm;
         }
     } else {
-        // collision equilibrium at v (equal to fe without a force)
-        R evv[NP], odv[NP], e0v;
-        if (has_force) {
-            eq_pairs<L, R>(rho, drho, v[0], v[1], v[2], evv, odv, e0v);
-        } else {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) { evv[q] = ev[q]; odv[q] = od[q]; }
-            e0v = e0;
-        }
+        // f~ = fe + f_reg; f' = f~ + omega (f_eq(v) - f~) + Guo term
         const R tr3 = (P[0] + P[1] + P[2]) * R(1.0 / 3.0);
         {
-            const R ft = fma((R)L::w(0) * R(4.5), -tr3, e0);
+            const R e0u = fma(w0 * rho, m15e, w0 * drho);
+            const R ft = fma(w0 * R(4.5), -tr3, e0u);
             R d0 = fma(om, e0v - ft, ft);
-            if (has_force) d0 = fma(cf, R(-3) * (R)L::w(0) * vF, d0);
+            if (has_force) d0 = fma(cf, R(-3) * w0 * vF, d0);
             d[0] = d0;
         }
 #pragma unroll
@@ -284,9 +272,17 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
             if (ex && ez) ePe = (ex * ez > 0) ? fma(R(2), P[4], ePe) : fma(R(-2), P[4], ePe);
             if (ey && ez) ePe = (ey * ez > 0) ? fma(R(2), P[5], ePe) : fma(R(-2), P[5], ePe);
             const R freg = wi * R(4.5) * (ePe - tr3);
-            const R ftp = (ev[q] + od[q]) + freg, ftm = (ev[q] - od[q]) + freg;
-            R dp = fma(om, (evv[q] + odv[q]) - ftp, ftp);
-            R dm = fma(om, (evv[q] - odv[q]) - ftm, ftm);
+            R evu, odu, evv, odv;
+            eq_pair<L, R>(i, rho, drho, e0, e1, e2, m15e, evu, odu);
+            if (has_force)
+                eq_pair<L, R>(i, rho, drho, v[0], v[1], v[2], m15v, evv, odv);
+            else {
+                evv = evu;
+                odv = odu;
+            }
+            const R ftp = (evu + odu) + freg, ftm = (evu - odu) + freg;
+            R dp = fma(om, (evv + odv) - ftp, ftp);
+            R dm = fma(om, (evv - odv) - ftm, ftm);
             if (has_force) {
                 const R eu = edot<L, R>(i, v[0], v[1], v[2]);
                 const R eF = edot<L, R>(i, F0, F1, F2);
@@ -319,126 +315,128 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
 //    with e_it != 0 (two edge links; the four body diagonals on D3Q15);
 //  regularized: unknown f_i as Zou-He before the correction, then
 //    f_i = f_eq_i + w_i 9/2 (e_i e_i - I/3) : Pi^neq - 3/2 w_i e_i . F.
-// Rare nodes: plain f-form arithmetic in the compute type.
+// Rare nodes; deviation-form arithmetic in the compute type, as in the collisions.
 // ---------------------------------------------------------------------------
 template <class L, class R>
 __device__ __forceinline__ void bc_apply(R (&d)[L::Q], const BCEntry& b, R F0, R F1, R F2)
 {
+    // Deviation form throughout (d = f - w), like the collision operators:
+    // on a symmetric lattice the weights of the e.n = 0 and e.n < 0 sets
+    // satisfy W_0 + 2 W_out = 1, so S_0 + 2 S_out = 1 + (D_0 + 2 D_out) with D
+    // the deviation sums; w_opp(i) = w_i, so the bounce-back of the
+    // non-equilibrium part is d_i = d_opp(i) + (e_i - e_opp(i)) equilibrium
+    // deviations; momenta are sums of e d.  The normal's axis is a run-time
+    // value: components are picked with selects (no run-time indexed arrays,
+    // which would live in local memory).
     constexpr int Q = L::Q, D = L::D;
-    // the normal's axis is a run-time value: components are picked with
-    // selects (no run-time indexed arrays, which would live in local memory)
     const int ax = b.axis, sg = b.sign;
     auto pick = [ax](R c0, R c1, R c2) { return ax == 0 ? c0 : (ax == 1 ? c1 : c2); };
-    R f[Q];
-    R S0 = R(0), So = R(0);
+    auto en = [&](int i) { return sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i))); };
+    R D0 = R(0), Do = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        f[i] = (R)L::w(i) + d[i];
-        const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
-        if (en == 0) S0 += f[i];
-        else if (en < 0) So += f[i];
+        const int e = en(i);
+        if (e == 0) D0 += d[i];
+        else if (e < 0) Do += d[i];
     }
     const R Fax = pick(F0, F1, F2);
     const R Fn = sg > 0 ? Fax : -Fax;
-    const R known = fma(R(2), So, S0) - R(0.5) * Fn;
-    R rho, v0, v1, v2;
+    const R K = fma(R(2), Do, D0) - R(0.5) * Fn;    // S_0 + 2 S_out - F_n/2 - 1
+    R rho, drho, v0, v1, v2;
     if (b.kind == 1) {
         v0 = sel<R>(b.val_f[0], b.val[0]);
         v1 = sel<R>(b.val_f[1], b.val[1]);
         v2 = D == 3 ? sel<R>(b.val_f[2], b.val[2]) : R(0);
         const R vax = pick(v0, v1, v2);
-        rho = known / (R(1) - (sg > 0 ? vax : -vax));
+        const R vn = sg > 0 ? vax : -vax;
+        drho = (K + vn) / (R(1) - vn);                // rho = (1 + K) / (1 - v_n)
+        rho = R(1) + drho;
     } else {
         rho = sel<R>(b.val_f[0], b.val[0]);
-        const R vn = R(1) - known / rho;
+        drho = rho - R(1);
+        const R vn = (drho - K) / rho;                // 1 - (1 + K) / rho
         const R va = sg > 0 ? vn : -vn;
         v0 = ax == 0 ? va : R(0);
         v1 = ax == 1 ? va : R(0);
         v2 = ax == 2 ? va : R(0);
     }
-    const R usq = fma(v0, v0, fma(v1, v1, v2 * v2));
-    R feq[Q];
+    const R m15 = R(-1.5) * fma(v0, v0, fma(v1, v1, v2 * v2));
+    R qe[Q];   // equilibrium deviations f_eq - w
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const R eu = edot<L, R>(i, v0, v1, v2);
-        feq[i] = (R)L::w(i) * rho *
-                 fma(R(3), eu, fma(R(4.5) * eu, eu, fma(R(-1.5), usq, R(1))));
+        const R wi = (R)L::w(i);
+        qe[i] = fma(wi * rho, fma(R(3), eu, fma(R(4.5) * eu, eu, m15)), wi * drho);
     }
     if (b.method == 0) {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            f[i] = fma(R(-1.5) * (R)L::w(i), edot<L, R>(i, F0, F1, F2), feq[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
-            if (en > 0) f[i] = f[L::opp(i)] + (feq[i] - feq[L::opp(i)]);
-        }
-        if (b.method == 1) {
-            R J0 = R(0), J1 = R(0), J2 = R(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                if (L::ex(i)) J0 = L::ex(i) > 0 ? J0 + f[i] : J0 - f[i];
-                if (L::ey(i)) J1 = L::ey(i) > 0 ? J1 + f[i] : J1 - f[i];
-                if (L::ez(i)) J2 = L::ez(i) > 0 ? J2 + f[i] : J2 - f[i];
-            }
-            const R dJ0 = fma(rho, v0, R(-0.5) * F0) - J0;
-            const R dJ1 = fma(rho, v1, R(-0.5) * F1) - J1;
-            const R dJ2 = D == 3 ? fma(rho, v2, R(-0.5) * F2) - J2 : R(0);
-            const R dJn = pick(dJ0, dJ1, dJ2);
-            constexpr int tlen = (Q == 15) ? 3 : 2;      // shortest unknown links with e_t != 0
-            constexpr R tshare = (Q == 15) ? R(0.25) : R(0.5);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int en = sg * (ax == 0 ? L::ex(i) : (ax == 1 ? L::ey(i) : L::ez(i)));
-                if (en <= 0) continue;
-                const int l2 = L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
-                if (l2 == 1) f[i] += sg > 0 ? dJn : -dJn;      // the link along n
-                if (l2 == tlen) {
-                    if (L::ex(i) && ax != 0) f[i] = fma(L::ex(i) > 0 ? tshare : -tshare, dJ0, f[i]);
-                    if (L::ey(i) && ax != 1) f[i] = fma(L::ey(i) > 0 ? tshare : -tshare, dJ1, f[i]);
-                    if (L::ez(i) && ax != 2) f[i] = fma(L::ez(i) > 0 ? tshare : -tshare, dJ2, f[i]);
-                }
-            }
-        } else {
-            // Hermite coefficient a2 = sum (f - f_eq)(e e - I/3): the node's
-            // mass defect m = sum (f - f_eq) (F_n/2 under a force) enters the
-            // diagonal
-            R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
-            R m = R(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const R nq = f[i] - feq[i];
-                const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-                m += nq;
-                if (ex) P[0] += nq;
-                if (ey) P[1] += nq;
-                if (ez) P[2] += nq;
-                if (ex && ey) P[3] = (ex * ey > 0) ? P[3] + nq : P[3] - nq;
-                if (ex && ez) P[4] = (ex * ez > 0) ? P[4] + nq : P[4] - nq;
-                if (ey && ez) P[5] = (ey * ez > 0) ? P[5] + nq : P[5] - nq;
-            }
-#pragma unroll
-            for (int a = 0; a < D; ++a) P[a] = fma(R(-1.0 / 3.0), m, P[a]);
-            const R tr3 = (P[0] + P[1] + P[2]) * R(1.0 / 3.0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-                R ePe = R(0);
-                if (ex) ePe += P[0];
-                if (ey) ePe += P[1];
-                if (ez) ePe += P[2];
-                if (ex && ey) ePe = (ex * ey > 0) ? fma(R(2), P[3], ePe) : fma(R(-2), P[3], ePe);
-                if (ex && ez) ePe = (ex * ez > 0) ? fma(R(2), P[4], ePe) : fma(R(-2), P[4], ePe);
-                if (ey && ez) ePe = (ey * ez > 0) ? fma(R(2), P[5], ePe) : fma(R(-2), P[5], ePe);
-                const R wi = (R)L::w(i);
-                f[i] = fma(R(4.5) * wi, ePe - tr3,
-                           fma(R(-1.5) * wi, edot<L, R>(i, F0, F1, F2), feq[i]));
-            }
-        }
+            d[i] = fma(R(-1.5) * (R)L::w(i), edot<L, R>(i, F0, F1, F2), qe[i]);
+        return;
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = f[i] - (R)L::w(i);
+    for (int i = 0; i < Q; ++i)
+        if (en(i) > 0) d[i] = d[L::opp(i)] + (qe[i] - qe[L::opp(i)]);
+    if (b.method == 1) {
+        R J0 = R(0), J1 = R(0), J2 = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (L::ex(i)) J0 = L::ex(i) > 0 ? J0 + d[i] : J0 - d[i];
+            if (L::ey(i)) J1 = L::ey(i) > 0 ? J1 + d[i] : J1 - d[i];
+            if (L::ez(i)) J2 = L::ez(i) > 0 ? J2 + d[i] : J2 - d[i];
+        }
+        const R dJ0 = fma(rho, v0, R(-0.5) * F0) - J0;
+        const R dJ1 = fma(rho, v1, R(-0.5) * F1) - J1;
+        const R dJ2 = D == 3 ? fma(rho, v2, R(-0.5) * F2) - J2 : R(0);
+        const R dJn = pick(dJ0, dJ1, dJ2);
+        constexpr int tlen = (Q == 15) ? 3 : 2;      // shortest unknown links with e_t != 0
+        constexpr R tshare = (Q == 15) ? R(0.25) : R(0.5);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (en(i) <= 0) continue;
+            const int l2 = L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
+            if (l2 == 1) d[i] += sg > 0 ? dJn : -dJn;      // the link along n
+            if (l2 == tlen) {
+                if (L::ex(i) && ax != 0) d[i] = fma(L::ex(i) > 0 ? tshare : -tshare, dJ0, d[i]);
+                if (L::ey(i) && ax != 1) d[i] = fma(L::ey(i) > 0 ? tshare : -tshare, dJ1, d[i]);
+                if (L::ez(i) && ax != 2) d[i] = fma(L::ez(i) > 0 ? tshare : -tshare, dJ2, d[i]);
+            }
+        }
+        return;
+    }
+    // regularized: Hermite coefficient a2 = sum (f - f_eq)(e e - I/3); the
+    // node's mass defect m = sum (f - f_eq) (F_n/2 under a force) enters the
+    // diagonal
+    R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
+    R m = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R nq = d[i] - qe[i];
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        m += nq;
+        if (ex) P[0] += nq;
+        if (ey) P[1] += nq;
+        if (ez) P[2] += nq;
+        if (ex && ey) P[3] = (ex * ey > 0) ? P[3] + nq : P[3] - nq;
+        if (ex && ez) P[4] = (ex * ez > 0) ? P[4] + nq : P[4] - nq;
+        if (ey && ez) P[5] = (ey * ez > 0) ? P[5] + nq : P[5] - nq;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) P[a] = fma(R(-1.0 / 3.0), m, P[a]);
+    const R tr3 = (P[0] + P[1] + P[2]) * R(1.0 / 3.0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        R ePe = R(0);
+        if (ex) ePe += P[0];
+        if (ey) ePe += P[1];
+        if (ez) ePe += P[2];
+        if (ex && ey) ePe = (ex * ey > 0) ? fma(R(2), P[3], ePe) : fma(R(-2), P[3], ePe);
+        if (ex && ez) ePe = (ex * ez > 0) ? fma(R(2), P[4], ePe) : fma(R(-2), P[4], ePe);
+        if (ey && ez) ePe = (ey * ez > 0) ? fma(R(2), P[5], ePe) : fma(R(-2), P[5], ePe);
+        const R wi = (R)L::w(i);
+        d[i] = fma(R(4.5) * wi, ePe - tr3, fma(R(-1.5) * wi, edot<L, R>(i, F0, F1, F2), qe[i]));
+    }
 }
 
 // ---------------------------------------------------------------------------

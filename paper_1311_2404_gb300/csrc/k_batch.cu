@@ -90,32 +90,48 @@ __device__ bool grid_barrier(const BatchParams& bp, bool skip_arrive)
     return ok != 0;
 }
 
-// Loads of one node's incoming populations (pull, periodic, half-way
-// bounce-back at solid upstream nodes).  Returns false for a solid node.
+// Pull loads of one node's incoming populations (periodic wrap).  They do
+// not wait for the node's flag byte, which is loaded beside them and
+// returned: a solid node's populations are read and dropped, and the
+// half-way bounce-back substitution (batch_bounce) follows only where the
+// flag says a neighbour is solid.
 template <class S>
-__device__ __forceinline__ bool batch_load(const DomDev& D, const typename S::T* __restrict__ A,
-                                           const uint8_t* __restrict__ flags, int x, int y,
-                                           float (&d)[9], unsigned& fl)
+__device__ __forceinline__ unsigned batch_load(const DomDev& D, const typename S::T* __restrict__ A,
+                                               const uint8_t* __restrict__ flags, int x, int y,
+                                               float (&d)[9])
 {
     using L = D2Q9;
-    const int n = y * D.nxp + x;
-    fl = flags[n];
-    if (fl & FLAG_SOLID) return false;
+    // element indices in 32 bits (a domain holds at most 9 x 2^20 values):
+    // one widening multiply-add per access instead of 64-bit plane products
+    const int sq = (int)D.sq;
     const int cx[3] = {x == 0 ? D.nx - 1 : x - 1, x, x == D.nx - 1 ? 0 : x + 1};
     const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
                        (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        d[i] = S::load(A + (size_t)i * D.sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)], L::w(i));
-    if (fl & FLAG_NEAR_WALL) {
+        d[i] = S::load(A + (i * sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)]), L::w(i));
+    return flags[ry[1] + x];
+}
+
+// Half-way bounce-back of a node next to a solid one: an incoming
+// population whose upstream node is solid is the node's own outgoing
+// population in the opposite direction from the previous step.
+template <class S>
+__device__ __forceinline__ void batch_bounce(const DomDev& D, const typename S::T* __restrict__ A,
+                                             const uint8_t* __restrict__ flags, int x, int y,
+                                             float (&d)[9])
+{
+    using L = D2Q9;
+    const int sq = (int)D.sq;
+    const int n = y * D.nxp + x;
+    const int cx[3] = {x == 0 ? D.nx - 1 : x - 1, x, x == D.nx - 1 ? 0 : x + 1};
+    const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
+                       (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-            if (flags[src] & FLAG_SOLID)
-                d[i] = S::load(A + (size_t)L::opp(i) * D.sq + n, L::w(L::opp(i)));
-        }
+    for (int i = 1; i < 9; ++i) {
+        const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+        if (flags[src] & FLAG_SOLID) d[i] = S::load(A + (L::opp(i) * sq + n), L::w(L::opp(i)));
     }
-    return true;
 }
 
 // Collision and store of one node (the single-domain kernel's arithmetic).
@@ -126,70 +142,92 @@ __device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams&
                                              float (&d)[9])
 {
     using L = D2Q9;
+    const int sq = (int)D.sq;
     float rho, v[3];
     bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
     if constexpr (S::kHalf) {
         if (!bp.round_nearest) {
             store_node_sr<L, S>(d, (unsigned)n * kSaltNode,
-                                [&](int i) { return B + (size_t)i * D.sq + n; });
+                                [&](int i) { return B + (i * sq + n); });
         } else {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
+            for (int i = 0; i < 9; ++i) S::store(B + (i * sq + n), d[i], L::w(i));
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) S::store(B + (size_t)i * D.sq + n, d[i], L::w(i));
+        for (int i = 0; i < 9; ++i) S::store(B + (i * sq + n), d[i], L::w(i));
     }
     if (out) {
         o[n] = rho;
-        o[D.sq + n] = v[0];
-        o[2 * D.sq + n] = v[1];
+        o[sq + n] = v[0];
+        o[2 * sq + n] = v[1];
         if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(bp.status, STATUS_NAN);
     }
 }
 
+// One persistent launch for n steps.  CTA g owns the contiguous tile range
+// [g T / G, (g+1) T / G) of the list ordered by (domain, y0, x0); it reads
+// only its first tile from the list and walks the rest arithmetically,
+// loading a domain's record when it enters that domain.  A thread handles
+// column x0 + threadIdx.x of a tile and rows threadIdx.y + k blockDim.y; NPT
+// of its rows are loaded together before any is updated.
 template <class S, int NPT>
-__global__ void k_batch(const BatchParams bp)
+__global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
 {
     using T = typename S::T;
     const int G = gridDim.x;
-    const long long t0 = (long long)bp.ntiles * blockIdx.x / G;
-    const long long t1 = (long long)bp.ntiles * (blockIdx.x + 1) / G;
+    const int t0 = (int)((long long)bp.ntiles * blockIdx.x / G);
+    const int t1 = (int)((long long)bp.ntiles * (blockIdx.x + 1) / G);
+    const int tw = blockDim.x, by = blockDim.y;
+    int4 first = make_int4(0, 0, 0, 0);
+    if (t0 < t1) first = bp.tiles[t0];
     int cur = bp.cur;
     for (int step = 0; step < bp.nsteps; ++step) {
         const bool out = (step == bp.nsteps - 1);
-        for (long long t = t0; t < t1; ++t) {
-            const int4 tile = bp.tiles[t];
-            const DomDev D = bp.dom[tile.x];
+        int dom = first.x, x0 = first.y, y0 = first.z;
+        DomDev D{};
+        if (t0 < t1) D = bp.dom[dom];
+        for (int t = t0; t < t1; ++t) {
             const T* __restrict__ A =
                 reinterpret_cast<const T*>(bp.base + (cur == 0 ? D.offA : D.offB));
             T* __restrict__ B = reinterpret_cast<T*>(bp.base + (cur == 0 ? D.offB : D.offA));
             const uint8_t* __restrict__ flags = reinterpret_cast<const uint8_t*>(bp.base + D.offF);
             float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
-            const int x = tile.y + threadIdx.x;
-            if (x >= D.nx) continue;
-            // NPT rows per pass (1 or 2): with 2, both nodes' loads are in
-            // flight together at the cost of twice the registers
-            for (int r = threadIdx.y; r < bp.th; r += NPT * blockDim.y) {
-                const int ya = tile.z + r;
-                const int rb = r + blockDim.y;
-                const int yb = tile.z + rb;
-                const bool va = ya < D.ny;
-                const bool vb = NPT == 2 && rb < bp.th && yb < D.ny;
-                float da[9], db[9];
-                unsigned fa = 0, fb = 0;
-                bool la = false, lb = false;
-                if (va) la = batch_load<S>(D, A, flags, x, ya, da, fa);
-                if (vb) lb = batch_load<S>(D, A, flags, x, yb, db, fb);
-                if (va) {
-                    const int n = ya * D.nxp + x;
-                    if (la) batch_update<S>(D, bp, B, o, n, out, da);
-                    else if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+            const int x = x0 + threadIdx.x;
+            const int yend = min(y0 + bp.th, D.ny);
+            if (x < D.nx) {
+                for (int ya = y0 + threadIdx.y; ya < yend; ya += NPT * by) {
+                    float d[NPT][9];
+                    unsigned fl[NPT];
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int y = ya + k * by;
+                        fl[k] = 0x80u;                       // no node (beyond the tile)
+                        if (k == 0 || y < yend) fl[k] = batch_load<S>(D, A, flags, x, y, d[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int y = ya + k * by;
+                        if (fl[k] & 0x80u) continue;
+                        const int n = y * D.nxp + x;
+                        if (fl[k] & FLAG_SOLID) {
+                            if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+                            continue;
+                        }
+                        if (fl[k] & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, x, y, d[k]);
+                        batch_update<S>(D, bp, B, o, n, out, d[k]);
+                    }
                 }
-                if (vb) {
-                    const int n = yb * D.nxp + x;
-                    if (lb) batch_update<S>(D, bp, B, o, n, out, db);
-                    else if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+            }
+            // the next tile in (domain, y0, x0) order
+            x0 += tw;
+            if (x0 >= D.nx) {
+                x0 = 0;
+                y0 += bp.th;
+                if (y0 >= D.ny) {
+                    y0 = 0;
+                    ++dom;
+                    if (t + 1 < t1) D = bp.dom[dom];
                 }
             }
         }
@@ -269,8 +307,10 @@ static void drop_graphs(lbm_batch b)
 static const void* kernel_for(int dtype, int npt)
 {
     if (dtype == LBM_F16S)
-        return npt == 2 ? batch_kernel_ptr<StoreF16S, 2>() : batch_kernel_ptr<StoreF16S, 1>();
-    return npt == 2 ? batch_kernel_ptr<StoreF32S, 2>() : batch_kernel_ptr<StoreF32S, 1>();
+        return npt == 4 ? batch_kernel_ptr<StoreF16S, 4>()
+             : npt == 2 ? batch_kernel_ptr<StoreF16S, 2>() : batch_kernel_ptr<StoreF16S, 1>();
+    return npt == 4 ? batch_kernel_ptr<StoreF32S, 4>()
+         : npt == 2 ? batch_kernel_ptr<StoreF32S, 2>() : batch_kernel_ptr<StoreF32S, 1>();
 }
 
 // Build and upload the tile list for tile shape (tw, th).
@@ -452,7 +492,7 @@ int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask)
         "copy mask");
     int* bad = reinterpret_cast<int*>(b->base + b->off_bar + 32);
     BCK(b, cudaMemsetAsync(bad, 0, sizeof(int), b->stream), "clear mask check");
-    BCK(b, launch_flags(0, stage, reinterpret_cast<uint8_t*>(b->base + D.offF), nullptr, D.nx,
+    BCK(b, launch_flags(0, stage, nullptr, reinterpret_cast<uint8_t*>(b->base + D.offF), D.nx,
                         D.ny, 1, D.nxp, 1, bad, b->stream),
         "node-type map kernel");
     b->launches += 1;
@@ -523,7 +563,7 @@ static int check_ready(lbm_batch b)
 
 static int step_impl(lbm_batch b, int n)
 {
-    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th * 4 + b->npt);
+    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th * 8 + b->npt);
     if (b->use_graph && b->stream != nullptr && !b->withhold) {
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
@@ -589,13 +629,13 @@ int lbm_batch_autotune(lbm_batch b)
     float best = 1e30f;
     int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th, bn = b->npt;
     const int steps = 4;
-    for (int npt : {1, 2})
+    for (int npt : {1, 2, 4})
         for (int threads : {128, 256, 512})
             for (int tw : {64, 128, 256}) {
                 if (tw > threads) continue;
                 const int mc = max_ctas(b, threads, npt);
                 if (mc < 1) continue;
-                for (int th : {2, 4, 8, 16}) {
+                for (int th : {2, 4, 8, 16, 32, 64}) {
                     if (th < npt * (threads / tw)) continue;
                     if (upload_tiles(b, tw, th)) continue;
                     const int per_sm = std::max(1, mc / b->sms);
@@ -645,6 +685,30 @@ int lbm_batch_get_config(lbm_batch b, int* out5)
     out5[2] = b->tw;
     out5[3] = b->th;
     out5[4] = b->npt;
+    return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch b, const int* in5)
+{
+    if (!b || !in5) return bfail(b, LBM_EINVAL, "NULL argument");
+    const int threads = in5[0], ctas = in5[1], tw = in5[2], th = in5[3], npt = in5[4];
+    if (tw < 32 || tw % 32 || threads < tw || threads > 512 || threads % tw)
+        return bfail(b, LBM_EINVAL, "threads %d / tile width %d: need 32 | tw, tw | threads <= 512",
+                     threads, tw);
+    if (npt != 1 && npt != 2 && npt != 4)
+        return bfail(b, LBM_EINVAL, "rows per thread and pass must be 1, 2 or 4");
+    if (th < 1 || th > 4096) return bfail(b, LBM_EINVAL, "tile rows %d out of range", th);
+    const int mc = max_ctas(b, threads, npt);
+    if (ctas < 1 || ctas > mc)
+        return bfail(b, LBM_EINVAL, "%d CTAs: between 1 and %d can be co-resident", ctas, mc);
+    int r = upload_tiles(b, tw, th);
+    if (r) return r;
+    b->threads = threads;
+    b->tw = tw;
+    b->th = th;
+    b->npt = npt;
+    b->ctas = std::min(ctas, b->ntiles);
+    drop_graphs(b);
     return LBM_OK;
 }
 

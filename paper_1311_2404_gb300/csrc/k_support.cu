@@ -6,17 +6,17 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------
-// Node-type map (Sec. 3.4): from the caller's mask (0 fluid, 1 solid, 2 + k a
-// boundary node of condition k) to one byte per node: bit 0 solid, bit 1 a
-// fluid node with at least one solid upstream neighbour (the only nodes that
-// need the bounce-back check), bits 2..5 condition id + 1; and for every node
-// a link mask, bit i set when the upstream node x - e_i is solid (links may be
-// NULL).  A mask value above max_code sets *bad.  dense: [nz][ny][nx];
-// flags and links: padded rows.
+// Node-type map (Sec. 3.4), from the caller's mask (0 fluid, 1 solid, 2 + k a
+// boundary node of condition k).  Handles get one 32-bit word per node:
+// link mask (bit i set when the upstream node x - e_i is solid), NODE_SOLID,
+// condition id + 1 in the top bits.  The batched ensemble gets bytes: bit 0
+// solid, bit 1 a fluid node with a solid upstream neighbour.  Exactly one of
+// words / flags is non-null.  A mask value above max_code sets *bad.
+// dense: [nz][ny][nx]; words and flags: padded rows.
 // ---------------------------------------------------------------------------
 template <class L>
-__global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__ flags,
-                        uint32_t* __restrict__ links, int nx, int ny, int nz, int nxp,
+__global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict__ words,
+                        uint8_t* __restrict__ flags, int nx, int ny, int nz, int nxp,
                         int max_code, int* __restrict__ bad)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,9 +24,15 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__
     const int z = blockIdx.z;
     if (x >= nxp) return;
     const size_t out = ((size_t)z * ny + y) * nxp + x;
-    if (x >= nx) {
-        flags[out] = FLAG_SOLID;  // padding never updates
-        if (links) links[out] = 0;
+    auto put = [&](bool solid, uint32_t lk, int code) {
+        if (words)
+            words[out] = (solid ? NODE_SOLID : 0u) | lk |
+                         (code >= 2 ? (uint32_t)(code - 1) << NODE_BC_SHIFT : 0u);
+        else
+            flags[out] = (solid ? FLAG_SOLID : 0) | (lk ? FLAG_NEAR_WALL : 0);
+    };
+    if (x >= nx) {        // padding never updates
+        put(true, 0u, 0);
         return;
     }
     auto at = [&](int xx, int yy, int zz) {
@@ -38,8 +44,7 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__
     const int code = at(x, y, z);
     if (code > max_code) {
         atomicOr(bad, 1);
-        flags[out] = FLAG_SOLID;
-        if (links) links[out] = 0;
+        put(true, 0u, 0);
         return;
     }
     const bool solid = code == 1;
@@ -47,21 +52,18 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint8_t* __restrict__
     if (!solid)
         for (int i = 1; i < L::Q; ++i)
             if (at(x - L::ex(i), y - L::ey(i), z - L::ez(i)) == 1) lk |= 1u << i;
-    const bool near = lk != 0;
-    if (links) links[out] = lk;
-    flags[out] = (solid ? FLAG_SOLID : 0) | (near ? FLAG_NEAR_WALL : 0) |
-                 (code >= 2 ? ((code - 1) << FLAG_BC_SHIFT) : 0);
+    put(solid, lk, code);
 }
 
-cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, uint32_t* links,
+cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
                          int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s)
 {
     dim3 block(128), grid((nxp + 127) / 128, ny, nz);
     switch (lattice) {
-    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
-    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
-    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
-    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, flags, links, nx, ny, nz, nxp, max_code, bad); break;
+    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
+    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
+    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
+    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -210,7 +212,7 @@ cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, in
 template <class RT>
 __global__ void __launch_bounds__(256) k_reduce_partial(const RT* __restrict__ rho,
                                                         const RT* __restrict__ u,
-                                                        const uint8_t* __restrict__ flags, int D,
+                                                        const uint32_t* __restrict__ nodes, int D,
                                                         int nx, int ny, int nz, int nxp,
                                                         long long sq, double* __restrict__ part)
 {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256) k_reduce_partial(const RT* __restrict__ r
         const long long base = r * nxp;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const long long n = base + x;
-            if (flags && (flags[n] & FLAG_SOLID)) continue;
+            if (nodes && (nodes[n] & NODE_SOLID)) continue;
             const double rr = (double)rho[n];
             double ke = 0;
             acc[0] += rr;
@@ -260,16 +262,16 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__
     if (threadIdx.x < 5) out[threadIdx.x] = sh[0][threadIdx.x];
 }
 
-cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint8_t* flags, int D,
+cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint32_t* nodes, int D,
                           int nx, int ny, int nz, int nxp, long long sq, double* partials,
                           double* out, cudaStream_t s)
 {
     if (f64)
         k_reduce_partial<double><<<kReduceBlocks, 256, 0, s>>>(
-            (const double*)rho, (const double*)u, flags, D, nx, ny, nz, nxp, sq, partials);
+            (const double*)rho, (const double*)u, nodes, D, nx, ny, nz, nxp, sq, partials);
     else
         k_reduce_partial<float><<<kReduceBlocks, 256, 0, s>>>(
-            (const float*)rho, (const float*)u, flags, D, nx, ny, nz, nxp, sq, partials);
+            (const float*)rho, (const float*)u, nodes, D, nx, ny, nz, nxp, sq, partials);
     k_reduce_final<<<1, 256, 0, s>>>(partials, kReduceBlocks, out);
     return cudaGetLastError();
 }

@@ -40,9 +40,8 @@ struct lbm_ctx {
     char* base = nullptr;
     size_t bytes = 0;
     bool owned = false;
-    size_t off_A = 0, off_B = 0, off_flags = 0, off_rho = 0, off_u = 0, off_alpha = 0,
-           off_misc = 0, off_part = 0, off_mlp = 0, off_stage = 0, stage_bytes = 0,
-           off_links = 0;
+    size_t off_A = 0, off_B = 0, off_nodes = 0, off_rho = 0, off_u = 0, off_alpha = 0,
+           off_misc = 0, off_part = 0, off_mlp = 0, off_stage = 0, stage_bytes = 0;
     int cur = 0;            // 0: state in A, 1: state in B
     bool has_mask = false, inited = false, have_out = false;
     cudaStream_t stream = nullptr;
@@ -151,8 +150,7 @@ static void layout(lbm_ctx* h)
     h->off_A = o; o = align256(o + dist);
     h->off_B = o;
     if (!h->aa) o = align256(o + dist);   // AA: a single array
-    h->off_flags = o; o = align256(o + (size_t)h->sq);
-    h->off_links = o; o = align256(o + (size_t)h->sq * 4);
+    h->off_nodes = o; o = align256(o + (size_t)h->sq * 4);
     h->off_rho = o; o = align256(o + (size_t)h->sq * h->rsize);
     h->off_u = o; o = align256(o + (size_t)h->D * h->sq * h->rsize);
     h->off_alpha = o;
@@ -181,7 +179,7 @@ static int ensure_memory(lbm_ctx* h)
     h->base = static_cast<char*>(p);
     h->owned = true;
     CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
-    CK(h, cudaMemsetAsync(h->base + h->off_flags, 0, (size_t)h->sq, h->stream), "clear flags");
+    CK(h, cudaMemsetAsync(h->base + h->off_nodes, 0, (size_t)h->sq * 4, h->stream), "clear node words");
     return LBM_OK;
 }
 
@@ -287,7 +285,7 @@ int lbm_bind_memory(lbm_handle h, void* dev_ptr, size_t bytes)
     h->base = static_cast<char*>(dev_ptr);
     h->owned = false;
     CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
-    CK(h, cudaMemsetAsync(h->base + h->off_flags, 0, (size_t)h->sq, h->stream), "clear flags");
+    CK(h, cudaMemsetAsync(h->base + h->off_nodes, 0, (size_t)h->sq * 4, h->stream), "clear node words");
     return LBM_OK;
 }
 
@@ -313,8 +311,8 @@ int lbm_set_geometry(lbm_handle h, const uint8_t* mask)
        "copy mask");
     int* bad = at<int>(h, h->off_misc + MISC_BAD);
     CK(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream), "clear mask check");
-    CK(h, launch_flags(h->lattice, stage, at<uint8_t>(h, h->off_flags), at<uint32_t>(h, h->off_links),
-                       h->nx, h->ny, h->nz, h->nxp, 1 + kMaxBC, bad, h->stream),
+    CK(h, launch_flags(h->lattice, stage, at<uint32_t>(h, h->off_nodes), nullptr, h->nx, h->ny,
+                       h->nz, h->nxp, 1 + kMaxBC, bad, h->stream),
        "node-type map kernel");
     h->launches += 1;
     int hbad = 0;
@@ -523,8 +521,7 @@ static StepParams make_params(lbm_ctx* h)
 {
     StepParams p;
     std::memset(&p, 0, sizeof p);
-    p.flags = h->has_mask ? at<uint8_t>(h, h->off_flags) : nullptr;
-    p.links = h->has_mask ? at<uint32_t>(h, h->off_links) : nullptr;
+    p.nodes = h->has_mask ? at<uint32_t>(h, h->off_nodes) : nullptr;
     p.rho = h->base + h->off_rho;
     p.u = h->base + h->off_u;
     p.alpha_out = (h->model == LBM_ELBM && h->alpha_out) ? at<double>(h, h->off_alpha) : nullptr;
@@ -717,7 +714,7 @@ int lbm_reduce(lbm_handle h, double* out)
     if (!h->have_out) return fail(h, LBM_ESTATE, "no step has produced output yet");
     double* dres = at<double>(h, h->off_misc + MISC_RED);
     CK(h, launch_reduce(h->rsize == 8, h->base + h->off_rho, h->base + h->off_u,
-                        h->has_mask ? at<uint8_t>(h, h->off_flags) : nullptr, h->D, h->nx, h->ny,
+                        h->has_mask ? at<uint32_t>(h, h->off_nodes) : nullptr, h->D, h->nx, h->ny,
                         h->nz, h->nxp, h->sq, at<double>(h, h->off_part), dres, h->stream),
        "reduce kernels");
     h->launches += 2;

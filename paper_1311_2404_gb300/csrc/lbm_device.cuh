@@ -269,9 +269,14 @@ __device__ __forceinline__ void store_node_sr(const float (&d)[L::Q], unsigned s
 // Kernel parameters (passed by value).
 // ---------------------------------------------------------------------------
 enum { MODEL_BGK = 0, MODEL_MRT = 1, MODEL_ELBM = 2, MODEL_REG = 3, MODEL_SMAG = 4 };
-// node-type byte: bit 0 solid, bit 1 fluid with a solid upstream neighbour,
-// bits 2..5 boundary condition id + 1 (0: none)
-enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2, FLAG_BC_SHIFT = 2, FLAG_BC_MASK = 0x3c };
+// node-type byte of the batched ensemble: bit 0 solid, bit 1 fluid with a
+// solid upstream neighbour
+enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2 };
+// node word of a single-domain handle (one 32-bit load per node, issued with
+// the population loads): bits 1..26 link mask (bit i: the upstream node
+// x - e_i is solid), bit 27 solid, bits 28..31 boundary condition id + 1
+constexpr uint32_t NODE_LINKS = 0x07fffffeu, NODE_SOLID = 1u << 27;
+constexpr int NODE_BC_SHIFT = 28;
 constexpr int kMaxBC = 15;
 // ELBM counter replicas: slots 0..5 evals, skipped, clamped, at cap, guarded,
 // updated; 6 sum of |g(alpha)|/a2 (double bits), 7 its max (double bits),
@@ -295,8 +300,7 @@ enum { MLP_NPARAM = 1394 };
 struct StepParams {
     const void* A;             // post-collision distributions at t (read)
     void* B;                   // post-collision distributions at t+1 (written)
-    const uint8_t* flags;
-    const uint32_t* links;     // near-wall nodes: bit i set when node x - e_i is solid
+    const uint32_t* nodes;     // node words, or nullptr without a geometry
     // plane i of A and B (A + i sq, B + i sq): the kernels address each
     // direction's plane through these, so a load is one 32-bit offset from a
     // parameter-bank pointer instead of a 64-bit plane product per access

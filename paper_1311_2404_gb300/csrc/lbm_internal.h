@@ -41,14 +41,14 @@ cudaError_t launch_step_elbm_part(int store, const StepParams& p, bool mask, boo
 // storage groups of the ELBM objects: {F64}, {F32, F32S}, {F16S, BF16S}
 constexpr unsigned kElbmStoreGroup[5] = {1u, 6u, 6u, 24u, 24u};
 
-cudaError_t launch_flags(int lattice, const uint8_t* dense, uint8_t* flags, uint32_t* links,
+cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
                          int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s);
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s);
 cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, int nfields, int nx,
                         int ny, int nz, int nxp, long long sq, cudaStream_t s);
-cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint8_t* flags, int D,
+cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint32_t* nodes, int D,
                           int nx, int ny, int nz, int nxp, long long sq, double* partials,
                           double* out, cudaStream_t s);
 cudaError_t launch_sum_ctr(const unsigned long long* rep, double* out, cudaStream_t s);

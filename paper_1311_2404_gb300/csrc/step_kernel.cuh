@@ -30,8 +30,7 @@ namespace lbm {
 constexpr int kStepThreads = 128;
 
 template <class L, class S, int MODEL, bool MASK, bool AA>
-__global__ void __launch_bounds__(kStepThreads)
-    k_stream_collide(const StepParams p)
+__device__ __forceinline__ void stream_collide_body(const StepParams& p)
 {
     using R = typename S::R;
     using T = typename S::T;
@@ -57,8 +56,8 @@ __global__ void __launch_bounds__(kStepThreads)
     // loads do not wait for the flag (a solid node's populations are read and
     // dropped), so a masked domain keeps the unmasked kernel's memory-level
     // parallelism.
-    unsigned fl = 0;
-    if (MASK && active) fl = __ldg(p.flags + n);
+    uint32_t fl = 0;
+    if (MASK && active) fl = __ldg(p.nodes + n);
     auto Ai = [&](int i) { return static_cast<const T*>(p.Ap[i]); };
     auto Bi = [&](int i) { return static_cast<T*>(p.Bp[i]); };
     // neighbour coordinates (periodic)
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(kStepThreads)
                 d[i] = S::load(Ai(i) + n, L::w(i));
         }
     }
-    if (active && (fl & FLAG_SOLID)) {
+    if (active && (fl & NODE_SOLID)) {
         if (p.out) {
             static_cast<R*>(p.rho)[n] = R(0);
 #pragma unroll
@@ -94,12 +93,11 @@ __global__ void __launch_bounds__(kStepThreads)
     int evals = 0, astat = -1;
     double resid = 0.0;
     if (active) {
-        if (MASK && (fl & FLAG_NEAR_WALL)) {
-            const uint32_t lk = __ldg(p.links + n);
+        if (MASK && (fl & NODE_LINKS)) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-                if ((lk >> i) & 1u) {
+                if ((fl >> i) & 1u) {
                     if (!AA)
                         d[i] = S::load(Ai(L::opp(i)) + n, L::w(i));
                     else if (pushpull)
@@ -109,8 +107,8 @@ __global__ void __launch_bounds__(kStepThreads)
                 }
             }
         }
-        if (MASK && (fl & FLAG_BC_MASK))
-            bc_apply<L, R>(d, p.bc[((fl & FLAG_BC_MASK) >> FLAG_BC_SHIFT) - 1],
+        if (MASK && (fl >> NODE_BC_SHIFT))
+            bc_apply<L, R>(d, p.bc[(fl >> NODE_BC_SHIFT) - 1],
                            sel<R>(p.F_f[0], p.F[0]), sel<R>(p.F_f[1], p.F[1]),
                            sel<R>(p.F_f[2], p.F[2]));
         R rho, v[3];
@@ -223,6 +221,24 @@ __global__ void __launch_bounds__(kStepThreads)
     }
 }
 
+template <class L, class S, int MODEL, bool MASK, bool AA>
+__global__ void __launch_bounds__(kStepThreads) k_stream_collide(const StepParams p)
+{
+    stream_collide_body<L, S, MODEL, MASK, AA>(p);
+}
+
+// The same update with a register budget that keeps MINB CTAs resident per
+// SM, for FP32-arithmetic AB instances whose register count would otherwise
+// cost warps in flight: the regularized and Smagorinsky operators on unmasked
+// domains (10 CTAs, 48 registers; left alone Smagorinsky takes 56 and the
+// Kida vortex ran 10% below the LBGK rate) and the masked LBGK / regularized /
+// Smagorinsky kernels (9 CTAs, 56 registers instead of 64).
+template <class L, class S, int MODEL, bool MASK, bool AA, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB) k_stream_collide_occ(const StepParams p)
+{
+    stream_collide_body<L, S, MODEL, MASK, AA>(p);
+}
+
 // ---------------------------------------------------------------------------
 // Half-width storage, AB pattern: two x-adjacent nodes (x0 even, x0 + 1) per
 // thread.  The directions without an x component are read as one 32-bit pair,
@@ -248,11 +264,11 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
     const int plane = p.ny * p.nxp;
     const int n0 = z * plane + y * p.nxp + x0;
     bool act[2] = {true, x1 < nx};
-    unsigned fl[2] = {0u, 0u};
-    if (MASK) {   // the two flag bytes in one load (padding flags are solid)
-        const unsigned f2 = __ldg(reinterpret_cast<const unsigned short*>(p.flags + n0));
-        fl[0] = f2 & 0xffu;
-        fl[1] = f2 >> 8;
+    uint32_t fl[2] = {0u, 0u};
+    if (MASK) {   // the two node words in one load (padding words are solid)
+        const uint2 f2 = __ldg(reinterpret_cast<const uint2*>(p.nodes + n0));
+        fl[0] = f2.x;
+        fl[1] = f2.y;
     }
     auto Ai = [&](int i) { return static_cast<const T*>(p.Ap[i]); };
     auto Bi = [&](int i) { return static_cast<T*>(p.Bp[i]); };
@@ -281,16 +297,15 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int n = n0 + k;
-        if (MASK && (fl[k] & FLAG_SOLID)) act[k] = false;
+        if (MASK && (fl[k] & NODE_SOLID)) act[k] = false;
         if (!act[k]) continue;
-        if (MASK && (fl[k] & FLAG_NEAR_WALL)) {
-            const uint32_t lk = __ldg(p.links + n);
+        if (MASK && (fl[k] & NODE_LINKS)) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i)
-                if ((lk >> i) & 1u) d[k][i] = S::load(Ai(L::opp(i)) + n, L::w(i));
+                if ((fl[k] >> i) & 1u) d[k][i] = S::load(Ai(L::opp(i)) + n, L::w(i));
         }
-        if (MASK && (fl[k] & FLAG_BC_MASK))
-            bc_apply<L, R>(d[k], p.bc[((fl[k] & FLAG_BC_MASK) >> FLAG_BC_SHIFT) - 1],
+        if (MASK && (fl[k] >> NODE_BC_SHIFT))
+            bc_apply<L, R>(d[k], p.bc[(fl[k] >> NODE_BC_SHIFT) - 1],
                            p.F_f[0], p.F_f[1], p.F_f[2]);
         if (MODEL == MODEL_BGK) {
             bgk_collide<L, R>(d[k], p.omega_f, p.F_f[0], p.F_f[1], p.F_f[2], p.has_force != 0,
@@ -394,10 +409,18 @@ cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t 
         else
             k_stream_collide<L, S, MODEL, false, true><<<grid, block, 0, s>>>(p);
     } else {
-        if (mask)
-            k_stream_collide<L, S, MODEL, true, false><<<grid, block, 0, s>>>(p);
-        else
+        constexpr bool f32 = sizeof(typename S::R) == 4;
+        constexpr bool les = MODEL == MODEL_REG || MODEL == MODEL_SMAG;
+        if (mask) {
+            if constexpr (f32 && (les || MODEL == MODEL_BGK))
+                k_stream_collide_occ<L, S, MODEL, true, false, 9><<<grid, block, 0, s>>>(p);
+            else
+                k_stream_collide<L, S, MODEL, true, false><<<grid, block, 0, s>>>(p);
+        } else if constexpr (f32 && les) {
+            k_stream_collide_occ<L, S, MODEL, false, false, 10><<<grid, block, 0, s>>>(p);
+        } else {
             k_stream_collide<L, S, MODEL, false, false><<<grid, block, 0, s>>>(p);
+        }
     }
     return cudaGetLastError();
 }

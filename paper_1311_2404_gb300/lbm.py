@@ -120,6 +120,7 @@ _PROTOS = {
     "lbm_batch_init_equilibrium": (_i, [_vp, _i, _vp, _vp, _i]),
     "lbm_batch_autotune": (_i, [_vp]),
     "lbm_batch_get_config": (_i, [_vp, _vp]),
+    "lbm_batch_set_config": (_i, [_vp, _vp]),
     "lbm_batch_step": (_i, [_vp, _i]),
     "lbm_batch_get_macro": (_i, [_vp, _i, _vp, _vp, _i]),
     "lbm_batch_sync": (_i, [_vp]),
@@ -439,6 +440,12 @@ def lbm_batch_get_config(b):
     out = np.zeros(5, dtype=np.int32)
     _check(_L.lbm_batch_get_config(b, _ptr(out)), b, batch=True)
     return out
+
+
+def lbm_batch_set_config(b, cfg):
+    """cfg: (threads, ctas, tile width, tile rows, rows per thread and pass)."""
+    arr = np.ascontiguousarray(np.asarray(cfg, dtype=np.int32).reshape(5))
+    _check(_L.lbm_batch_set_config(b, _ptr(arr)), b, batch=True)
 
 
 def lbm_batch_step(b, n=1):

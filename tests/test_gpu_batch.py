@@ -178,3 +178,50 @@ def test_batch_reinit_one_domain_mid_run(t_reinit):
         rho, u = _init_state(specs[d], 100 + d)
         r, v = _single(specs[d], rho, u, t_reinit + 4, lbm.LBM_F32S)
         assert np.array_equal(got[d][0], r) and np.array_equal(got[d][1], v)
+
+
+CONFIGS = [
+    # threads, ctas, tile width, tile rows, rows per thread and pass
+    (256, 7, 128, 8, 1),
+    (64, 1, 32, 3, 1),        # one CTA walks every tile of every domain
+    (128, 3, 64, 5, 2),       # tile rows not a multiple of the rows per pass
+    (512, 2, 128, 64, 4),
+    (96, 5, 32, 1, 4),        # one-row tiles: only the first row of a pass exists
+    (256, 11, 256, 16, 2),
+]
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F32S, lbm.LBM_F16S])
+def test_every_launch_configuration_gives_the_same_bits(dtype):
+    """The persistent kernel walks its tile range arithmetically across
+    domain boundaries; every tile shape, CTA count and rows-per-pass
+    choice must reproduce the same fields bit for bit."""
+    specs = _specs(7, seed=21)
+    ref = None
+    for cfg in CONFIGS:
+        b = _make_batch(specs, dtype)
+        lbm.lbm_batch_set_config(b, cfg)
+        assert list(lbm.lbm_batch_get_config(b)) == list(cfg)
+        lbm.lbm_batch_step(b, 5)
+        lbm.lbm_batch_step(b, 4)
+        got = _batch_fields(b, specs)
+        lbm.lbm_batch_destroy(b)
+        if ref is None:
+            ref = got
+            continue
+        for (r1, u1), (r2, u2) in zip(ref, got):
+            assert np.array_equal(r1, r2) and np.array_equal(u1, u2), cfg
+
+
+def test_set_config_rejects_bad_values():
+    specs = _specs(3, seed=22)
+    b = _make_batch(specs, lbm.LBM_F32S)
+    before = list(lbm.lbm_batch_get_config(b))
+    for bad in [(256, 4, 48, 8, 1), (256, 4, 128, 8, 3), (1024, 4, 128, 8, 1),
+                (256, 0, 128, 8, 1), (256, 10 ** 6, 128, 8, 1), (192, 4, 128, 8, 1),
+                (256, 4, 128, 0, 1)]:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_batch_set_config(b, bad)
+        assert ei.value.code == lbm.LBM_EINVAL
+        assert list(lbm.lbm_batch_get_config(b)) == before
+    lbm.lbm_batch_destroy(b)
