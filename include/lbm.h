@@ -333,18 +333,23 @@ LBM_API int lbm_batch_set_force(lbm_batch b, int d, double fx, double fy);
  * the batch's time are unchanged). */
 LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* u,
                                int field_dtype);
-/* Choose block size, tile shape, rows per thread and CTAs per SM by timing a
- * few steps of each candidate (CUDA events); restores the state afterwards. */
+/* Choose the kernel variant, block size, tile shape, rows per thread and
+ * CTAs per SM by timing a few steps of each candidate (CUDA events); restores
+ * the state afterwards. */
 LBM_API int lbm_batch_autotune(lbm_batch b);
 /* Current launch configuration (5 ints): threads per CTA, CTAs, tile width,
- * tile rows, rows per thread and pass (1, 2 or 4). */
+ * tile rows, and the kernel variant: 1, 2 or 4 = the register kernel with
+ * that many rows per thread and pass; 0 = the staged kernel, which copies
+ * each tile's inputs into shared memory with bulk asynchronous copies,
+ * double-buffered, while the previous tile is updated. */
 LBM_API int lbm_batch_get_config(lbm_batch b, int* out5);
 /* Set the launch configuration (5 ints, as lbm_batch_get_config returns
  * them), e.g. one found by an earlier lbm_batch_autotune.  Threads per CTA
  * at most 512 and a multiple of the tile width, itself a multiple of 32;
- * rows per thread and pass 1, 2 or 4; CTAs between 1 and the number that can
- * be co-resident (the launch is cooperative).  LBM_EINVAL otherwise, with
- * the configuration unchanged. */
+ * variant 0, 1, 2 or 4 (the staged kernel's two stages within 200 KB of
+ * shared memory); CTAs between 1 and the number that can be co-resident (the
+ * launch is cooperative).  LBM_EINVAL otherwise, with the configuration
+ * unchanged. */
 LBM_API int lbm_batch_set_config(lbm_batch b, const int* in5);
 /* Advance every domain n steps in one persistent launch.  The per-step
  * grid barrier spins a bounded number of times; if it gives up, the kernel
@@ -357,9 +362,13 @@ LBM_API int lbm_batch_set_rounding(lbm_batch b, int mode);
  * about two seconds).  A wait that exceeds it ends the launch early and the
  * next synchronising call returns LBM_ETIMEOUT. */
 LBM_API int lbm_batch_set_wait_limit(lbm_batch b, long long spins);
-/* Fault-injection hook for testing the timeout path: when on, CTA 0 leaves
+/* Fault-injection hook for testing the timeout paths.  on = 1: CTA 0 leaves
  * the first grid barrier of the next launch without arriving, so every other
- * CTA's bounded wait runs out.  The state after such a launch is incomplete. */
+ * CTA's bounded wait runs out.  on = 2 (staged kernel): the first stage of
+ * the next launch expects 16 bytes more than its copies deliver, so the wait
+ * for it runs out.  Either way the next synchronising call returns
+ * LBM_ETIMEOUT and the state after that launch is incomplete.  0 turns the
+ * hook off. */
 LBM_API int lbm_batch_inject_missing_arrival(lbm_batch b, int on);
 LBM_API int lbm_batch_sync(lbm_batch b);
 LBM_API long long lbm_batch_launch_count(lbm_batch b);

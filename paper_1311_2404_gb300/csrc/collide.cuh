@@ -681,6 +681,7 @@ struct LogEval {
 // for a <= 0.1 / max|x|, where the terms beyond K = 14 are below 1e-17 of
 // a_2 (the scale of g'); an iterate outside that range falls back to LogEval.
 constexpr int kSeriesK = 14;
+constexpr int kSeriesK64 = 9;    // moments above this order are accumulated in FP32
 constexpr double kSeriesMaxX = 0.03;
 struct SeriesEval {
     double c[kSeriesK + 1];      // c_k, k = 2..K
@@ -932,9 +933,17 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         bool solved = false;
         if (entropic && maxabs <= kSeriesMaxX) {
             // moments a_k and A from the series (no per-direction logarithm)
+            // a_2..a_9 in FP64; a_10..a_14 in FP32.  With |a_k| <= max|x|^(k-2) a_2
+            // and a max|x| <= 0.1 over the series' range, term k of g is at most
+            // 2 (a max|x|)^(k-2) / (k (k-1)) of a^2 a_2 / 2: from k = 10 on below
+            // 2.3e-10, so FP32's relative error (< 2e-6 after 14 products and 19
+            // sums) moves g by less than 5e-16 of its scale.
             double a[kSeriesK + 1];
+            float ahi[kSeriesK - kSeriesK64];
 #pragma unroll
             for (int k = 0; k <= kSeriesK; ++k) a[k] = 0;
+#pragma unroll
+            for (int k = 0; k < kSeriesK - kSeriesK64; ++k) ahi[k] = 0.f;
             double s0 = 0, s1[3] = {0, 0, 0}, sy = 0;
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
@@ -942,9 +951,16 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                 double pw = Dl;
                 a[1] += pw;
 #pragma unroll
-                for (int k = 2; k <= kSeriesK; ++k) {
+                for (int k = 2; k <= kSeriesK64; ++k) {
                     pw *= x[i];
                     a[k] += pw;
+                }
+                const float xf = (float)x[i];
+                float pwf = (float)pw;
+#pragma unroll
+                for (int k = 0; k < kSeriesK - kSeriesK64; ++k) {
+                    pwf *= xf;
+                    ahi[k] += pwf;
                 }
                 s0 += Dl;
                 s1[0] += L::ex(i) * Dl;
@@ -953,17 +969,20 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                 const double yi = y[i];
                 sy = fma(Dl, yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
             }
+#pragma unroll
+            for (int k = 0; k < kSeriesK - kSeriesK64; ++k) a[kSeriesK64 + 1 + k] = (double)ahi[k];
             // A = sum Delta ln(f_eq/w) - sum Delta log1p(x), with
             // sum Delta ln(f_eq/w) = ln c0 s0 + sum_a ln r_a s1_a + sum Delta log1p(y)
             // and sum Delta log1p(x) = sum_{n>=1} (-1)^(n+1) a_(n+1) / n
             double sl = 0;
 #pragma unroll
-            for (int n = kSeriesK - 1; n >= 1; --n) sl += ((n & 1) ? 1.0 : -1.0) * a[n + 1] / n;
+            for (int n = kSeriesK - 1; n >= 1; --n)
+                sl = fma(a[n + 1], ((n & 1) ? 1.0 : -1.0) * (1.0 / n), sl);
             A = fma(lc0, s0, fma(lr[0], s1[0], fma(lr[1], s1[1], fma(lr[2], s1[2], sy - sl))));
             SeriesEval ev;
 #pragma unroll
             for (int k = 2; k <= kSeriesK; ++k)
-                ev.c[k] = ((k & 1) ? -1.0 : 1.0) * a[k] / (double)(k * (k - 1));
+                ev.c[k] = a[k] * (((k & 1) ? -1.0 : 1.0) * (1.0 / (double)(k * (k - 1))));
             ev.c[0] = ev.c[1] = 0;
             ev.A1 = A + a[1];
             ev.amax = 0.1 / maxabs;

@@ -46,10 +46,13 @@ struct BatchParams {
     int nsteps;
     int cur;                            // 0: state in A regions
     int th;                             // tile rows
+    int tw;                             // tile width (the staged kernel's tiles)
     unsigned* bar;                      // [0] arrivals, [1] generation
     unsigned* status;
     long long wait_limit;               // spins before giving up
-    int withhold;                       // test hook: CTA 0 skips its first arrival
+    int withhold;                       // test hooks: 1 CTA 0 skips its first grid-barrier
+                                        // arrival; 2 (staged kernel) the first stage of
+                                        // the launch expects 16 bytes that never arrive
     int round_nearest;                  // FP16 storage: 1 round to nearest, 0 dither
 };
 
@@ -90,6 +93,15 @@ __device__ bool grid_barrier(const BatchParams& bp, bool skip_arrive)
     return ok != 0;
 }
 
+// A population written during this launch (by any CTA, in an earlier step):
+// a coherent load, not the read-only (non-coherent) path.
+template <class S>
+__device__ __forceinline__ float bload(const typename S::T* p)
+{
+    if constexpr (S::kHalf) return __half2float(*p);
+    else return *p;
+}
+
 // Pull loads of one node's incoming populations (periodic wrap).  They do
 // not wait for the node's flag byte, which is loaded beside them and
 // returned: a solid node's populations are read and dropped, and the
@@ -109,7 +121,7 @@ __device__ __forceinline__ unsigned batch_load(const DomDev& D, const typename S
                        (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        d[i] = S::load(A + (i * sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)]), L::w(i));
+        d[i] = bload<S>(A + (i * sq + ry[1 - L::ey(i)] + cx[1 - L::ex(i)]));
     return flags[ry[1] + x];
 }
 
@@ -130,7 +142,7 @@ __device__ __forceinline__ void batch_bounce(const DomDev& D, const typename S::
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int src = ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-        if (flags[src] & FLAG_SOLID) d[i] = S::load(A + (L::opp(i) * sq + n), L::w(L::opp(i)));
+        if (flags[src] & FLAG_SOLID) d[i] = bload<S>(A + (L::opp(i) * sq + n));
     }
 }
 
@@ -233,11 +245,384 @@ __global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
         }
         cur ^= 1;
         if (step + 1 < bp.nsteps) {
-            const bool skip = bp.withhold && blockIdx.x == 0 && step == 0;
+            const bool skip = bp.withhold == 1 && blockIdx.x == 0 && step == 0;
             if (!grid_barrier(bp, skip)) return;
         }
     }
 }
+
+// ---- staged variant: bulk copies into shared memory ------------------------
+//
+// The register kernel's bytes in flight are bounded by its registers (one
+// node's 9 loads per thread).  Here a producer warp copies tiles' inputs into
+// a ring of kStages shared-memory stages with cp.async.bulk, up to kStages
+// tiles ahead, while the consumer warps update nodes from the filled stages:
+// the bytes in flight are several tiles per CTA, and no CTA-wide barrier is
+// taken inside a step (a "full" mbarrier per stage signals landed bytes, an
+// "empty" one the consumers' release).  Stage layout (bytes, esize = sizeof(T)):
+//   planes  [9][th][tw] x esize: row r of plane i holds global row
+//           y0 + r - e_iy (wrapped), columns [x0, x0 + tw)
+//   flags   [th][tw]: the tile's own node flags
+//   halo    [6][th] 32-bit words: for the planes with e_x = +1 the column
+//           left of the tile (x0 - 1, or nx - 1 at x0 = 0), for e_x = -1 the
+//           column right of it (x0 + tw, or 0 when the tile reaches nx); the
+//           aligned 4-byte word holding that element
+// Row copies start at element x0 + (plane, row) offsets, all multiples of 32
+// elements from a 256-byte aligned region: 16-byte aligned, and their length
+// min(tw, nxp - x0) elements is a multiple of 32.
+
+constexpr int kStages = 4;
+
+__host__ __device__ constexpr int tile_stage_bytes(int esize, int tw, int th)
+{
+    return (((9 * th * tw * esize + th * tw + 15) & ~15) + 6 * th * 4 + 127) & ~127;
+}
+__host__ __device__ constexpr int stage_halo_offset(int esize, int tw, int th)
+{
+    return (9 * th * tw * esize + th * tw + 15) & ~15;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// arrive (counts one) and raise the expected transaction bytes of the phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// global -> shared bulk copy completing on bar (bytes a multiple of 16, both
+// addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 4-byte asynchronous copy (src 4-byte aligned); its completion is signalled
+// by the issuing thread's later cp_arrive_noinc
+__device__ __forceinline__ void cp4_g2s(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_arrive_noinc(unsigned long long* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// order this thread's generic-proxy view of global memory with its later
+// (or, on the writing side, others' later) bulk-copy reads
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Bounded wait for a stage's phase: gives up after `cycles` SM clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long cycles)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+
+// D2Q9 planes with e_x = +1 (their pull reads the left halo) and e_x = -1
+// (right halo), in halo-slot order, as 4-bit fields of one constant; e_y + 1
+// of every plane as 2-bit fields (no run-time indexed local arrays)
+constexpr unsigned kHaloPlanes = 1u | 5u << 4 | 7u << 8 | 2u << 12 | 6u << 16 | 8u << 20;
+static_assert(D2Q9::ex(1) == 1 && D2Q9::ex(5) == 1 && D2Q9::ex(7) == 1 && D2Q9::ex(2) == -1 &&
+                  D2Q9::ex(6) == -1 && D2Q9::ex(8) == -1,
+              "halo planes");
+__host__ __device__ constexpr unsigned ey_code()
+{
+    unsigned c = 0;
+    for (int i = 0; i < 9; ++i) c |= (unsigned)(D2Q9::ey(i) + 1) << (2 * i);
+    return c;
+}
+__device__ __forceinline__ int halo_plane(int k) { return (int)((kHaloPlanes >> (4 * k)) & 15u); }
+__device__ __forceinline__ int d2q9_ey(int i) { return (int)((ey_code() >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int halo_slot(int i)
+{
+    return i == 1 ? 0 : i == 5 ? 1 : i == 7 ? 2 : i == 2 ? 3 : i == 6 ? 4 : 5;
+}
+
+// Warp-0 side: queue the copies of tile (D, x0, y0) into stage st (all 32
+// lanes call it).  The phase completes when the expected bytes have landed
+// and all 32 lanes' 4-byte copies are done (count 33 = 1 + 32).
+template <class S>
+__device__ __forceinline__ void stage_issue(const BatchParams& bp, const DomDev& D, int cur, int x0,
+                                            int y0, int tw, int th, unsigned char* st,
+                                            unsigned long long* bar, unsigned extra = 0)
+{
+    using T = typename S::T;
+    constexpr int es = (int)sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const int nrows = min(th, D.ny - y0);
+    const int ncols = min(tw, D.nxp - x0);
+    const unsigned rowb = (unsigned)(ncols * es);
+    const int pb = th * tw * es;
+    const char* A = bp.base + (cur == 0 ? D.offA : D.offB);
+    const char* F = bp.base + D.offF;
+    const int sq = (int)D.sq;
+    if (lane == 0)
+        mbar_arrive_expect_tx(bar, 9u * nrows * rowb + (unsigned)(nrows * ncols) + extra);
+    for (int c = lane; c < 10 * nrows; c += 32) {
+        const int i = c / nrows, r = c - i * nrows;
+        if (i < 9) {
+            int ys = y0 + r - d2q9_ey(i);
+            ys = ys < 0 ? ys + D.ny : (ys >= D.ny ? ys - D.ny : ys);
+            bulk_g2s(st + i * pb + r * tw * es, A + (size_t)(i * sq + ys * D.nxp + x0) * es, rowb,
+                     bar);
+        } else {
+            bulk_g2s(st + 9 * pb + r * tw, F + (size_t)((y0 + r) * D.nxp + x0), (unsigned)ncols,
+                     bar);
+        }
+    }
+    const int cl = x0 == 0 ? D.nx - 1 : x0 - 1;
+    const int cr = x0 + tw < D.nx ? x0 + tw : 0;
+    unsigned* halo = reinterpret_cast<unsigned*>(st + stage_halo_offset(es, tw, th));
+    for (int c = lane; c < 6 * nrows; c += 32) {
+        const int k = c / nrows, r = c - k * nrows;
+        const int i = halo_plane(k);
+        int ys = y0 + r - d2q9_ey(i);
+        ys = ys < 0 ? ys + D.ny : (ys >= D.ny ? ys - D.ny : ys);
+        int col = k < 3 ? cl : cr;
+        if (es == 2) col &= ~1;                      // the aligned pair holding it
+        cp4_g2s(halo + k * th + r, A + (size_t)(i * sq + ys * D.nxp + col) * es);
+    }
+    cp_arrive_noinc(bar);
+}
+
+template <class S>
+__device__ __forceinline__ float stage_dec(typename S::T v)
+{
+    if constexpr (S::kHalf) return __half2float(v);
+    else return v;
+}
+
+// a halo element from its 4-byte word (half-width: the half at column col)
+template <class S>
+__device__ __forceinline__ float halo_dec(unsigned w, int col)
+{
+    if constexpr (S::kHalf) {
+        const unsigned short h = (col & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+        return __half2float(__ushort_as_half(h));
+    } else {
+        return __uint_as_float(w);
+    }
+}
+
+// next tile in (domain, y0, x0) order; loads the domain record on entering
+// a domain when `more`
+__device__ __forceinline__ void tile_advance(const BatchParams& bp, DomDev& D, int& dom, int& x0,
+                                             int& y0, int tw, bool more)
+{
+    x0 += tw;
+    if (x0 >= D.nx) {
+        x0 = 0;
+        y0 += bp.th;
+        if (y0 >= D.ny) {
+            y0 = 0;
+            ++dom;
+            if (more) D = bp.dom[dom];
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up when another thread of the CTA has
+// raised *abort.
+__device__ __forceinline__ bool mbar_wait_abortable(unsigned long long* bar, unsigned parity,
+                                                    long long cycles, volatile int* abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > cycles) return false;
+    }
+    return true;
+}
+
+// Update of the nodes of one staged tile owned by consumer thread (tx, ty)
+// of a tw x cy arrangement.
+template <class S>
+__device__ __forceinline__ void staged_tile(const BatchParams& bp, const DomDev& D, int cur, int x0,
+                                            int y0, int tw, int th, int tx, int ty, int cy, bool out,
+                                            const unsigned char* st)
+{
+    using T = typename S::T;
+    using L = D2Q9;
+    constexpr int es = (int)sizeof(T);
+    const int pb = th * tw * es;
+    const T* __restrict__ A = reinterpret_cast<const T*>(bp.base + (cur == 0 ? D.offA : D.offB));
+    T* __restrict__ B = reinterpret_cast<T*>(bp.base + (cur == 0 ? D.offB : D.offA));
+    const uint8_t* __restrict__ flags = reinterpret_cast<const uint8_t*>(bp.base + D.offF);
+    float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
+    const T* pl = reinterpret_cast<const T*>(st);
+    const unsigned* halo = reinterpret_cast<const unsigned*>(st + stage_halo_offset(es, tw, th));
+    const int x = x0 + tx;
+    if (x >= D.nx) return;
+    const int nrows = min(th, D.ny - y0);
+    const int cl = x0 == 0 ? D.nx - 1 : x0 - 1;
+    const int cr = x0 + tw < D.nx ? x0 + tw : 0;
+    const bool left_h = tx == 0;
+    const bool right_h = tx + 1 == tw || x + 1 == D.nx;
+    for (int r = ty; r < nrows; r += cy) {
+        const int y = y0 + r;
+        const int n = y * D.nxp + x;
+        const unsigned fl = st[9 * pb + r * tw + tx];
+        if (fl & FLAG_SOLID) {
+            if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+            continue;
+        }
+        float d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const T* row = pl + (i * th + r) * tw;
+            if (L::ex(i) == 0)
+                d[i] = stage_dec<S>(row[tx]);
+            else if (L::ex(i) == 1)
+                d[i] = left_h ? halo_dec<S>(halo[halo_slot(i) * th + r], cl)
+                              : stage_dec<S>(row[tx - 1]);
+            else
+                d[i] = right_h ? halo_dec<S>(halo[halo_slot(i) * th + r], cr)
+                               : stage_dec<S>(row[tx + 1]);
+        }
+        if (fl & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, x, y, d);
+        batch_update<S>(D, bp, B, o, n, out, d);
+    }
+}
+
+// blockDim.x = 32 + consumer threads: warp 0 produces, the rest consume.
+template <class S>
+__global__ void __launch_bounds__(544) k_batch_staged(const BatchParams bp)
+{
+    using T = typename S::T;
+    constexpr int es = (int)sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+    __shared__ int abort_flag;
+    volatile int* abort_v = &abort_flag;
+    const int tw = bp.tw, th = bp.th;
+    const int ncons = (int)blockDim.x - 32;
+    const int sb = tile_stage_bytes(es, tw, th);
+    const int G = gridDim.x;
+    const int t0 = (int)((long long)bp.ntiles * blockIdx.x / G);
+    const int t1 = (int)((long long)bp.ntiles * (blockIdx.x + 1) / G);
+    const bool producer = threadIdx.x < 32;
+    const int lane = threadIdx.x & 31;
+    const long long wait_cycles = bp.wait_limit * 256;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 33);                 // expect_tx arrival + 32 lanes' copies
+            mbar_init(&empty[s], ncons / 32);        // one arrival per consumer warp
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int4 first = make_int4(0, 0, 0, 0);
+    if (t0 < t1) first = bp.tiles[t0];
+    unsigned k = 0;                                  // tiles through the ring so far
+    int cur = bp.cur;
+    for (int step = 0; step < bp.nsteps; ++step) {
+        const bool out = (step == bp.nsteps - 1);
+        int dom = first.x, x0 = first.y, y0 = first.z;
+        DomDev D{};
+        if (t0 < t1) D = bp.dom[dom];
+        if (producer) {
+            fence_proxy_async_global();
+            for (int t = t0; t < t1; ++t, ++k) {
+                const int s = (int)(k % kStages);
+                const unsigned use = k / kStages;
+                if (use > 0 &&
+                    !mbar_wait_abortable(&empty[s], (use - 1) & 1u, wait_cycles, abort_v)) {
+                    *abort_v = 1;
+                    break;
+                }
+                stage_issue<S>(bp, D, cur, x0, y0, tw, th, smem + s * sb, &full[s],
+                               (bp.withhold == 2 && step == 0 && t == t0) ? 16u : 0u);
+                tile_advance(bp, D, dom, x0, y0, tw, t + 1 < t1);
+            }
+        } else {
+            const int c = (int)threadIdx.x - 32;
+            const int tx = c % tw, ty = c / tw, cy = ncons / tw;
+            for (int t = t0; t < t1; ++t, ++k) {
+                const int s = (int)(k % kStages);
+                const unsigned use = k / kStages;
+                if (!mbar_wait_abortable(&full[s], use & 1u, wait_cycles, abort_v)) {
+                    *abort_v = 1;
+                    break;
+                }
+                staged_tile<S>(bp, D, cur, x0, y0, tw, th, tx, ty, cy, out, smem + s * sb);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                tile_advance(bp, D, dom, x0, y0, tw, t + 1 < t1);
+            }
+        }
+        cur ^= 1;
+        if (__syncthreads_or(*abort_v)) {
+            // the CTA stops together; the producer first lets the copies it
+            // issued land (bounded), so no copy targets a finished CTA
+            if (producer) {
+#pragma unroll 1
+                for (int s = 0; s < kStages; ++s) {
+                    if (k <= (unsigned)s) continue;
+                    const unsigned last = (k - 1 - s) / kStages;       // last use of stage s
+                    mbar_wait_bounded(&full[s], last & 1u, wait_cycles);
+                }
+            }
+            if (threadIdx.x == 0) atomicOr(bp.status, STATUS_TIMEOUT);
+            return;
+        }
+        if (step + 1 < bp.nsteps) {
+            fence_proxy_async_global();
+            const bool skip = bp.withhold == 1 && blockIdx.x == 0 && step == 0;
+            if (!grid_barrier(bp, skip)) return;
+        }
+    }
+}
+
+template <class S>
+const void* staged_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch_staged<S>); }
 
 template <class S, int NPT>
 const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch<S, NPT>); }
@@ -307,11 +692,21 @@ static void drop_graphs(lbm_batch b)
 static const void* kernel_for(int dtype, int npt)
 {
     if (dtype == LBM_F16S)
-        return npt == 4 ? batch_kernel_ptr<StoreF16S, 4>()
+        return npt == 0   ? staged_kernel_ptr<StoreF16S>()
+             : npt == 4 ? batch_kernel_ptr<StoreF16S, 4>()
              : npt == 2 ? batch_kernel_ptr<StoreF16S, 2>() : batch_kernel_ptr<StoreF16S, 1>();
-    return npt == 4 ? batch_kernel_ptr<StoreF32S, 4>()
+    return npt == 0   ? staged_kernel_ptr<StoreF32S>()
+         : npt == 4 ? batch_kernel_ptr<StoreF32S, 4>()
          : npt == 2 ? batch_kernel_ptr<StoreF32S, 2>() : batch_kernel_ptr<StoreF32S, 1>();
 }
+
+// dynamic shared memory of a launch (the staged kernel's two stages)
+static size_t launch_smem(lbm_batch b, int tw, int th, int npt)
+{
+    return npt == 0 ? kStages * (size_t)tile_stage_bytes((int)b->esize, tw, th) : 0;
+}
+
+constexpr size_t kMaxStagedSmem = 200 * 1024;
 
 // Build and upload the tile list for tile shape (tw, th).
 static int upload_tiles(lbm_batch b, int tw, int th)
@@ -334,10 +729,23 @@ static int upload_tiles(lbm_batch b, int tw, int th)
     return LBM_OK;
 }
 
-static int max_ctas(lbm_batch b, int threads, int npt)
+static int max_ctas(lbm_batch b, int threads, int npt, int tw, int th)
 {
+    const size_t smem = launch_smem(b, tw, th, npt);
+    if (smem > kMaxStagedSmem) return 0;
+    const void* k = kernel_for(b->dtype, npt);
+    if (npt == 0 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStagedSmem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(b->dtype, npt), threads, 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, npt == 0 ? threads + 32 : threads,
+                                                      smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return per_sm * b->sms;
 }
 
@@ -351,6 +759,7 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     bp.nsteps = nsteps;
     bp.cur = from;
     bp.th = b->th;
+    bp.tw = b->tw;
     bp.bar = reinterpret_cast<unsigned*>(b->base + b->off_bar);
     bp.status = reinterpret_cast<unsigned*>(b->base + b->off_bar + 8);
     bp.wait_limit = b->wait_limit;
@@ -361,8 +770,9 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(b->ctas);
-    cfg.blockDim = dim3(b->tw, b->threads / b->tw);
-    cfg.dynamicSmemBytes = 0;
+    // the staged kernel adds its producer warp to the consumer threads
+    cfg.blockDim = b->npt == 0 ? dim3(b->threads + 32) : dim3(b->tw, b->threads / b->tw);
+    cfg.dynamicSmemBytes = launch_smem(b, b->tw, b->th, b->npt);
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -451,7 +861,7 @@ int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, 
         delete b;
         return bfail(nullptr, r, "%s", m.c_str());
     }
-    b->ctas = std::min(max_ctas(b, b->threads, b->npt), std::max(1, b->ntiles));
+    b->ctas = std::min(max_ctas(b, b->threads, b->npt, b->tw, b->th), std::max(1, b->ntiles));
     if (b->ctas < 1) {
         cudaFree(p);
         delete b;
@@ -629,17 +1039,19 @@ int lbm_batch_autotune(lbm_batch b)
     float best = 1e30f;
     int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th, bn = b->npt;
     const int steps = 4;
-    for (int npt : {1, 2, 4})
+    // npt 0: the staged kernel; 1, 2, 4: the register kernel's rows per pass
+    for (int npt : {0, 1, 2, 4})
         for (int threads : {128, 256, 512})
             for (int tw : {64, 128, 256}) {
                 if (tw > threads) continue;
-                const int mc = max_ctas(b, threads, npt);
-                if (mc < 1) continue;
                 for (int th : {2, 4, 8, 16, 32, 64}) {
-                    if (th < npt * (threads / tw)) continue;
+                    if (th < std::max(npt, 1) * (threads / tw)) continue;
+                    if (npt == 0 && th > 32) continue;
+                    const int mc = max_ctas(b, threads, npt, tw, th);
+                    if (mc < 1) continue;
                     if (upload_tiles(b, tw, th)) continue;
                     const int per_sm = std::max(1, mc / b->sms);
-                    for (int k = 1; k <= per_sm; k *= 2) {
+                    for (int k = 1; k <= per_sm; k = (k * 2 > per_sm && k < per_sm) ? per_sm : k * 2) {
                         b->threads = threads; b->tw = tw; b->th = th; b->npt = npt;
                         b->ctas = std::min(k * b->sms, b->ntiles);
                         if (launch_batch(b, 1, b->cur) != cudaSuccess) {
@@ -695,10 +1107,13 @@ int lbm_batch_set_config(lbm_batch b, const int* in5)
     if (tw < 32 || tw % 32 || threads < tw || threads > 512 || threads % tw)
         return bfail(b, LBM_EINVAL, "threads %d / tile width %d: need 32 | tw, tw | threads <= 512",
                      threads, tw);
-    if (npt != 1 && npt != 2 && npt != 4)
-        return bfail(b, LBM_EINVAL, "rows per thread and pass must be 1, 2 or 4");
+    if (npt != 0 && npt != 1 && npt != 2 && npt != 4)
+        return bfail(b, LBM_EINVAL, "rows per thread and pass must be 0 (staged), 1, 2 or 4");
     if (th < 1 || th > 4096) return bfail(b, LBM_EINVAL, "tile rows %d out of range", th);
-    const int mc = max_ctas(b, threads, npt);
+    if (launch_smem(b, tw, th, npt) > kMaxStagedSmem)
+        return bfail(b, LBM_EINVAL, "staged tile %d x %d needs %zu bytes of shared memory", tw, th,
+                     launch_smem(b, tw, th, npt));
+    const int mc = max_ctas(b, threads, npt, tw, th);
     if (ctas < 1 || ctas > mc)
         return bfail(b, LBM_EINVAL, "%d CTAs: between 1 and %d can be co-resident", ctas, mc);
     int r = upload_tiles(b, tw, th);
@@ -734,7 +1149,8 @@ int lbm_batch_set_rounding(lbm_batch b, int mode)
 int lbm_batch_inject_missing_arrival(lbm_batch b, int on)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
-    b->withhold = on ? 1 : 0;
+    if (on < 0 || on > 2) return bfail(b, LBM_EINVAL, "hook %d: 0, 1 or 2", on);
+    b->withhold = on;
     drop_graphs(b);
     return LBM_OK;
 }

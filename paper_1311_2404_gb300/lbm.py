@@ -467,7 +467,7 @@ def lbm_batch_set_wait_limit(b, spins):
 
 
 def lbm_batch_inject_missing_arrival(b, on):
-    _check(_L.lbm_batch_inject_missing_arrival(b, int(bool(on))), b, batch=True)
+    _check(_L.lbm_batch_inject_missing_arrival(b, int(on)), b, batch=True)
 
 
 def lbm_batch_sync(b):

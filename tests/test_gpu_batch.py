@@ -188,6 +188,12 @@ CONFIGS = [
     (512, 2, 128, 64, 4),
     (96, 5, 32, 1, 4),        # one-row tiles: only the first row of a pass exists
     (256, 11, 256, 16, 2),
+    # the staged kernel (bulk copies into double-buffered shared memory)
+    (256, 7, 128, 8, 0),
+    (64, 1, 32, 3, 0),
+    (128, 3, 64, 5, 0),
+    (512, 2, 64, 16, 0),
+    (96, 5, 32, 1, 0),
 ]
 
 
@@ -213,13 +219,38 @@ def test_every_launch_configuration_gives_the_same_bits(dtype):
             assert np.array_equal(r1, r2) and np.array_equal(u1, u2), cfg
 
 
+@pytest.mark.parametrize("hook,cfg", [(1, (256, 4, 128, 8, 0)), (2, (256, 4, 128, 8, 0)),
+                                      (2, (64, 1, 32, 2, 0))])
+def test_staged_kernel_bounded_waits(hook, cfg):
+    """Hook 1: a withheld grid-barrier arrival; hook 2: a stage whose copies
+    deliver fewer bytes than it expects.  Either wait runs out, the next
+    synchronising call reports LBM_ETIMEOUT, and the context stays usable."""
+    specs = _specs(4, seed=23)
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_set_config(b, cfg)
+    lbm.lbm_batch_set_wait_limit(b, 20000)
+    lbm.lbm_batch_inject_missing_arrival(b, hook)
+    lbm.lbm_batch_step(b, 3)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_sync(b)
+    assert ei.value.code == lbm.LBM_ETIMEOUT
+    lbm.lbm_batch_destroy(b)
+    b = _make_batch(specs, lbm.LBM_F32S)
+    lbm.lbm_batch_set_config(b, cfg)
+    lbm.lbm_batch_step(b, 3)
+    lbm.lbm_batch_sync(b)
+    lbm.lbm_batch_destroy(b)
+    x = torch.ones(4, device="cuda") * 2
+    assert float(x.sum()) == 8.0
+
+
 def test_set_config_rejects_bad_values():
     specs = _specs(3, seed=22)
     b = _make_batch(specs, lbm.LBM_F32S)
     before = list(lbm.lbm_batch_get_config(b))
     for bad in [(256, 4, 48, 8, 1), (256, 4, 128, 8, 3), (1024, 4, 128, 8, 1),
                 (256, 0, 128, 8, 1), (256, 10 ** 6, 128, 8, 1), (192, 4, 128, 8, 1),
-                (256, 4, 128, 0, 1)]:
+                (256, 4, 128, 0, 1), (512, 4, 256, 32, 0)]:
         with pytest.raises(lbm.LBMError) as ei:
             lbm.lbm_batch_set_config(b, bad)
         assert ei.value.code == lbm.LBM_EINVAL
