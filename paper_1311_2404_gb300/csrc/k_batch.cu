@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
 // min(tw, nxp - x0) elements is a multiple of 32.
 
 constexpr int kStages = 4;
+constexpr int kStagedMaxThreads = 256;   // consumer threads per CTA
 
 __host__ __device__ constexpr int tile_stage_bytes(int esize, int tw, int th)
 {
@@ -480,12 +481,42 @@ __device__ __forceinline__ bool mbar_wait_abortable(unsigned long long* bar, uns
     return true;
 }
 
-// Update of the nodes of one staged tile owned by consumer thread (tx, ty)
-// of a tw x cy arrangement.
+// rho, v of an output step, with the non-finite check
+__device__ __forceinline__ void batch_out(const DomDev& D, const BatchParams& bp,
+                                          float* __restrict__ o, int n, float rho,
+                                          const float (&v)[3])
+{
+    o[n] = rho;
+    o[D.sq + n] = v[0];
+    o[2 * D.sq + n] = v[1];
+    if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(bp.status, STATUS_NAN);
+}
+
+// store of one node's nine values (the one-node path's rounding)
 template <class S>
-__device__ __forceinline__ void staged_tile(const BatchParams& bp, const DomDev& D, int cur, int x0,
-                                            int y0, int tw, int th, int tx, int ty, int cy, bool out,
-                                            const unsigned char* st)
+__device__ __forceinline__ void staged_store1(const BatchParams& bp, typename S::T* __restrict__ B,
+                                              int sq, int n, unsigned salt, const float (&d)[9])
+{
+    using L = D2Q9;
+    if constexpr (S::kHalf) {
+        if (!bp.round_nearest) {
+            store_node_sr<L, S>(d, salt, [&](int i) { return B + (i * sq + n); });
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) S::store(B + (i * sq + n), d[i], L::w(i));
+}
+
+// Update of two x-adjacent nodes (tile columns c0 = 2 pp and c0 + 1) on the
+// rows ty, ty + cy, ... of one staged tile.  Same per-node arithmetic and the
+// same per-value stochastic rounding as the one-node path: a half-width
+// direction of the pair is one conversion and one 32-bit store, an FP32
+// direction one 64-bit store.
+template <class S>
+__device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev& D, int cur,
+                                             int x0, int y0, int tw, int th, int pp, int ty,
+                                             int cy, bool out, const unsigned char* st)
 {
     using T = typename S::T;
     using L = D2Q9;
@@ -497,42 +528,98 @@ __device__ __forceinline__ void staged_tile(const BatchParams& bp, const DomDev&
     float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
     const T* pl = reinterpret_cast<const T*>(st);
     const unsigned* halo = reinterpret_cast<const unsigned*>(st + stage_halo_offset(es, tw, th));
-    const int x = x0 + tx;
-    if (x >= D.nx) return;
+    const int c0 = 2 * pp;
+    const int xa = x0 + c0;
+    if (xa >= D.nx) return;
+    const bool vb = xa + 1 < D.nx;              // node b exists
     const int nrows = min(th, D.ny - y0);
+    const int sq = (int)D.sq;
     const int cl = x0 == 0 ? D.nx - 1 : x0 - 1;
     const int cr = x0 + tw < D.nx ? x0 + tw : 0;
-    const bool left_h = tx == 0;
-    const bool right_h = tx + 1 == tw || x + 1 == D.nx;
+    const bool a_left = c0 == 0;                 // node a's e_x = +1 source is the left halo
+    const bool a_right = !vb;                    // node a = nx - 1: its e_x = -1 source wraps
+    const bool b_right = c0 + 2 == tw || xa + 2 == D.nx;
     for (int r = ty; r < nrows; r += cy) {
         const int y = y0 + r;
-        const int n = y * D.nxp + x;
-        const unsigned fl = st[9 * pb + r * tw + tx];
-        if (fl & FLAG_SOLID) {
-            if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+        const int n = y * D.nxp + xa;
+        const unsigned char* frow = st + 9 * pb + r * tw;
+        const unsigned fa = frow[c0];
+        const unsigned fb = vb ? frow[c0 + 1] : (unsigned)FLAG_SOLID;
+        const bool la = !(fa & FLAG_SOLID), lb = !(fb & FLAG_SOLID);
+        if (!la && !lb) {
+            if (out) {
+                o[n] = 0.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f;
+                if (vb) { o[n + 1] = 0.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
+            }
             continue;
         }
-        float d[9];
+        float da[9], db[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const T* row = pl + (i * th + r) * tw;
-            if (L::ex(i) == 0)
-                d[i] = stage_dec<S>(row[tx]);
-            else if (L::ex(i) == 1)
-                d[i] = left_h ? halo_dec<S>(halo[halo_slot(i) * th + r], cl)
-                              : stage_dec<S>(row[tx - 1]);
-            else
-                d[i] = right_h ? halo_dec<S>(halo[halo_slot(i) * th + r], cr)
-                               : stage_dec<S>(row[tx + 1]);
+            if (L::ex(i) == 0) {
+                da[i] = stage_dec<S>(row[c0]);
+                db[i] = stage_dec<S>(row[c0 + 1]);
+            } else if (L::ex(i) == 1) {
+                da[i] = a_left ? halo_dec<S>(halo[halo_slot(i) * th + r], cl)
+                               : stage_dec<S>(row[c0 - 1]);
+                db[i] = stage_dec<S>(row[c0]);
+            } else {
+                da[i] = a_right ? halo_dec<S>(halo[halo_slot(i) * th + r], cr)
+                                : stage_dec<S>(row[c0 + 1]);
+                db[i] = b_right ? halo_dec<S>(halo[halo_slot(i) * th + r], cr)
+                                : stage_dec<S>(row[c0 + 2]);
+            }
         }
-        if (fl & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, x, y, d);
-        batch_update<S>(D, bp, B, o, n, out, d);
+        float ra = 0.f, rb = 0.f, va[3] = {0.f, 0.f, 0.f}, vbv[3] = {0.f, 0.f, 0.f};
+        if (la) {
+            if (fa & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, xa, y, da);
+            bgk_collide<L, float>(da, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, ra, va);
+        }
+        if (lb) {
+            if (fb & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, xa + 1, y, db);
+            bgk_collide<L, float>(db, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rb, vbv);
+        }
+        const unsigned s0 = (unsigned)n * kSaltNode, s1 = s0 + kSaltNode;
+        if (la && lb) {
+            if constexpr (S::kHalf) {
+                if (!bp.round_nearest) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        *reinterpret_cast<unsigned*>(B + (i * sq + n)) =
+                            S::encode_pair(db[i], da[i], s1 + (unsigned)i * kSaltDir,
+                                           s0 + (unsigned)i * kSaltDir);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        S::store(B + (i * sq + n), da[i], L::w(i));
+                        S::store(B + (i * sq + n + 1), db[i], L::w(i));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    *reinterpret_cast<float2*>(B + (i * sq + n)) = make_float2(da[i], db[i]);
+            }
+        } else if (la) {
+            staged_store1<S>(bp, B, sq, n, s0, da);
+        } else {
+            staged_store1<S>(bp, B, sq, n + 1, s1, db);
+        }
+        if (out) {
+            if (la) batch_out(D, bp, o, n, ra, va);
+            else { o[n] = 0.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f; }
+            if (vb) {
+                if (lb) batch_out(D, bp, o, n + 1, rb, vbv);
+                else { o[n + 1] = 0.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
+            }
+        }
     }
 }
 
 // blockDim.x = 32 + consumer threads: warp 0 produces, the rest consume.
 template <class S>
-__global__ void __launch_bounds__(544) k_batch_staged(const BatchParams bp)
+__global__ void __launch_bounds__(kStagedMaxThreads + 32) k_batch_staged(const BatchParams bp)
 {
     using T = typename S::T;
     constexpr int es = (int)sizeof(T);
@@ -584,7 +671,8 @@ __global__ void __launch_bounds__(544) k_batch_staged(const BatchParams bp)
             }
         } else {
             const int c = (int)threadIdx.x - 32;
-            const int tx = c % tw, ty = c / tw, cy = ncons / tw;
+            const int hw = tw / 2;                   // threads per tile row (two nodes each)
+            const int pp = c % hw, ty = c / hw, cy = ncons / hw;
             for (int t = t0; t < t1; ++t, ++k) {
                 const int s = (int)(k % kStages);
                 const unsigned use = k / kStages;
@@ -592,7 +680,7 @@ __global__ void __launch_bounds__(544) k_batch_staged(const BatchParams bp)
                     *abort_v = 1;
                     break;
                 }
-                staged_tile<S>(bp, D, cur, x0, y0, tw, th, tx, ty, cy, out, smem + s * sb);
+                staged_tile2<S>(bp, D, cur, x0, y0, tw, th, pp, ty, cy, out, smem + s * sb);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
                 tile_advance(bp, D, dom, x0, y0, tw, t + 1 < t1);
@@ -1045,8 +1133,9 @@ int lbm_batch_autotune(lbm_batch b)
             for (int tw : {64, 128, 256}) {
                 if (tw > threads) continue;
                 for (int th : {2, 4, 8, 16, 32, 64}) {
-                    if (th < std::max(npt, 1) * (threads / tw)) continue;
-                    if (npt == 0 && th > 32) continue;
+                    // every consumer thread gets a row (staged: two columns per thread)
+                    if (th < (npt == 0 ? 2 : npt) * (threads / tw)) continue;
+                    if (npt == 0 && (th > 32 || threads > kStagedMaxThreads)) continue;
                     const int mc = max_ctas(b, threads, npt, tw, th);
                     if (mc < 1) continue;
                     if (upload_tiles(b, tw, th)) continue;
@@ -1109,6 +1198,9 @@ int lbm_batch_set_config(lbm_batch b, const int* in5)
                      threads, tw);
     if (npt != 0 && npt != 1 && npt != 2 && npt != 4)
         return bfail(b, LBM_EINVAL, "rows per thread and pass must be 0 (staged), 1, 2 or 4");
+    if (npt == 0 && threads > kStagedMaxThreads)
+        return bfail(b, LBM_EINVAL, "the staged kernel takes at most %d consumer threads",
+                     kStagedMaxThreads);
     if (th < 1 || th > 4096) return bfail(b, LBM_EINVAL, "tile rows %d out of range", th);
     if (launch_smem(b, tw, th, npt) > kMaxStagedSmem)
         return bfail(b, LBM_EINVAL, "staged tile %d x %d needs %zu bytes of shared memory", tw, th,

@@ -53,3 +53,12 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
                             impl="reference", gpus=2)
     bench.run_reference(ns)
     assert capsys.readouterr().out == ""
+
+
+def test_algorithmic_bytes_count_solid_nodes_by_their_geometry_word():
+    """A fluid node moves its q values in and out plus its geometry word; a
+    solid node only the word (D3Q19 FP32S: 156 B and 4 B)."""
+    assert bench.bytes_per_node("f32s", 1) == 152
+    assert bench.bytes_per_node("f16s", 0) == 36
+    assert bench.algorithmic_bytes(100, 80, 156, 4) == 80 * 156 + 20 * 4
+    assert bench.algorithmic_bytes(10, 10, 152, 0) == 1520

@@ -192,7 +192,7 @@ CONFIGS = [
     (256, 7, 128, 8, 0),
     (64, 1, 32, 3, 0),
     (128, 3, 64, 5, 0),
-    (512, 2, 64, 16, 0),
+    (256, 2, 64, 16, 0),
     (96, 5, 32, 1, 0),
 ]
 
