@@ -486,100 +486,202 @@ __host__ __device__ constexpr bool mrt_odd(int k)
     return (k >= 3 && k <= 8) || k >= 16;
 }
 
-// MRT collision.  Every basis row is even or odd under e -> -e, and the
-// velocity set comes in opposite pairs (2q+1, 2q+2), so both transforms split
-// over the 9 pairs: even moments use pair sums, odd moments pair differences,
-// and the inverse transform returns an even part (added to both members) and
-// an odd part (added to one, subtracted from the other).  Same arithmetic as
-// m = M n, f' = f - M^T diag(1/|M_k|^2) t, with about half the operations.
+// MRT collision, Eq. mrt_collision with Guo's term in moment space:
+//   m' = m - S (m - m_eq) + (I - S/2) M F~,   f' = f + M^-1 (m' - m).
+// Written in closed form for this basis instead of as generic 19 x 19
+// products:
+//  * the moments of the deviations d = f - w come from the opposite-pair
+//    sums (even rows) and differences (odd rows) with the rows' small
+//    integer coefficients (checked against mrt_poly at compile time);
+//  * the equilibrium moments of the polynomial f_eq(rho, v) (Eq. equilibrium)
+//    in this basis are, with the weights' own moments (e 11, eps 3) removed:
+//      e: -11 drho + 19 rho v^2     eps: 3 drho - 11/2 rho v^2
+//      3p_xx: rho (3 v_x^2 - v^2)   3pi_xx: -1/2 of 3p_xx
+//      p_ww: rho (v_y^2 - v_z^2)    pi_ww: -1/2 of p_ww
+//      p_ab: rho v_a v_b            q_a: -2/3 rho v_a     m_a: 0
+//  * the moments of Guo's term F~_i = w_i [3 (e_i - v) + 9 (e_i.v) e_i].F are
+//      rho 0, j_a F_a, e 38 v.F, eps -11 v.F, q_a -2/3 F_a, m_a 0,
+//      3p_xx 2 G_x, 3pi_xx -G_x with G_x = 3 v_x F_x - v.F,
+//      p_ww 2 G_w, pi_ww -G_w with G_w = v_y F_y - v_z F_z,
+//      p_ab v_a F_b + v_b F_a
+//    (the second-order terms follow from 4th-order isotropy, the 6th-order
+//    sums for pi vanish on D3Q19 like those of its equilibrium);
+//  * the conserved rows need no rate: m - m_eq is 0 for rho and -F/2 for j
+//    (v is Guo's force-shifted velocity), so m' - m is 0 and F for any s;
+//  * the inverse M^-1 = M^T diag(1/|M_k|^2) is applied per opposite pair:
+//    an even part shared by both members and an odd part of opposite sign.
+// t_k = c_k (m_k - m_eq_k) - cf_k mf_k with c_k = s_k/|M_k|^2 and
+// cf_k = (1 - s_k/2)/|M_k|^2 from the host; f' = f - M^T t.
+// ---------------------------------------------------------------------------
+namespace mrt_check {
+// pair q of D3Q19 has the directions 2q+1 (e_q) and 2q+2 (-e_q): three axis
+// pairs x, y, z, then xy (1,1,0), (1,-1,0), xz (1,0,1), (1,0,-1),
+// yz (0,1,1), (0,1,-1).  Every coefficient the operator uses, by row k and
+// direction i:
+constexpr bool rows_ok()
+{
+    // even rows: rest, axis x, y, z, xy+, xy-, xz+, xz-, yz+, yz-
+    constexpr int ev[10][10] = {
+        /* e     */ {-30, -11, -11, -11, 8, 8, 8, 8, 8, 8},
+        /* eps   */ {12, -4, -4, -4, 1, 1, 1, 1, 1, 1},
+        /* 3pxx  */ {0, 2, -1, -1, 1, 1, 1, 1, -2, -2},
+        /* 3pixx */ {0, -4, 2, 2, 1, 1, 1, 1, -2, -2},
+        /* pww   */ {0, 0, 1, -1, 1, 1, -1, -1, 0, 0},
+        /* piww  */ {0, 0, -2, 2, 1, 1, -1, -1, 0, 0},
+        /* pxy   */ {0, 0, 0, 0, 1, -1, 0, 0, 0, 0},
+        /* pyz   */ {0, 0, 0, 0, 0, 0, 0, 0, 1, -1},
+        /* pxz   */ {0, 0, 0, 0, 0, 0, 1, -1, 0, 0},
+        /* rho   */ {1, 1, 1, 1, 1, 1, 1, 1, 1, 1}};
+    constexpr int evk[10] = {1, 2, 9, 10, 11, 12, 13, 14, 15, 0};
+    // odd rows on the first member of each pair
+    constexpr int od[9][9] = {
+        /* jx */ {1, 0, 0, 1, 1, 1, 1, 0, 0},
+        /* qx */ {-4, 0, 0, 1, 1, 1, 1, 0, 0},
+        /* jy */ {0, 1, 0, 1, -1, 0, 0, 1, 1},
+        /* qy */ {0, -4, 0, 1, -1, 0, 0, 1, 1},
+        /* jz */ {0, 0, 1, 0, 0, 1, -1, 1, -1},
+        /* qz */ {0, 0, -4, 0, 0, 1, -1, 1, -1},
+        /* mx */ {0, 0, 0, 1, 1, -1, -1, 0, 0},
+        /* my */ {0, 0, 0, -1, 1, 0, 0, 1, 1},
+        /* mz */ {0, 0, 0, 0, 0, 1, -1, -1, 1}};
+    constexpr int odk[9] = {3, 4, 5, 6, 7, 8, 16, 17, 18};
+    for (int r = 0; r < 10; ++r) {
+        if (mrt_odd(evk[r])) return false;
+        if (mrt_M(evk[r], 0) != ev[r][0]) return false;
+        for (int q = 0; q < 9; ++q)
+            if (mrt_M(evk[r], 2 * q + 1) != ev[r][q + 1] ||
+                mrt_M(evk[r], 2 * q + 2) != ev[r][q + 1])
+                return false;
+    }
+    for (int r = 0; r < 9; ++r) {
+        if (!mrt_odd(odk[r]) || mrt_M(odk[r], 0) != 0) return false;
+        for (int q = 0; q < 9; ++q)
+            if (mrt_M(odk[r], 2 * q + 1) != od[r][q] || mrt_M(odk[r], 2 * q + 2) != -od[r][q])
+                return false;
+    }
+    return mrt_norm2(3) == 10 && mrt_norm2(5) == 10 && mrt_norm2(7) == 10;
+}
+static_assert(rows_ok(), "closed-form MRT rows disagree with the basis polynomials");
+}  // namespace mrt_check
+
 template <class R>
 __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& rho_out,
                                                      R (&v)[3])
 {
-    using L = D3Q19;
+    // pair sums and differences; axis pairs 0..2, then the diagonal pairs
     R S[9], A[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         S[q] = d[2 * q + 1] + d[2 * q + 2];
         A[q] = d[2 * q + 1] - d[2 * q + 2];
     }
-    R drho = d[0], j[3] = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const int i = 2 * q + 1;
-        drho += S[q];
-        if (L::ex(i)) j[0] = L::ex(i) > 0 ? j[0] + A[q] : j[0] - A[q];
-        if (L::ey(i)) j[1] = L::ey(i) > 0 ? j[1] + A[q] : j[1] - A[q];
-        if (L::ez(i)) j[2] = L::ez(i) > 0 ? j[2] + A[q] : j[2] - A[q];
-    }
+    const R Dxy = S[3] + S[4], Dxz = S[5] + S[6], Dyz = S[7] + S[8];
+    const R Sax = (S[0] + S[1]) + S[2], Sdg = (Dxy + Dxz) + Dyz;
+    const R drho = (d[0] + Sax) + Sdg;
+    // diagonal parts of the odd rows (shared by j and q)
+    const R Jx = (A[3] + A[4]) + (A[5] + A[6]);
+    const R Jy = (A[3] - A[4]) + (A[7] + A[8]);
+    const R Jz = (A[5] - A[6]) + (A[7] - A[8]);
+    const R j0 = A[0] + Jx, j1 = A[1] + Jy, j2 = A[2] + Jz;
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
     const R F0 = sel<R>(p.F_f[0], p.F[0]), F1 = sel<R>(p.F_f[1], p.F[1]),
             F2 = sel<R>(p.F_f[2], p.F[2]);
-    v[0] = fma(R(0.5), F0, j[0]) * irho;
-    v[1] = fma(R(0.5), F1, j[1]) * irho;
-    v[2] = fma(R(0.5), F2, j[2]) * irho;
-    const R usq = fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2]));
-    const R m15 = R(-1.5) * usq;
-    const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
     const bool force = p.has_force != 0;
-    // non-equilibrium parts: rest, pair sums (even), pair differences (odd)
-    const R w0 = (R)L::w(0);
-    const R n0 = d[0] - fma(w0 * rho, m15, w0 * drho);
-    const R g0 = force ? R(-3) * w0 * vF : R(0);
-    R NS[9], NA[9], GS[9], GA[9];
+    // Guo: rho v = j + F/2
+    const R jF0 = fma(R(0.5), F0, j0), jF1 = fma(R(0.5), F1, j1), jF2 = fma(R(0.5), F2, j2);
+    v[0] = jF0 * irho;
+    v[1] = jF1 * irho;
+    v[2] = jF2 * irho;
+    const R rx = jF0 * v[0], ry = jF1 * v[1], rz = jF2 * v[2];   // rho v_a^2
+    const R rusq = (rx + ry) + rz;                                // rho v^2
+    auto c = [&](int k) { return sel<R>(p.mrt_c_f[k], p.mrt_c[k]); };
+    auto cf = [&](int k) { return sel<R>(p.mrt_cf_f[k], p.mrt_cf[k]); };
+
+    // non-equilibrium moments
+    const R ne = fma(R(-30), d[0], fma(R(-11), Sax, R(8) * Sdg)) -
+                 fma(R(-11), drho, R(19) * rusq);
+    const R neps = fma(R(12), d[0], fma(R(-4), Sax, Sdg)) - fma(R(3), drho, R(-5.5) * rusq);
+    const R pxx_eq = fma(R(2), rx, -(ry + rz));                   // rho (3 v_x^2 - v^2)
+    const R pww_eq = ry - rz;
+    const R a1 = fma(R(2), S[0], -(S[1] + S[2]));                 // axis part of 3p_xx
+    const R a2 = (Dxy + Dxz) - R(2) * Dyz;                        // diagonal part of both
+    const R npxx = (a1 + a2) - pxx_eq;
+    const R npixx = fma(R(-2), a1, a2) + R(0.5) * pxx_eq;
+    const R b1 = S[1] - S[2], b2 = Dxy - Dxz;
+    const R npww = (b1 + b2) - pww_eq;
+    const R npiww = fma(R(-2), b1, b2) + R(0.5) * pww_eq;
+    const R npxy = (S[3] - S[4]) - jF0 * v[1];
+    const R npyz = (S[7] - S[8]) - jF1 * v[2];
+    const R npxz = (S[5] - S[6]) - jF0 * v[2];
+    constexpr R k23 = R(2) / R(3);
+    const R nqx = fma(R(-4), A[0], Jx) + k23 * jF0;
+    const R nqy = fma(R(-4), A[1], Jy) + k23 * jF1;
+    const R nqz = fma(R(-4), A[2], Jz) + k23 * jF2;
+    const R nmx = (A[3] + A[4]) - (A[5] + A[6]);
+    const R nmy = (A[4] - A[3]) + (A[7] + A[8]);
+    const R nmz = (A[5] - A[6]) - (A[7] - A[8]);
+
+    R te = c(1) * ne, teps = c(2) * neps, tpxx = c(9) * npxx, tpixx = c(10) * npixx;
+    R tpww = c(11) * npww, tpiww = c(12) * npiww;
+    R tpxy = c(13) * npxy, tpyz = c(14) * npyz, tpxz = c(15) * npxz;
+    R tqx = c(4) * nqx, tqy = c(6) * nqy, tqz = c(8) * nqz;
+    const R tmx = c(16) * nmx, tmy = c(17) * nmy, tmz = c(18) * nmz;
+    // momentum rows: m' - m = F, |M_j|^2 = 10
+    R tjx = R(0), tjy = R(0), tjz = R(0);
+    if (force) {
+        const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
+        const R Gx = fma(R(3) * v[0], F0, -vF);
+        const R Gw = fma(v[1], F1, -(v[2] * F2));
+        te = fma(-cf(1), R(38) * vF, te);
+        teps = fma(cf(2), R(11) * vF, teps);
+        tpxx = fma(-cf(9), R(2) * Gx, tpxx);
+        tpixx = fma(cf(10), Gx, tpixx);
+        tpww = fma(-cf(11), R(2) * Gw, tpww);
+        tpiww = fma(cf(12), Gw, tpiww);
+        tpxy = fma(-cf(13), fma(v[0], F1, v[1] * F0), tpxy);
+        tpyz = fma(-cf(14), fma(v[1], F2, v[2] * F1), tpyz);
+        tpxz = fma(-cf(15), fma(v[0], F2, v[2] * F0), tpxz);
+        tqx = fma(cf(4), k23 * F0, tqx);
+        tqy = fma(cf(6), k23 * F1, tqy);
+        tqz = fma(cf(8), k23 * F2, tqz);
+        tjx = R(-0.1) * F0;
+        tjy = R(-0.1) * F1;
+        tjz = R(-0.1) * F2;
+    }
+
+    // inverse transform, f' = f - M^T t
+    d[0] -= fma(R(-30), te, R(12) * teps);
+    const R Eax = fma(R(-11), te, R(-4) * teps);
+    const R Edg = fma(R(8), te, teps);
+    const R P1 = fma(R(2), tpixx, -tpxx);            // y and z axis pairs; x gets -2 P1
+    const R W = fma(R(-2), tpiww, tpww);             // +y, -z
+    const R Q1 = tpxx + tpixx, Q2 = tpww + tpiww;    // diagonal pairs
+    const R X = tjx + tqx, Y = tjy + tqy, Z = tjz + tqz;
+    R ev[9], od[9];
+    ev[0] = fma(R(-2), P1, Eax);
+    ev[1] = (Eax + P1) + W;
+    ev[2] = (Eax + P1) - W;
+    od[0] = fma(R(-4), tqx, tjx);
+    od[1] = fma(R(-4), tqy, tjy);
+    od[2] = fma(R(-4), tqz, tjz);
+    const R exy = (Edg + Q1) + Q2, exz = (Edg + Q1) - Q2, eyz = fma(R(-2), Q1, Edg);
+    ev[3] = exy + tpxy;
+    ev[4] = exy - tpxy;
+    ev[5] = exz + tpxz;
+    ev[6] = exz - tpxz;
+    ev[7] = eyz + tpyz;
+    ev[8] = eyz - tpyz;
+    od[3] = (X + Y) + (tmx - tmy);
+    od[4] = (X - Y) + (tmx + tmy);
+    od[5] = (X + Z) + (tmz - tmx);
+    od[6] = (X - Z) - (tmx + tmz);
+    od[7] = (Y + Z) + (tmy - tmz);
+    od[8] = (Y - Z) + (tmy + tmz);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const int i = 2 * q + 1;
-        const R wi = (R)L::w(i);
-        const R bi = first_order_coef<L, R>(i);
-        const R eu = edot<L, R>(i, v[0], v[1], v[2]);
-        NS[q] = fma(R(-2), fma(wi * rho, fma(R(4.5) * eu, eu, m15), wi * drho), S[q]);
-        NA[q] = fma(R(-2), (bi * rho) * eu, A[q]);
-        if (force) {
-            const R eF = edot<L, R>(i, F0, F1, F2);
-            GS[q] = R(2) * wi * fma(R(9) * eu, eF, R(-3) * vF);  // Guo term, pair sum
-            GA[q] = R(2) * bi * eF;                               // Guo term, pair difference
-        } else {
-            GS[q] = GA[q] = R(0);
-        }
-    }
-    R t[19];
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        R m = 0, mf = 0;
-        if (!mrt_odd(k) && mrt_M(k, 0) != 0) {
-            m = fma(R(mrt_M(k, 0)), n0, m);
-            mf = fma(R(mrt_M(k, 0)), g0, mf);
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int i = 2 * q + 1;
-            if (mrt_M(k, i) != 0) {
-                m = fma(R(mrt_M(k, i)), mrt_odd(k) ? NA[q] : NS[q], m);
-                mf = fma(R(mrt_M(k, i)), mrt_odd(k) ? GA[q] : GS[q], mf);
-            }
-        }
-        const R c = sel<R>(p.mrt_c_f[k], p.mrt_c[k]);
-        t[k] = force ? fma(c, m, -(sel<R>(p.mrt_cf_f[k], p.mrt_cf[k]) * mf)) : c * m;
-    }
-    R e0 = 0;
-#pragma unroll
-    for (int k = 0; k < 19; ++k)
-        if (!mrt_odd(k) && mrt_M(k, 0) != 0) e0 = fma(R(mrt_M(k, 0)), t[k], e0);
-    d[0] -= e0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const int i = 2 * q + 1;
-        R ev = 0, od = 0;
-#pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            if (mrt_M(k, i) == 0) continue;
-            if (mrt_odd(k)) od = fma(R(mrt_M(k, i)), t[k], od);
-            else ev = fma(R(mrt_M(k, i)), t[k], ev);
-        }
-        d[i] -= ev + od;
-        d[i + 1] -= ev - od;
+        d[2 * q + 1] -= ev[q] + od[q];
+        d[2 * q + 2] -= ev[q] - od[q];
     }
     rho_out = rho;
 }

@@ -383,8 +383,9 @@ template <class L, class S, int MODEL>
 cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t s)
 {
     if constexpr (S::kHalf && MODEL != MODEL_ELBM) {
-        // masked MRT keeps the one-node kernel: two MRT nodes need ~96
-        // registers and solid neighbours split the pairs (20% slower measured)
+        // masked MRT keeps the one-node kernel: solid neighbours split the
+        // pairs and two MRT nodes need ~94 registers (sphere duct FP16S:
+        // 35.7 GLUPS with two nodes per thread, 39.0 with one)
         if (!aa && !(MODEL == MODEL_MRT && mask)) {
             if (p.nrows <= 0) return cudaSuccess;
             const bool d2 = (L::D == 2);
