@@ -153,6 +153,27 @@ LBM_API int lbm_set_stream(lbm_handle h, void* cuda_stream);
  * LBM_EINVAL.  Must precede lbm_init_equilibrium.  Default: all fluid. */
 LBM_API int lbm_set_geometry(lbm_handle h, const uint8_t* mask);
 
+/* Kernel for masked AB steps on the 3-D lattices (all models but ELBM):
+ *   LBM_MASKED_AUTO (0, default) chooses from the geometry,
+ *   LBM_MASKED_NODE (1) one node per thread, node word loaded with the
+ *       populations and the bounced populations reloaded after it,
+ *   LBM_MASKED_ZRUN (2) each thread walks 8 z layers and loads the next
+ *       node's word ahead, so every population load, bounced or streamed
+ *       (Sec. 2.3's half-way rule), is issued at once and solid nodes load
+ *       nothing.
+ * AUTO takes ZRUN when more than 40% of the 32-node row segments hold a fluid
+ * node next to a solid one.  Both give bitwise equal results; this is a
+ * performance choice only.  LBM_EINVAL for other values. */
+#define LBM_MASKED_AUTO 0
+#define LBM_MASKED_NODE 1
+#define LBM_MASKED_ZRUN 2
+LBM_API int lbm_set_masked_kernel(lbm_handle h, int mode);
+
+/* Fraction of the 32-node row segments (x-aligned) that hold a fluid node
+ * with a solid upstream neighbour, measured by lbm_set_geometry: the
+ * statistic LBM_MASKED_AUTO uses.  LBM_ESTATE before lbm_set_geometry. */
+LBM_API int lbm_get_nearwall_fraction(lbm_handle h, double* frac);
+
 /* Uniform body force density F (lattice units), Sec. 2.4.  LBGK and MRT use
  * Guo's term (Eq. guo_force; in moment space with (I - S/2) for MRT), ELBM
  * uses the EDM term (Eq. edm_force).  Default 0. */

@@ -17,7 +17,7 @@ namespace lbm {
 template <class L>
 __global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict__ words,
                         uint8_t* __restrict__ flags, int nx, int ny, int nz, int nxp,
-                        int max_code, int* __restrict__ bad)
+                        int max_code, int* __restrict__ bad, unsigned* __restrict__ nearwall_segs)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -31,39 +31,50 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict_
         else
             flags[out] = (solid ? FLAG_SOLID : 0) | (lk ? FLAG_NEAR_WALL : 0);
     };
-    if (x >= nx) {        // padding never updates
-        put(true, 0u, 0);
-        return;
-    }
     auto at = [&](int xx, int yy, int zz) {
         xx = (xx + nx) % nx;
         yy = (yy + ny) % ny;
         zz = (zz + nz) % nz;
         return dense[((size_t)zz * ny + yy) * nx + xx];
     };
-    const int code = at(x, y, z);
-    if (code > max_code) {
-        atomicOr(bad, 1);
+    bool near_wall = false;
+    if (x >= nx) {        // padding never updates
         put(true, 0u, 0);
-        return;
+    } else {
+        const int code = at(x, y, z);
+        if (code > max_code) {
+            atomicOr(bad, 1);
+            put(true, 0u, 0);
+        } else {
+            const bool solid = code == 1;
+            uint32_t lk = 0;
+            if (!solid)
+                for (int i = 1; i < L::Q; ++i)
+                    if (at(x - L::ex(i), y - L::ey(i), z - L::ez(i)) == 1) lk |= 1u << i;
+            put(solid, lk, code);
+            near_wall = lk != 0;
+        }
     }
-    const bool solid = code == 1;
-    uint32_t lk = 0;
-    if (!solid)
-        for (int i = 1; i < L::Q; ++i)
-            if (at(x - L::ex(i), y - L::ey(i), z - L::ez(i)) == 1) lk |= 1u << i;
-    put(solid, lk, code);
+    // count the 32-node row segments (one warp of the step kernel) that hold
+    // a fluid node with a solid neighbour; nxp is a multiple of 32 when this
+    // is requested, so every warp here is complete
+    if (nearwall_segs) {
+        const unsigned b = __ballot_sync(0xffffffffu, near_wall);
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(nearwall_segs, 1u);
+    }
 }
 
 cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
-                         int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s)
+                         int nx, int ny, int nz, int nxp, int max_code, int* bad,
+                         unsigned* nearwall_segs, cudaStream_t s)
 {
+    if (nearwall_segs && nxp % 32 != 0) return cudaErrorInvalidValue;
     dim3 block(128), grid((nxp + 127) / 128, ny, nz);
     switch (lattice) {
-    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
-    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
-    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
-    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad); break;
+    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
+    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
+    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
+    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -54,6 +54,11 @@ struct lbm_ctx {
     bool mlp_loaded = false, alpha_out = false, use_graph = false, round_nearest = false;
     bool aa = false;        // AA access pattern (one distribution array)
     bool elbm_diag = false; // ELBM entropy-condition residual accumulation
+    // masked AB steps on 3-D lattices: 0 choose from the geometry, 1 one node
+    // per thread, 2 z runs; zrun_pick is the choice for the current geometry
+    int masked_kernel = 0;
+    bool zrun_pick = false;
+    double nearwall_frac = 0.0;  // 32-node row segments with a near-wall fluid node
     long long t = 0, launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -64,6 +69,7 @@ enum : size_t {
     MISC_STATUS = 0,        // uint32 status bits
     MISC_PAIRS = 8,         // int pairs counter
     MISC_BAD = 16,          // int: mask value out of range
+    MISC_NEARWALL = 20,     // unsigned: near-wall row segments (geometry statistics)
     MISC_RED = 64,          // 5 doubles reduction result
     MISC_CTR_OUT = 128,     // 9 doubles: combined counters
     MISC_CTR = 256,         // kCtrReplicas x kCtrStride unsigned long long counter replicas
@@ -310,17 +316,44 @@ int lbm_set_geometry(lbm_handle h, const uint8_t* mask)
                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
        "copy mask");
     int* bad = at<int>(h, h->off_misc + MISC_BAD);
-    CK(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream), "clear mask check");
+    unsigned* nw = at<unsigned>(h, h->off_misc + MISC_NEARWALL);
+    CK(h, cudaMemsetAsync(bad, 0, 2 * sizeof(int), h->stream), "clear mask check");
     CK(h, launch_flags(h->lattice, stage, at<uint32_t>(h, h->off_nodes), nullptr, h->nx, h->ny,
-                       h->nz, h->nxp, 1 + kMaxBC, bad, h->stream),
+                       h->nz, h->nxp, 1 + kMaxBC, bad, nw, h->stream),
        "node-type map kernel");
     h->launches += 1;
-    int hbad = 0;
-    CK(h, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+    int hbad[2] = {0, 0};
+    CK(h, cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
        "read mask check");
     CK(h, cudaStreamSynchronize(h->stream), "synchronise");
-    if (hbad) return fail(h, LBM_EINVAL, "mask values are 0, 1 or 2..%d", 1 + kMaxBC);
+    if (hbad[0]) return fail(h, LBM_EINVAL, "mask values are 0, 1 or 2..%d", 1 + kMaxBC);
     h->has_mask = true;
+    const double segs = (double)((h->nx + 31) / 32) * h->ny * h->nz;
+    h->nearwall_frac = (unsigned)hbad[1] / segs;
+    // Near-wall nodes of the one-node kernel wait for their node word before
+    // reloading their bounced populations: a second memory round trip for
+    // every warp holding one.  The z-run kernel knows the word beforehand;
+    // it pays off where such warps are common (sphere duct: 62% of the
+    // segments, FP16S +24%) and loses ~2% where they are not (cavity: 27%).
+    h->zrun_pick = h->nearwall_frac > 0.4;
+    return LBM_OK;
+}
+
+int lbm_set_masked_kernel(lbm_handle h, int mode)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (mode < 0 || mode > 2) return fail(h, LBM_EINVAL, "masked kernel mode is 0, 1 or 2");
+    if (h->masked_kernel != mode) drop_graphs(h);
+    h->masked_kernel = mode;
+    return LBM_OK;
+}
+
+int lbm_get_nearwall_fraction(lbm_handle h, double* frac)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!frac) return fail(h, LBM_EINVAL, "frac is NULL");
+    if (!h->has_mask) return fail(h, LBM_ESTATE, "no geometry set");
+    *frac = h->nearwall_frac;
     return LBM_OK;
 }
 
@@ -532,6 +565,8 @@ static StepParams make_params(lbm_ctx* h)
     p.sq = h->sq;
     p.row0 = 0;
     p.nrows = h->D == 3 ? h->nz : h->ny;
+    p.zrun = (h->has_mask && h->D == 3 && !h->aa &&
+              (h->masked_kernel == 2 || (h->masked_kernel == 0 && h->zrun_pick))) ? 8 : 0;
     p.salt_off = 0;
     p.omega = 1.0 / h->tau;
     p.F[0] = h->F[0]; p.F[1] = h->F[1]; p.F[2] = h->F[2];

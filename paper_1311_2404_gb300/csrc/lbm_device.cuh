@@ -322,6 +322,7 @@ struct StepParams {
     int round_nearest;         // half-width stores: 1 round to nearest, 0 dither
     int aa_pushpull;           // AA pattern: 1 = pull/push step (even t), 0 = in-place step
     int row0, nrows;           // rows updated: z layers (3-D lattices) or y rows (D2Q9)
+    int zrun;                  // z layers per thread of the masked z-run kernel (set at launch)
     int salt_off;              // node-index offset of the dither salt (subdomains)
     double omega;              // 1/tau
     double F[3];               // body force

@@ -41,8 +41,11 @@ cudaError_t launch_step_elbm_part(int store, const StepParams& p, bool mask, boo
 // storage groups of the ELBM objects: {F64}, {F32, F32S}, {F16S, BF16S}
 constexpr unsigned kElbmStoreGroup[5] = {1u, 6u, 6u, 24u, 24u};
 
+// nearwall_segs (optional, needs nxp % 32 == 0): incremented once per
+// 32-node row segment holding a fluid node with a solid upstream neighbour
 cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
-                         int nx, int ny, int nz, int nxp, int max_code, int* bad, cudaStream_t s);
+                         int nx, int ny, int nz, int nxp, int max_code, int* bad,
+                         unsigned* nearwall_segs, cudaStream_t s);
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s);

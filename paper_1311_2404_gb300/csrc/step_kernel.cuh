@@ -240,6 +240,118 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_stream_collide_occ(const
 }
 
 // ---------------------------------------------------------------------------
+// Masked domains on 3-D lattices, AB pattern: each thread walks a run of
+// p.zrun consecutive z layers at one (x, y) and loads the node word of the
+// next layer while it updates the current one.  With its word already in a
+// register, a node picks the address of every population before loading it:
+// the upstream node x - e_i, or, for a link to a solid node, its own slot
+// opp(i) (half-way bounce-back, Sec. 2.3), which lies one plane away in the
+// same array.  So each node issues exactly q independent loads, with no
+// reload that waits for the word, and solid nodes load nothing.  (Loaded
+// together with the populations, the word forces a second round trip on
+// every warp holding a near-wall node: 62% of the warps of the 512x256x256
+// sphere duct.)
+// ---------------------------------------------------------------------------
+template <class L>
+__host__ __device__ constexpr bool opp_adjacent()
+{
+    for (int i = 1; i < L::Q; ++i)
+        if (L::opp(i) != i + 1 && L::opp(i) != i - 1) return false;
+    return true;
+}
+
+template <class L, class S, int MODEL>
+__device__ __forceinline__ void zrun_body(const StepParams& p)
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    static_assert(L::D == 3 && MODEL != MODEL_ELBM, "z runs: 3-D lattices, non-entropic");
+    static_assert(opp_adjacent<L>(), "slot opp(i) must be plane i + 1 or i - 1");
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const int zb = p.row0 + (int)blockIdx.z * p.zrun;
+    const int ze = min(zb + p.zrun, p.row0 + p.nrows);
+    if (zb >= ze) return;
+    const int plane = p.ny * p.nxp;
+    auto Ai = [&](int i) { return static_cast<const T*>(p.Ap[i]); };
+    auto Bi = [&](int i) { return static_cast<T*>(p.Bp[i]); };
+    const int cx[3] = {x == 0 ? p.nx - 1 : x - 1, x, x == p.nx - 1 ? 0 : x + 1};
+    const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nxp, y * p.nxp,
+                       (y == p.ny - 1 ? 0 : y + 1) * p.nxp};
+    int n = zb * plane + y * p.nxp + x;
+    uint32_t next = __ldg(p.nodes + n);
+    bool bad = false;
+    for (int z = zb; z < ze; ++z, n += plane) {
+        const uint32_t fl = next;
+        if (z + 1 < ze) next = __ldg(p.nodes + n + plane);
+        if (fl & NODE_SOLID) {
+            if (p.out) {
+                static_cast<R*>(p.rho)[n] = R(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) static_cast<R*>(p.u)[a * p.sq + n] = R(0);
+            }
+            continue;
+        }
+        const int zm = z == 0 ? p.nz - 1 : z - 1;
+        const int zp = z == p.nz - 1 ? 0 : z + 1;
+        const int rz[3] = {zm * plane, z * plane, zp * plane};
+        const int own_up = n + p.sq, own_dn = n - p.sq;   // slot opp(i) = i +- 1 of node n
+        R d[L::Q];
+        d[0] = S::load(Ai(0) + n, L::w(0));
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+            const int own = L::opp(i) > i ? own_up : own_dn;
+            d[i] = S::load(Ai(i) + (((fl >> i) & 1u) ? own : src), L::w(i));
+        }
+        if (fl >> NODE_BC_SHIFT)
+            bc_apply<L, R>(d, p.bc[(fl >> NODE_BC_SHIFT) - 1], sel<R>(p.F_f[0], p.F[0]),
+                           sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]));
+        R rho, v[3];
+        if (MODEL == MODEL_BGK) {
+            bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
+                              sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
+                              p.has_force != 0, rho, v);
+        } else if (MODEL == MODEL_MRT) {
+            if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+        } else {
+            les_collide<L, R, MODEL == MODEL_SMAG>(
+                d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
+                sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
+                sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho, v);
+        }
+        if constexpr (S::kHalf) {
+            if (!p.round_nearest) {
+                store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode,
+                                    [&](int i) { return Bi(i) + n; });
+            } else {
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[i], L::w(i));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[i], L::w(i));
+        }
+        if (p.out) {
+            static_cast<R*>(p.rho)[n] = rho;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) static_cast<R*>(p.u)[a * p.sq + n] = v[a];
+            bad |= !isfinite((float)rho);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bad |= !isfinite((float)v[a]);
+        }
+    }
+    if (bad) atomicOr(p.status, STATUS_NAN);
+}
+
+template <class L, class S, int MODEL>
+__global__ void __launch_bounds__(kStepThreads) k_stream_collide_zrun(const StepParams p)
+{
+    zrun_body<L, S, MODEL>(p);
+}
+
+// ---------------------------------------------------------------------------
 // Half-width storage, AB pattern: two x-adjacent nodes (x0 even, x0 + 1) per
 // thread.  The directions without an x component are read as one 32-bit pair,
 // each direction's plane address is formed once for both nodes, and a pair of
@@ -382,6 +494,17 @@ inline dim3 step_block(int nxp)
 template <class L, class S, int MODEL>
 cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t s)
 {
+    if constexpr (L::D == 3 && MODEL != MODEL_ELBM) {
+        // masked AB step in z runs (the host sets p.zrun from the geometry)
+        if (mask && !aa && p.zrun > 0) {
+            if (p.nrows <= 0) return cudaSuccess;
+            const dim3 block = step_block(p.nxp);
+            const dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y,
+                            (p.nrows + p.zrun - 1) / p.zrun);
+            k_stream_collide_zrun<L, S, MODEL><<<grid, block, 0, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (S::kHalf && MODEL != MODEL_ELBM) {
         // masked MRT keeps the one-node kernel: solid neighbours split the
         // pairs and two MRT nodes need ~94 registers (sphere duct FP16S:

@@ -37,6 +37,7 @@ LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
 LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIXED2 = range(4)
 LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
 LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
+LBM_MASKED_AUTO, LBM_MASKED_NODE, LBM_MASKED_ZRUN = 0, 1, 2
 LBM_TRANSFER_STAGED, LBM_TRANSFER_DIRECT = 0, 1
 LBM_BC_VELOCITY, LBM_BC_PRESSURE = 1, 2
 LBM_BC_EQUILIBRIUM, LBM_BC_ZOUHE, LBM_BC_REGULARIZED = 0, 1, 2
@@ -85,6 +86,8 @@ _PROTOS = {
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_set_access_pattern": (_i, [_vp, _i]),
     "lbm_set_geometry": (_i, [_vp, _vp]),
+    "lbm_set_masked_kernel": (_i, [_vp, _i]),
+    "lbm_get_nearwall_fraction": (_i, [_vp, ctypes.POINTER(_d)]),
     "lbm_set_force": (_i, [_vp, _d, _d, _d]),
     "lbm_set_mrt_rates": (_i, [_vp, _vp, _i]),
     "lbm_set_smagorinsky": (_i, [_vp, _d]),
@@ -221,6 +224,16 @@ def lbm_set_stream(h, stream):
 
 def lbm_set_geometry(h, mask):
     _check(_L.lbm_set_geometry(h, _ptr(mask)), h)
+
+
+def lbm_set_masked_kernel(h, mode):
+    _check(_L.lbm_set_masked_kernel(h, int(mode)), h)
+
+
+def lbm_get_nearwall_fraction(h):
+    out = _d(0.0)
+    _check(_L.lbm_get_nearwall_fraction(h, ctypes.byref(out)), h)
+    return float(out.value)
 
 
 def lbm_set_force(h, fx, fy, fz=0.0):
