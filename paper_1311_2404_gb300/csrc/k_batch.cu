@@ -991,7 +991,7 @@ int lbm_batch_set_geometry(lbm_batch b, int d, const uint8_t* mask)
     int* bad = reinterpret_cast<int*>(b->base + b->off_bar + 32);
     BCK(b, cudaMemsetAsync(bad, 0, sizeof(int), b->stream), "clear mask check");
     BCK(b, launch_flags(0, stage, nullptr, reinterpret_cast<uint8_t*>(b->base + D.offF), D.nx,
-                        D.ny, 1, D.nxp, 1, bad, nullptr, b->stream),
+                        D.ny, 1, D.nxp, 1, bad, nullptr, 0, b->stream),
         "node-type map kernel");
     b->launches += 1;
     int hbad = 0;

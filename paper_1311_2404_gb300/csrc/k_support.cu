@@ -17,7 +17,8 @@ namespace lbm {
 template <class L>
 __global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict__ words,
                         uint8_t* __restrict__ flags, int nx, int ny, int nz, int nxp,
-                        int max_code, int* __restrict__ bad, unsigned* __restrict__ nearwall_segs)
+                        int max_code, int* __restrict__ bad, unsigned* __restrict__ nearwall_segs,
+                        int sector)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -51,8 +52,14 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict_
             if (!solid)
                 for (int i = 1; i < L::Q; ++i)
                     if (at(x - L::ex(i), y - L::ey(i), z - L::ez(i)) == 1) lk |= 1u << i;
+            if (solid && words && sector > 1) {
+                // rest-state fill of a solid node whose sector holds a fluid node
+                const int x0 = x & ~(sector - 1), x1 = min(x0 + sector, nx);
+                for (int xx = x0; xx < x1; ++xx)
+                    if (at(xx, y, z) != 1) { lk = NODE_FILL; break; }
+            }
             put(solid, lk, code);
-            near_wall = lk != 0;
+            near_wall = !solid && lk != 0;
         }
     }
     // count the 32-node row segments (one warp of the step kernel) that hold
@@ -66,15 +73,16 @@ __global__ void k_flags(const uint8_t* __restrict__ dense, uint32_t* __restrict_
 
 cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
                          int nx, int ny, int nz, int nxp, int max_code, int* bad,
-                         unsigned* nearwall_segs, cudaStream_t s)
+                         unsigned* nearwall_segs, int sector, cudaStream_t s)
 {
+    if (sector & (sector - 1)) return cudaErrorInvalidValue;
     if (nearwall_segs && nxp % 32 != 0) return cudaErrorInvalidValue;
     dim3 block(128), grid((nxp + 127) / 128, ny, nz);
     switch (lattice) {
-    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
-    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
-    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
-    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs); break;
+    case 0: k_flags<D2Q9><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs, sector); break;
+    case 1: k_flags<D3Q19><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs, sector); break;
+    case 2: k_flags<D3Q15><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs, sector); break;
+    case 3: k_flags<D3Q27><<<grid, block, 0, s>>>(dense, words, flags, nx, ny, nz, nxp, max_code, bad, nearwall_segs, sector); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -319,7 +319,8 @@ int lbm_set_geometry(lbm_handle h, const uint8_t* mask)
     unsigned* nw = at<unsigned>(h, h->off_misc + MISC_NEARWALL);
     CK(h, cudaMemsetAsync(bad, 0, 2 * sizeof(int), h->stream), "clear mask check");
     CK(h, launch_flags(h->lattice, stage, at<uint32_t>(h, h->off_nodes), nullptr, h->nx, h->ny,
-                       h->nz, h->nxp, 1 + kMaxBC, bad, nw, h->stream),
+                       h->nz, h->nxp, 1 + kMaxBC, bad, nw,
+                       h->aa ? 0 : (int)(32 / h->esize), h->stream),
        "node-type map kernel");
     h->launches += 1;
     int hbad[2] = {0, 0};

@@ -276,6 +276,14 @@ enum { FLAG_SOLID = 1, FLAG_NEAR_WALL = 2 };
 // the population loads): bits 1..26 link mask (bit i: the upstream node
 // x - e_i is solid), bit 27 solid, bits 28..31 boundary condition id + 1
 constexpr uint32_t NODE_LINKS = 0x07fffffeu, NODE_SOLID = 1u << 27;
+// On a solid node (whose link bits are otherwise unused), bit 1 marks a node
+// that shares its 32-byte sector of every direction plane with a fluid node
+// (AB pattern only): the AB kernels write the rest state (deviation 0) into
+// its slots so that the sector is written whole.  A partly written sector
+// costs the memory a read of the whole sector first (read-modify-write):
+// 0.38 GB per step of the 512x256x256 sphere duct in FP32.  Nothing reads
+// those slots.
+constexpr uint32_t NODE_FILL = 1u << 1;
 constexpr int NODE_BC_SHIFT = 28;
 constexpr int kMaxBC = 15;
 // ELBM counter replicas: slots 0..5 evals, skipped, clamped, at cap, guarded,

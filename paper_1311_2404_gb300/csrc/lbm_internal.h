@@ -42,10 +42,13 @@ cudaError_t launch_step_elbm_part(int store, const StepParams& p, bool mask, boo
 constexpr unsigned kElbmStoreGroup[5] = {1u, 6u, 6u, 24u, 24u};
 
 // nearwall_segs (optional, needs nxp % 32 == 0): incremented once per
-// 32-node row segment holding a fluid node with a solid upstream neighbour
+// 32-node row segment holding a fluid node with a solid upstream neighbour.
+// sector (a power of two, 0 for none): nodes per 32-byte sector of a direction
+// plane; solid nodes sharing an x-aligned sector with a fluid node get
+// NODE_FILL.
 cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uint8_t* flags,
                          int nx, int ny, int nz, int nxp, int max_code, int* bad,
-                         unsigned* nearwall_segs, cudaStream_t s);
+                         unsigned* nearwall_segs, int sector, cudaStream_t s);
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s);

@@ -88,6 +88,22 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
             for (int a = 0; a < L::D; ++a) static_cast<R*>(p.u)[a * p.sq + n] = R(0);
             if (ELBM && p.alpha_out) p.alpha_out[n] = 0.0;
         }
+        if (MASK && !AA && (fl & NODE_FILL)) {   // rest state: whole-sector writes
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) d[i] = R(0);
+            if constexpr (S::kHalf) {
+                if (!p.round_nearest) {
+                    store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode,
+                                        [&](int i) { return Bi(i) + n; });
+                } else {
+#pragma unroll
+                    for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[i], L::w(i));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[i], L::w(i));
+            }
+        }
         active = false;
     }
     int evals = 0, astat = -1;
@@ -285,7 +301,8 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
     for (int z = zb; z < ze; ++z, n += plane) {
         const uint32_t fl = next;
         if (z + 1 < ze) next = __ldg(p.nodes + n + plane);
-        if (fl & NODE_SOLID) {
+        const bool solid = (fl & NODE_SOLID) != 0;
+        if (solid && !(fl & NODE_FILL)) {
             if (p.out) {
                 static_cast<R*>(p.rho)[n] = R(0);
 #pragma unroll
@@ -293,33 +310,41 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
             }
             continue;
         }
-        const int zm = z == 0 ? p.nz - 1 : z - 1;
-        const int zp = z == p.nz - 1 ? 0 : z + 1;
-        const int rz[3] = {zm * plane, z * plane, zp * plane};
-        const int own_up = n + p.sq, own_dn = n - p.sq;   // slot opp(i) = i +- 1 of node n
+        // fluid nodes update; solid nodes that share a sector with one take
+        // the same store instructions with the rest state (NODE_FILL)
         R d[L::Q];
-        d[0] = S::load(Ai(0) + n, L::w(0));
+        R rho = R(0), v[3] = {R(0), R(0), R(0)};
+        if (!solid) {
+            const int zm = z == 0 ? p.nz - 1 : z - 1;
+            const int zp = z == p.nz - 1 ? 0 : z + 1;
+            const int rz[3] = {zm * plane, z * plane, zp * plane};
+            const int own_up = n + p.sq, own_dn = n - p.sq;   // slot opp(i) = i +- 1 of node n
+            d[0] = S::load(Ai(0) + n, L::w(0));
 #pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-            const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
-            const int own = L::opp(i) > i ? own_up : own_dn;
-            d[i] = S::load(Ai(i) + (((fl >> i) & 1u) ? own : src), L::w(i));
-        }
-        if (fl >> NODE_BC_SHIFT)
-            bc_apply<L, R>(d, p.bc[(fl >> NODE_BC_SHIFT) - 1], sel<R>(p.F_f[0], p.F[0]),
-                           sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]));
-        R rho, v[3];
-        if (MODEL == MODEL_BGK) {
-            bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
-                              sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
-                              p.has_force != 0, rho, v);
-        } else if (MODEL == MODEL_MRT) {
-            if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+            for (int i = 1; i < L::Q; ++i) {
+                const int src = rz[1 - L::ez(i)] + ry[1 - L::ey(i)] + cx[1 - L::ex(i)];
+                const int own = L::opp(i) > i ? own_up : own_dn;
+                d[i] = S::load(Ai(i) + (((fl >> i) & 1u) ? own : src), L::w(i));
+            }
+            if (fl >> NODE_BC_SHIFT)
+                bc_apply<L, R>(d, p.bc[(fl >> NODE_BC_SHIFT) - 1], sel<R>(p.F_f[0], p.F[0]),
+                               sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]));
+            if (MODEL == MODEL_BGK) {
+                bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
+                                  sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
+                                  p.has_force != 0, rho, v);
+            } else if (MODEL == MODEL_MRT) {
+                if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+            } else {
+                les_collide<L, R, MODEL == MODEL_SMAG>(
+                    d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
+                    sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
+                    sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho,
+                    v);
+            }
         } else {
-            les_collide<L, R, MODEL == MODEL_SMAG>(
-                d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
-                sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
-                sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho, v);
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) d[i] = R(0);
         }
         if constexpr (S::kHalf) {
             if (!p.round_nearest) {
@@ -358,8 +383,9 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_zrun(const Step
 // active nodes is narrowed by one stochastic-rounding conversion and written
 // with one 32-bit store.  The rounding of every value depends only on the
 // value and its (node, direction) salt, so the results are bitwise those of
-// the one-node kernel.  A pair with a solid or padding node writes only the
-// active node, leaving solid slots untouched as the one-node kernel does.
+// the one-node kernel.  A solid node is written only with the rest state and
+// only when its sector holds a fluid node (NODE_FILL), as in the one-node
+// kernel; padding is never written.
 // ---------------------------------------------------------------------------
 template <class L, class S, int MODEL, bool MASK>
 __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepParams p)
@@ -406,10 +432,20 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
     }
     R rho[2], v[2][3];
     bool bad = false;
+    // wr: the node's slots are written (fluid, or a solid node that shares a
+    // sector with a fluid one and takes the rest state, NODE_FILL)
+    bool wr[2] = {act[0], act[1]};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int n = n0 + k;
-        if (MASK && (fl[k] & NODE_SOLID)) act[k] = false;
+        if (MASK && (fl[k] & NODE_SOLID)) {
+            act[k] = false;
+            wr[k] = (fl[k] & NODE_FILL) != 0;
+            if (wr[k]) {
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) d[k][i] = R(0);
+            }
+        }
         if (!act[k]) continue;
         if (MASK && (fl[k] & NODE_LINKS)) {
 #pragma unroll
@@ -431,7 +467,7 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
         }
     }
     const unsigned s0 = (unsigned)(n0 + p.salt_off) * kSaltNode, s1 = s0 + kSaltNode;
-    if (act[0] && act[1]) {
+    if (wr[0] && wr[1]) {
         if (!p.round_nearest) {
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
@@ -449,7 +485,7 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
     } else {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            if (!act[k]) continue;
+            if (!wr[k]) continue;
             const int n = n0 + k;
             if (!p.round_nearest)
                 store_node_sr<L, S>(d[k], k ? s1 : s0, [&](int i) { return Bi(i) + n; });

@@ -147,3 +147,38 @@ def test_nearwall_statistic_and_choice():
     with pytest.raises(lbm.LBMError):
         lbm.lbm_set_masked_kernel(sim.h, 3)
     sim.close()
+
+
+@pytest.mark.parametrize("mode", [lbm.LBM_MASKED_NODE, lbm.LBM_MASKED_ZRUN])
+@pytest.mark.parametrize("dtype,esize,ntype", [(lbm.LBM_F32S, 4, np.float32),
+                                               (lbm.LBM_F16S, 2, np.float16)])
+def test_solid_slots_rest_fill(mode, dtype, esize, ntype):
+    """A solid node whose 32-byte sector holds a fluid node takes the rest
+    state (shifted value 0) in every direction after a step, so sectors are
+    written whole; other solid slots are never written."""
+    nz, ny, nx = shape = (10, 12, 40)
+    mask = _mask(shape, solid=0.3, seed=12)
+    rho, u = wl.random_state(nx, ny, nz, 3, seed=2, u_amp=0.04, rho_amp=0.01)
+    sim = lbm.Simulation(nx, ny, nz, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.7, dtype)
+    lbm.lbm_set_masked_kernel(sim.h, mode)
+    sim.set_geometry(mask)
+    sim.init(rho, u)
+    s0, _ = sim.state()
+    sim.step(2)                                # the state is back in the first array
+    s2, _ = sim.state()
+    sim.close()
+    nxp = -(-nx // 32) * 32
+    sq = -(-(nxp * ny * nz) // 128) * 128
+    a0 = s0.view(ntype).reshape(19, sq)[:, :nz * ny * nxp].reshape(19, nz, ny, nxp)[..., :nx]
+    a2 = s2.view(ntype).reshape(19, sq)[:, :nz * ny * nxp].reshape(19, nz, ny, nxp)[..., :nx]
+    per = 32 // esize
+    solid = mask == 1
+    grp = np.zeros((nz, ny, nxp), bool)
+    grp[..., :nx] = ~solid
+    mixed = np.repeat(grp.reshape(nz, ny, nxp // per, per).any(-1), per, axis=-1)[..., :nx]
+    fill = solid & mixed
+    keep = solid & ~mixed
+    assert fill.sum() > 0 and keep.sum() > 0
+    assert np.all(a2[:, fill] == 0)
+    assert np.array_equal(np.ascontiguousarray(a2[:, keep]).view(np.uint8),
+                          np.ascontiguousarray(a0[:, keep]).view(np.uint8))
