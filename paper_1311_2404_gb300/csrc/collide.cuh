@@ -111,10 +111,15 @@ __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R
     const R m15 = R(-1.5) * usq;
     const R cf = fma(R(-0.5), om, R(1));
     const R vF = fma(v[0], F0, fma(v[1], F1, v[2] * F2));
+    // f' = (1 - om) f + om f_eq, with om folded into the equilibrium's
+    // per-class factors (om w_i rho, om w_i drho, om b_i rho): two operations
+    // fewer per pair than relaxing f_eq - f.  b_i keeps sum b_i e_i e_i = I
+    // exact, so the equilibrium momentum om rho v is not rescaled coherently.
+    const R c1 = R(1) - om;
+    const R orho = om * rho, odrho = om * drho;
     {
         const R w0 = (R)L::w(0);
-        const R feq = fma(w0 * rho, m15, w0 * drho);
-        R d0 = fma(om, feq - d[0], d[0]);
+        R d0 = fma(c1, d[0], fma(w0 * orho, m15, w0 * odrho));
         if (has_force) d0 = fma(cf, R(-3) * w0 * vF, d0);
         d[0] = d0;
     }
@@ -125,10 +130,10 @@ __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R
         const R bi = first_order_coef<L, R>(i);
         const R eu = edot<L, R>(i, v[0], v[1], v[2]);
         const R t = fma(R(4.5) * eu, eu, m15);
-        const R even = fma(wi * rho, t, wi * drho);
-        const R odd = (bi * rho) * eu;
-        R dp = fma(om, (even + odd) - d[i], d[i]);
-        R dm = fma(om, (even - odd) - d[i + 1], d[i + 1]);
+        const R even = fma(wi * orho, t, wi * odrho);
+        const R odd = (bi * orho) * eu;
+        R dp = fma(c1, d[i], even + odd);
+        R dm = fma(c1, d[i + 1], even - odd);
         if (has_force) {
             const R eF = edot<L, R>(i, F0, F1, F2);
             const R ge = cf * wi * fma(R(9) * eu, eF, R(-3) * vF);   // even part of the Guo term

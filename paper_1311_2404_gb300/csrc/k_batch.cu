@@ -587,8 +587,7 @@ __device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev
 #pragma unroll
                     for (int i = 0; i < 9; ++i)
                         *reinterpret_cast<unsigned*>(B + (i * sq + n)) =
-                            S::encode_pair(db[i], da[i], s1 + (unsigned)i * kSaltDir,
-                                           s0 + (unsigned)i * kSaltDir);
+                            S::encode_pair(db[i], da[i], s1, s0, i, i);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {

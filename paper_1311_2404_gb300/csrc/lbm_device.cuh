@@ -144,26 +144,33 @@ static_assert(lattice_ok<D3Q27>(6, 12, 8), "D3Q27 table");
 // (cvt.rs, sm_100 family): it rounds up with probability equal to the
 // fraction the narrowing drops, subnormals and values below the smallest
 // subnormal included, and passes Inf and NaN through.  Its random bits come
-// from a multiplicative hash of each value's own 32 bits salted with node and
-// direction, so no counter is needed and CUDA-graph replay, the batched
-// kernel and subdomain runs reproduce results exactly.  Two directions of a
-// node share one conversion; each element takes 13 (FP16) or 16 (BF16) high
-// bits of its own hash (the instruction reads bits 16.. of the word for the
-// first element, bits 0.. for the second).
-__device__ __forceinline__ unsigned dither_hash(unsigned bits, unsigned salt)
+// from a multiplicative hash of each value's own 32 bits with an odd
+// multiplier per direction, salted with the node index, so no counter is
+// needed and CUDA-graph replay, the batched kernel and subdomain runs
+// reproduce results exactly.  With the direction a compile-time constant the
+// hash is one integer multiply-add per value.  Two values share one
+// conversion; each element takes 13 (FP16) or 16 (BF16) high bits of its own
+// hash (the instruction reads bits 16.. of the word for the first element,
+// bits 0.. for the second).
+__host__ __device__ constexpr unsigned dither_mul(int dir)
 {
-    return bits * 0x9E3779B1u + salt;
+    return 0x9E3779B1u + (unsigned)dir * 0x3C6EF372u;   // odd for every dir
 }
-constexpr unsigned kSaltNode = 0x85EBCA77u, kSaltDir = 0xC2B2AE3Du;
+__device__ __forceinline__ unsigned dither_hash(unsigned bits, unsigned salt, int dir)
+{
+    return bits * dither_mul(dir) + salt;
+}
+constexpr unsigned kSaltNode = 0x85EBCA77u;
 
 // random word for a pair: high 16 bits of a's hash in the high half, of b's
 // hash in the low half, shifted right by `sh` so that a field of 16 - sh bits
 // starts at each half's bit 0 with the hash's top bits
 template <int sh>
-__device__ __forceinline__ unsigned pair_rbits(float a, float b, unsigned sa, unsigned sb)
+__device__ __forceinline__ unsigned pair_rbits(float a, float b, unsigned sa, unsigned sb, int da,
+                                               int db)
 {
-    const unsigned ha = dither_hash(__float_as_uint(a), sa);
-    const unsigned hb = dither_hash(__float_as_uint(b), sb);
+    const unsigned ha = dither_hash(__float_as_uint(a), sa, da);
+    const unsigned hb = dither_hash(__float_as_uint(b), sb, db);
     return __byte_perm(hb, ha, 0x7632) >> sh;
 }
 
@@ -198,12 +205,13 @@ struct StoreF16S {
     __device__ static R load(const T* p, double) { return __half2float(__ldg(p)); }
     __device__ static void store(T* p, R d, double) { *p = __float2half_rn(d); }
     __device__ static T encode(R d, double) { return __float2half_rn(d); }
-    // a in the high half, b in the low half, stochastic rounding
-    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb)
+    // a (node salt sa, direction da) in the high half, b in the low half,
+    // stochastic rounding
+    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb, int da, int db)
     {
         unsigned out;
         asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
-            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<3>(a, b, sa, sb)));
+            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<3>(a, b, sa, sb, da, db)));
         return out;
     }
     __device__ static T hi(unsigned pk) { return __ushort_as_half((unsigned short)(pk >> 16)); }
@@ -223,11 +231,11 @@ struct StoreBF16S {
     __device__ static R load(const T* p, double) { return __bfloat162float(__ldg(p)); }
     __device__ static void store(T* p, R d, double) { *p = __float2bfloat16_rn(d); }
     __device__ static T encode(R d, double) { return __float2bfloat16_rn(d); }
-    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb)
+    __device__ static unsigned encode_pair(R a, R b, unsigned sa, unsigned sb, int da, int db)
     {
         unsigned out;
         asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;"
-            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<0>(a, b, sa, sb)));
+            : "=r"(out) : "f"(a), "f"(b), "r"(pair_rbits<0>(a, b, sa, sb, da, db)));
         return out;
     }
     __device__ static T hi(unsigned pk)
@@ -254,12 +262,11 @@ struct StoreBF16S {
 template <class L, class S, class F>
 __device__ __forceinline__ void store_node_sr(const float (&d)[L::Q], unsigned salt, F dst)
 {
-    *dst(0) = S::hi(S::encode_pair(d[0], d[0], salt, salt ^ 0x5bd1e995u));
+    *dst(0) = S::hi(S::encode_pair(d[0], d[0], salt, salt, 0, 0));
 #pragma unroll
     for (int k = 0; k < (L::Q - 1) / 2; ++k) {
         const int i = 2 * k + 1, j = i + 1;
-        const unsigned pk = S::encode_pair(d[i], d[j], salt + (unsigned)i * kSaltDir,
-                                           salt + (unsigned)j * kSaltDir);
+        const unsigned pk = S::encode_pair(d[i], d[j], salt, salt, i, j);
         *dst(i) = S::hi(pk);
         *dst(j) = S::lo(pk);
     }

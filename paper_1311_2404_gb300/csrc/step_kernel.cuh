@@ -471,8 +471,7 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
         if (!p.round_nearest) {
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const unsigned pk = S::encode_pair(d[1][i], d[0][i], s1 + (unsigned)i * kSaltDir,
-                                                   s0 + (unsigned)i * kSaltDir);
+                const unsigned pk = S::encode_pair(d[1][i], d[0][i], s1, s0, i, i);
                 *reinterpret_cast<unsigned*>(Bi(i) + n0) = pk;
             }
         } else {
