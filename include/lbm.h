@@ -360,14 +360,17 @@ LBM_API int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, cons
 LBM_API int lbm_batch_autotune(lbm_batch b);
 /* Current launch configuration (5 ints): threads per CTA, CTAs, tile width,
  * tile rows, and the kernel variant: 1, 2 or 4 = the register kernel with
- * that many rows per thread and pass; 0 = the staged kernel, which copies
- * each tile's inputs into shared memory with bulk asynchronous copies,
- * double-buffered, while the previous tile is updated. */
+ * that many rows per thread and pass; -1 or -2 = the same with two
+ * x-adjacent nodes per thread (pair loads and pair stores; tile width a
+ * multiple of 64); 0 = the staged kernel, which copies each tile's inputs
+ * into shared memory with bulk asynchronous copies into a ring of stages
+ * while earlier tiles are updated.  Every variant gives the same bits. */
 LBM_API int lbm_batch_get_config(lbm_batch b, int* out5);
 /* Set the launch configuration (5 ints, as lbm_batch_get_config returns
  * them), e.g. one found by an earlier lbm_batch_autotune.  Threads per CTA
- * at most 512 and a multiple of the tile width, itself a multiple of 32;
- * variant 0, 1, 2 or 4 (the staged kernel's two stages within 200 KB of
+ * at most 512 and a multiple of the tile width, itself a multiple of 32
+ * (64 for variants -1, -2); variant 0, 1, 2, 4, -1 or -2 (the
+ * staged kernel's stages within 200 KB of
  * shared memory); CTAs between 1 and the number that can be co-resident (the
  * launch is cooperative).  LBM_EINVAL otherwise, with the configuration
  * unchanged. */

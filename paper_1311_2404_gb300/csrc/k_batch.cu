@@ -251,6 +251,193 @@ __global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
     }
 }
 
+// ---- register kernel, two x-adjacent nodes per thread ----------------------
+//
+// Half-width storage makes the one-node kernel instruction-bound (about 317
+// instructions per D2Q9 node).  Here a thread updates columns x and x + 1
+// (x even; tiles are a multiple of 64 wide): the three directions without an
+// x component are one pair load, the two flag bytes one 16-bit load, and an
+// active pair is written with one store per direction (one stochastic-rounding
+// conversion for both values), with the per-value hashes of the one-node
+// kernel, so the fields are bitwise the same.
+template <class S>
+__device__ __forceinline__ void batch_load_pair(const typename S::T* __restrict__ row, float& a,
+                                                float& b)
+{
+    if constexpr (S::kHalf) {
+        const __half2 h = *reinterpret_cast<const __half2*>(row);
+        a = __low2float(h);
+        b = __high2float(h);
+    } else {
+        const float2 f = *reinterpret_cast<const float2*>(row);
+        a = f.x;
+        b = f.y;
+    }
+}
+
+template <class S, int NPT>
+__device__ __forceinline__ void batch2_body(const BatchParams& bp)
+{
+    using T = typename S::T;
+    using L = D2Q9;
+    const int G = gridDim.x;
+    const int t0 = (int)((long long)bp.ntiles * blockIdx.x / G);
+    const int t1 = (int)((long long)bp.ntiles * (blockIdx.x + 1) / G);
+    const int tw = 2 * blockDim.x, by = blockDim.y;
+    int4 first = make_int4(0, 0, 0, 0);
+    if (t0 < t1) first = bp.tiles[t0];
+    int cur = bp.cur;
+    for (int step = 0; step < bp.nsteps; ++step) {
+        const bool out = (step == bp.nsteps - 1);
+        int dom = first.x, x0 = first.y, y0 = first.z;
+        DomDev D{};
+        if (t0 < t1) D = bp.dom[dom];
+        for (int t = t0; t < t1; ++t) {
+            const T* __restrict__ A =
+                reinterpret_cast<const T*>(bp.base + (cur == 0 ? D.offA : D.offB));
+            T* __restrict__ B = reinterpret_cast<T*>(bp.base + (cur == 0 ? D.offB : D.offA));
+            const uint8_t* __restrict__ flags = reinterpret_cast<const uint8_t*>(bp.base + D.offF);
+            float* __restrict__ o = reinterpret_cast<float*>(bp.base + D.offO);
+            const int x = x0 + 2 * (int)threadIdx.x;
+            const int yend = min(y0 + bp.th, D.ny);
+            if (x < D.nx) {
+                const int sq = (int)D.sq;
+                const bool has1 = x + 1 < D.nx;
+                // source columns of node k for e_x = +1, 0, -1 (periodic); a
+                // padding node x + 1 reads inside the row and is not written
+                const int cx[2][3] = {{x == 0 ? D.nx - 1 : x - 1, x, x + 1 >= D.nx ? 0 : x + 1},
+                                      {x, x + 1, x + 2 >= D.nx ? x + 2 - D.nx : x + 2}};
+                for (int ya = y0 + threadIdx.y; ya < yend; ya += NPT * by) {
+                    float d[NPT][2][9];
+                    unsigned fl[NPT];
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int y = ya + k * by;
+                        fl[k] = 0x8080u;                     // no node (beyond the tile)
+                        if (k == 0 || y < yend) {
+                            const int ry[3] = {(y == 0 ? D.ny - 1 : y - 1) * D.nxp, y * D.nxp,
+                                               (y == D.ny - 1 ? 0 : y + 1) * D.nxp};
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) {
+                                const int rs = i * sq + ry[1 - L::ey(i)];
+                                if (L::ex(i) == 0) {
+                                    batch_load_pair<S>(A + (rs + x), d[k][0][i], d[k][1][i]);
+                                } else {
+                                    d[k][0][i] = bload<S>(A + (rs + cx[0][1 - L::ex(i)]));
+                                    d[k][1][i] = bload<S>(A + (rs + cx[1][1 - L::ex(i)]));
+                                }
+                            }
+                            fl[k] = *reinterpret_cast<const unsigned short*>(flags + ry[1] + x);
+                            if (!has1) fl[k] |= 0x8000u;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int y = ya + k * by;
+                        if (fl[k] & 0x80u) continue;
+                        const int n = y * D.nxp + x;
+                        bool act[2];
+                        float rho[2], v[2][3];
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const unsigned f = (fl[k] >> (8 * c)) & 0xffu;
+                            act[c] = !(f & (0x80u | FLAG_SOLID));
+                            if (!(f & 0x80u) && (f & FLAG_SOLID) && out) {
+                                o[n + c] = 0.f;
+                                o[sq + n + c] = 0.f;
+                                o[2 * sq + n + c] = 0.f;
+                            }
+                            if (!act[c]) continue;
+                            if (f & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, x + c, y, d[k][c]);
+                            bgk_collide<L, float>(d[k][c], D.omega, D.gx, D.gy, 0.f,
+                                                  D.has_force != 0, rho[c], v[c]);
+                        }
+                        if (act[0] && act[1]) {
+                            if constexpr (S::kHalf) {
+                                if (!bp.round_nearest) {
+                                    const unsigned s0 = (unsigned)n * kSaltNode, s1 = s0 + kSaltNode;
+#pragma unroll
+                                    for (int i = 0; i < 9; ++i)
+                                        *reinterpret_cast<unsigned*>(B + (i * sq + n)) =
+                                            S::encode_pair(d[k][1][i], d[k][0][i], s1, s0, i, i);
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < 9; ++i) {
+                                        S::store(B + (i * sq + n), d[k][0][i], L::w(i));
+                                        S::store(B + (i * sq + n + 1), d[k][1][i], L::w(i));
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 9; ++i)
+                                    *reinterpret_cast<float2*>(B + (i * sq + n)) =
+                                        make_float2(d[k][0][i], d[k][1][i]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                if (!act[c]) continue;
+                                const int m = n + c;
+                                if constexpr (S::kHalf) {
+                                    if (!bp.round_nearest) {
+                                        store_node_sr<L, S>(d[k][c], (unsigned)m * kSaltNode,
+                                                            [&](int i) { return B + (i * sq + m); });
+                                    } else {
+#pragma unroll
+                                        for (int i = 0; i < 9; ++i)
+                                            S::store(B + (i * sq + m), d[k][c][i], L::w(i));
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < 9; ++i)
+                                        S::store(B + (i * sq + m), d[k][c][i], L::w(i));
+                                }
+                            }
+                        }
+                        if (out) {
+                            bool bad = false;
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                if (!act[c]) continue;
+                                o[n + c] = rho[c];
+                                o[sq + n + c] = v[c][0];
+                                o[2 * sq + n + c] = v[c][1];
+                                bad |= !isfinite(rho[c]) || !isfinite(v[c][0]) || !isfinite(v[c][1]);
+                            }
+                            if (bad) atomicOr(bp.status, STATUS_NAN);
+                        }
+                    }
+                }
+            }
+            // the next tile in (domain, y0, x0) order
+            x0 += tw;
+            if (x0 >= D.nx) {
+                x0 = 0;
+                y0 += bp.th;
+                if (y0 >= D.ny) {
+                    y0 = 0;
+                    ++dom;
+                    if (t + 1 < t1) D = bp.dom[dom];
+                }
+            }
+        }
+        cur ^= 1;
+        if (step + 1 < bp.nsteps) {
+            const bool skip = bp.withhold == 1 && blockIdx.x == 0 && step == 0;
+            if (!grid_barrier(bp, skip)) return;
+        }
+    }
+}
+
+// Register budgets per instance (launches of up to 512 threads would allow
+// 128; the compiler then spends them and occupancy drops): the largest
+// budget without spills, measured with -Xptxas -v.
+template <class S, int NPT, int MAXR>
+__global__ void __maxnreg__(MAXR) k_batch2(const BatchParams bp)
+{
+    batch2_body<S, NPT>(bp);
+}
+
 // ---- staged variant: bulk copies into shared memory ------------------------
 //
 // The register kernel's bytes in flight are bounded by its registers (one
@@ -713,6 +900,8 @@ const void* staged_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch_
 
 template <class S, int NPT>
 const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch<S, NPT>); }
+template <class S, int NPT, int MAXR>
+const void* batch2_kernel_ptr() { return reinterpret_cast<const void*>(&k_batch2<S, NPT, MAXR>); }
 
 }  // namespace
 
@@ -776,8 +965,17 @@ static void drop_graphs(lbm_batch b)
     b->graphs.clear();
 }
 
+// npt: 0 the staged kernel; 1, 2, 4 the register kernel with that many rows
+// per thread and pass; -1, -2 the same with two x-adjacent nodes per thread
 static const void* kernel_for(int dtype, int npt)
 {
+    if (npt < 0) {
+        if (dtype == LBM_F16S)
+            return npt == -2 ? batch2_kernel_ptr<StoreF16S, 2, 96>()
+                             : batch2_kernel_ptr<StoreF16S, 1, 80>();
+        return npt == -2 ? batch2_kernel_ptr<StoreF32S, 2, 128>()
+                         : batch2_kernel_ptr<StoreF32S, 1, 96>();
+    }
     if (dtype == LBM_F16S)
         return npt == 0   ? staged_kernel_ptr<StoreF16S>()
              : npt == 4 ? batch_kernel_ptr<StoreF16S, 4>()
@@ -858,7 +1056,9 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     std::memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(b->ctas);
     // the staged kernel adds its producer warp to the consumer threads
-    cfg.blockDim = b->npt == 0 ? dim3(b->threads + 32) : dim3(b->tw, b->threads / b->tw);
+    cfg.blockDim = b->npt == 0  ? dim3(b->threads + 32)
+                 : b->npt < 0 ? dim3(b->tw / 2, b->threads / (b->tw / 2))
+                              : dim3(b->tw, b->threads / b->tw);
     cfg.dynamicSmemBytes = launch_smem(b, b->tw, b->th, b->npt);
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
@@ -1127,13 +1327,16 @@ int lbm_batch_autotune(lbm_batch b)
     int bt = b->threads, bc = b->ctas, bw = b->tw, bh = b->th, bn = b->npt;
     const int steps = 4;
     // npt 0: the staged kernel; 1, 2, 4: the register kernel's rows per pass
-    for (int npt : {0, 1, 2, 4})
+    for (int npt : {0, 1, 2, 4, -1, -2})
         for (int threads : {128, 256, 512})
             for (int tw : {64, 128, 256}) {
                 if (tw > threads) continue;
                 for (int th : {2, 4, 8, 16, 32, 64}) {
-                    // every consumer thread gets a row (staged: two columns per thread)
-                    if (th < (npt == 0 ? 2 : npt) * (threads / tw)) continue;
+                    // every consumer thread gets a row (staged and paired: two
+                    // columns per thread)
+                    if (th < (npt == 0 ? 2 * (threads / tw)
+                              : npt < 0 ? -npt * (threads / (tw / 2)) : npt * (threads / tw)))
+                        continue;
                     if (npt == 0 && (th > 32 || threads > kStagedMaxThreads)) continue;
                     const int mc = max_ctas(b, threads, npt, tw, th);
                     if (mc < 1) continue;
@@ -1195,8 +1398,12 @@ int lbm_batch_set_config(lbm_batch b, const int* in5)
     if (tw < 32 || tw % 32 || threads < tw || threads > 512 || threads % tw)
         return bfail(b, LBM_EINVAL, "threads %d / tile width %d: need 32 | tw, tw | threads <= 512",
                      threads, tw);
-    if (npt != 0 && npt != 1 && npt != 2 && npt != 4)
-        return bfail(b, LBM_EINVAL, "rows per thread and pass must be 0 (staged), 1, 2 or 4");
+    if (npt != 0 && npt != 1 && npt != 2 && npt != 4 && npt != -1 && npt != -2)
+        return bfail(b, LBM_EINVAL,
+                     "variant must be 0 (staged), 1, 2, 4 or (two nodes per thread) -1, -2");
+    if (npt < 0 && (tw % 64 || threads % (tw / 2)))
+        return bfail(b, LBM_EINVAL, "two nodes per thread: tile width %d must be a multiple of 64"
+                     " and threads %d a multiple of half of it", tw, threads);
     if (npt == 0 && threads > kStagedMaxThreads)
         return bfail(b, LBM_EINVAL, "the staged kernel takes at most %d consumer threads",
                      kStagedMaxThreads);

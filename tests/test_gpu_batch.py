@@ -194,6 +194,13 @@ CONFIGS = [
     (128, 3, 64, 5, 0),
     (256, 2, 64, 16, 0),
     (96, 5, 32, 1, 0),
+    # the register kernel with two x-adjacent nodes per thread
+    (128, 3, 64, 5, -1),
+    (64, 1, 64, 3, -1),       # one CTA walks every tile of every domain
+    (256, 7, 128, 8, -2),
+    (512, 2, 128, 64, -2),
+    (256, 11, 256, 16, -2),
+    (128, 5, 64, 1, -2),      # one-row tiles
 ]
 
 
