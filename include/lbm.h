@@ -118,6 +118,14 @@ LBM_API int lbm_destroy(lbm_handle h);
 /* Message of the last error on h (thread-local message for h == NULL). */
 LBM_API const char* lbm_last_error(lbm_handle h);
 
+/* Fault injection for testing (no counterpart in the paper): the next n
+ * device allocations the library makes (a handle's arena, a batch, the
+ * subdomain buffers, the autotuner's backup, the MLP training buffers) fail
+ * as if the device were out of memory, without calling cudaMalloc; the call
+ * that needed the memory returns LBM_ENOMEM and its object stays valid.
+ * n = 0 turns it off.  Process-wide.  LBM_EINVAL for n < 0. */
+LBM_API int lbm_debug_fail_allocations(int n);
+
 /* ---- memory and stream ------------------------------------------------- */
 
 /* Bytes of device memory the handle needs: two copies of the distributions

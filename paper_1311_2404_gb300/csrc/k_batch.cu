@@ -1125,7 +1125,7 @@ int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, b->bytes);
+    cudaError_t e = dev_alloc(&p, b->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -1314,7 +1314,12 @@ int lbm_batch_autotune(lbm_batch b)
     // keep the state: copy the per-domain regions aside and restore them
     const size_t span = b->off_tables;     // every per-domain region lies below the tables
     void* save = nullptr;
-    BCK(b, cudaMalloc(&save, span), "autotune backup");
+    {
+        const cudaError_t e = dev_alloc(&save, span);
+        if (e != cudaSuccess)
+            return bfail(b, LBM_ENOMEM, "autotune backup (%zu bytes): %s", span,
+                         cudaGetErrorString(e));
+    }
     BCK(b, cudaMemcpyAsync(save, b->base, span, cudaMemcpyDeviceToDevice, b->stream), "backup");
     const int saved_cur = b->cur;
     const long long saved_t = b->t;

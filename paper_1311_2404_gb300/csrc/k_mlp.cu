@@ -217,16 +217,17 @@ bool is_dev(const void* p)
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
-    cudaError_t alloc(size_t n) { return cudaMalloc(&p, n); }
+    cudaError_t alloc(size_t n) { return lbm::dev_alloc(&p, n); }
     template <class T> T* as() { return static_cast<T*>(p); }
 };
 
 }  // namespace
 
-#define MCK(call, what)                                  \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return mfail(LBM_ECUDA, (what), e_); \
+#define MCK(call, what)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return mfail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, (what), e_); \
     } while (0)
 
 extern "C" {

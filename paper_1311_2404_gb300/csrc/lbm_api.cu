@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <string>
 #include <utility>
@@ -173,11 +174,23 @@ static void layout(lbm_ctx* h)
 template <class T>
 static T* at(lbm_ctx* h, size_t off) { return reinterpret_cast<T*>(h->base + off); }
 
+static std::atomic<int> g_fail_allocs{0};
+
+namespace lbm {
+cudaError_t dev_alloc(void** p, size_t bytes)
+{
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+}  // namespace lbm
+
 static int ensure_memory(lbm_ctx* h)
 {
     if (h->base) return LBM_OK;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, h->bytes);
+    cudaError_t e = dev_alloc(&p, h->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(h, LBM_ENOMEM, "cudaMalloc(%zu bytes): %s", h->bytes, cudaGetErrorString(e));
@@ -292,6 +305,13 @@ int lbm_bind_memory(lbm_handle h, void* dev_ptr, size_t bytes)
     h->owned = false;
     CK(h, cudaMemsetAsync(h->base + h->off_misc, 0, MISC_BYTES, h->stream), "clear status");
     CK(h, cudaMemsetAsync(h->base + h->off_nodes, 0, (size_t)h->sq * 4, h->stream), "clear node words");
+    return LBM_OK;
+}
+
+int lbm_debug_fail_allocations(int n)
+{
+    if (n < 0) return fail(nullptr, LBM_EINVAL, "allocation count %d is negative", n);
+    g_fail_allocs.store(n);
     return LBM_OK;
 }
 
@@ -1179,7 +1199,7 @@ int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau,
     for (int s = 0; s < nsub; ++s) maxloc = std::max(maxloc, m->hi[s] - m->lo[s]);
     m->scr_bytes = (size_t)(maxloc + 2) * m->layer_dense * 8 * (1 + D);
     m->off_scr = o; o = align256(o + m->scr_bytes);
-    cudaError_t e = cudaMalloc(&m->mem, o);
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&m->mem), o);
     if (e != cudaSuccess) {
         int code = mfail(nullptr, LBM_ENOMEM, "multi buffers (%zu bytes): %s", o,
                          cudaGetErrorString(e));

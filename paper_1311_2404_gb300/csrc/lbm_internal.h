@@ -10,6 +10,11 @@ namespace lbm {
 
 constexpr int kReduceBlocks = 1024;   // FP64 partial sums: kReduceBlocks x 5 doubles
 
+// Every device allocation the library makes goes through dev_alloc, so that
+// lbm_debug_fail_allocations can make the next ones fail (out of memory)
+// without calling cudaMalloc: the error paths are tested on the host.
+cudaError_t dev_alloc(void** p, size_t bytes);
+
 cudaError_t launch_step_bgk(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s);
 cudaError_t launch_step_mrt(int lattice, int store, const StepParams& p, bool mask, bool aa,

@@ -81,6 +81,7 @@ _PROTOS = {
     "lbm_multi_sync": (_i, [_vp]),
     "lbm_destroy": (_i, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_debug_fail_allocations": (_i, [_i]),
     "lbm_required_bytes": (_sz, [_vp]),
     "lbm_bind_memory": (_i, [_vp, _vp, _sz]),
     "lbm_set_stream": (_i, [_vp, _vp]),
@@ -204,6 +205,11 @@ def lbm_destroy(h):
 
 def lbm_last_error(h):
     return (_L.lbm_last_error(h) or b"").decode()
+
+
+def lbm_debug_fail_allocations(n):
+    """Make the library's next n device allocations fail (testing)."""
+    _check(_L.lbm_debug_fail_allocations(int(n)))
 
 
 def lbm_required_bytes(h):

@@ -119,3 +119,23 @@ def test_workload_generators_are_seeded():
     assert all(0.52 <= s["tau"] <= 0.9 for s in specs)
     m = wl.batch_channel_mask(specs[0])
     assert m.shape == (1, specs[0]["ny"], specs[0]["nx"]) and m[0, 0].all()
+
+
+def test_injected_allocation_failure_on_host(lbm):
+    """An allocation failure injected on the host: the call that needs the
+    arena returns LBM_ENOMEM (no cudaMalloc is attempted) and the handle
+    stays valid."""
+    h = lbm.lbm_create(16, 8, 8, lbm.LBM_D3Q19, lbm.LBM_BGK, 0.6, lbm.LBM_F32S)
+    try:
+        lbm.lbm_debug_fail_allocations(1)
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_set_geometry(h, np.zeros((8, 8, 16), dtype=np.uint8))
+        assert ei.value.code == lbm.LBM_ENOMEM
+        assert "out of memory" in lbm.lbm_last_error(h)
+        assert lbm.lbm_required_bytes(h) > 0
+    finally:
+        lbm.lbm_debug_fail_allocations(0)
+        lbm.lbm_destroy(h)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_debug_fail_allocations(-1)
+    assert ei.value.code == lbm.LBM_EINVAL
