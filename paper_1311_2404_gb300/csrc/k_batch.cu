@@ -971,7 +971,7 @@ static const void* kernel_for(int dtype, int npt)
 {
     if (npt < 0) {
         if (dtype == LBM_F16S)
-            return npt == -2 ? batch2_kernel_ptr<StoreF16S, 2, 96>()
+            return npt == -2 ? batch2_kernel_ptr<StoreF16S, 2, 104>()
                              : batch2_kernel_ptr<StoreF16S, 1, 80>();
         return npt == -2 ? batch2_kernel_ptr<StoreF32S, 2, 128>()
                          : batch2_kernel_ptr<StoreF32S, 1, 96>();
