@@ -614,15 +614,17 @@ def cpu_baseline(spec, budget_s=12.0, steps=None, threads=0):
     import oracle
     oracle.build()
     cores = oracle.max_threads(threads)
-    p, F, mask, n = _oracle_sample(spec, 1)
+    # pilot step on a slab deep enough to keep every thread busy (the oracle
+    # parallelises over z), then as many steps as fit the budget
+    nz_s = min(spec["n"][2], max(4 * cores, 32))
+    p, F, mask, n = _oracle_sample(spec, nz_s)
     p.nthreads = threads
     t0 = time.perf_counter()
     oracle.run(p, F, 1, mask)
     dt1 = time.perf_counter() - t0
-    nz_s = max(1, min(spec["n"][2], int(budget_s / 4 / max(dt1, 1e-6))))
     p, F, mask, n = _oracle_sample(spec, nz_s)
     p.nthreads = threads
-    nsteps = max(1, min(50, int(budget_s / max(dt1 * nz_s, 1e-6))))
+    nsteps = max(1, min(400, int(budget_s / max(dt1, 1e-6))))
     t0 = time.perf_counter()
     oracle.run(p, F, nsteps, mask)
     dt = time.perf_counter() - t0
