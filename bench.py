@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
                     help="ELBM alpha solve for --workload elbm")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
+    ap.add_argument("--batch-config", default="",
+                    help="launch configuration for --workload batch instead of autotuning: "
+                         "threads,ctas,tile_width,tile_rows,variant")
     ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
                     help="distribution access pattern (AA: one array)")
     ap.add_argument("--round", default="dither", choices=["dither", "nearest"],
@@ -743,7 +746,10 @@ def run_batch(args):
         lbm.lbm_batch_init_equilibrium(b, d, r, u)
         rho_bytes += r.nbytes
     nodes = lbm.lbm_batch_nodes(b)
-    lbm.lbm_batch_autotune(b)
+    if args.batch_config:
+        lbm.lbm_batch_set_config(b, [int(v) for v in args.batch_config.split(",")])
+    else:
+        lbm.lbm_batch_autotune(b)
     cfg = lbm.lbm_batch_get_config(b)
     lbm.lbm_batch_step(b, max(args.warmup, 3))
     lbm.lbm_batch_sync(b)
