@@ -139,3 +139,33 @@ def test_injected_allocation_failure_on_host(lbm):
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_debug_fail_allocations(-1)
     assert ei.value.code == lbm.LBM_EINVAL
+
+
+def test_header_is_plain_c(lbm, tmp_path):
+    """The ABI header compiles as C99 (no C++ in the interface) and a C
+    program links against the library and calls it."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = os.path.join(root, "paper_1311_2404_gb300", "_lib", "liblbm.so")
+    if not os.path.exists(lib):
+        pytest.skip("library not built")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include "lbm.h"\n'
+        "int main(void) {\n"
+        "    lbm_handle h = 0;\n"
+        "    if (lbm_create(8, 8, 8, LBM_D3Q19, LBM_BGK, 0.6, LBM_F32S, &h) != LBM_OK) return 1;\n"
+        "    if (lbm_required_bytes(h) == 0) return 2;\n"
+        "    if (lbm_create(0, 8, 8, LBM_D3Q19, LBM_BGK, 0.6, LBM_F32S, &h) != LBM_EINVAL) return 3;\n"
+        "    return lbm_destroy(h);\n"
+        "}\n")
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(root, "include"), str(src), "-o", str(exe), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
