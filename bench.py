@@ -672,11 +672,13 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = oracle.max_threads(0)
-    # per-step sample sized so warmup + steps finish in about two minutes
-    p1, F1, m1, n1 = _oracle_sample(spec, 1)
+    # per-step sample sized so warmup + steps finish in about two minutes; the
+    # pilot slab keeps every oracle thread busy (it parallelises over z)
+    nz_p = min(spec["n"][2], max(4 * cores, 32))
+    p1, F1, m1, n1 = _oracle_sample(spec, nz_p)
     t0 = time.perf_counter()
     oracle.run(p1, F1, 1, m1)
-    plane_s = time.perf_counter() - t0
+    plane_s = (time.perf_counter() - t0) / nz_p
     total_steps = max(args.steps, 1) + max(args.warmup, 0)
     per_step_budget = 120.0 / total_steps
     if per_step_budget >= plane_s:
