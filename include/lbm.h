@@ -329,7 +329,10 @@ LBM_API size_t lbm_state_bytes(lbm_handle h);
 
 /* Copy the raw state out / in (host or device pointer, lbm_state_bytes).
  * The layout is internal; a state is only meaningful for a handle created
- * with the same arguments.  set_state also sets the step counter to t. */
+ * with the same arguments (and access pattern).  set_state also sets the
+ * step counter to t.  With the AB pattern the slots of solid nodes carry no
+ * information: nothing reads them, and a step may overwrite those next to
+ * fluid nodes with the rest state (whole-sector writes). */
 LBM_API int lbm_get_state(lbm_handle h, void* dst, long long* t);
 LBM_API int lbm_set_state(lbm_handle h, const void* src, long long t);
 
