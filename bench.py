@@ -4,7 +4,9 @@
 Default workload (the headline metric): D3Q19 LBGK, FP32 arithmetic with
 FP32 shifted storage (f - w), 256^3 periodic Taylor-Green vortex, tau 0.6,
 u0 0.05.  One bench step = one lattice Boltzmann time step over all nodes
-(one fused stream-collide launch).  Prints ONE JSON line.
+(one fused stream-collide launch); the K timed steps are replayed as one CUDA
+graph (captured beforehand in an untimed run of K steps; --no-graph times K
+direct launches).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload tg256|duct|elbm|kida|ldc|batch] [--dtype f32s|f16s|bf16s|f32]
@@ -87,6 +89,9 @@ def parse():
     ap.add_argument("--no-overlap", action="store_true",
                     help="with --subdomains: exchange after whole slabs, no bulk/boundary split")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="time K direct launches instead of replaying the K steps as one CUDA "
+                         "graph (captured in an untimed run of K steps after the warm-up)")
     return ap.parse_args()
 
 
@@ -458,6 +463,11 @@ def run_ours(args):
         stream.synchronize()
         for _ in range(max(args.warmup, 3)):
             lbm.lbm_step(sim.h, 1)
+        if args.graph:
+            lbm.lbm_set_graph(sim.h, True)
+            lbm.lbm_step(sim.h, args.steps)               # capture (untimed)
+            if args.steps % 2:                            # the state back in the first array
+                lbm.lbm_step(sim.h, 1)
         stream.synchronize()
 
         sampler = ClockSampler(local) if rank == 0 else None
@@ -547,6 +557,7 @@ def run_ours(args):
                    **({"alpha": args.alpha} if spec["model"] == 2 else {}),
                    **({"rounding": args.round} if args.dtype in ("f16s", "bf16s") else {}),
                    **({"pattern": "AA"} if args.pattern == "aa" else {}),
+                   "launch": "cuda_graph" if args.graph else "direct",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
                          % (bytes_per_node(args.dtype, spec["lattice"]) * nodes / 1e9)},
