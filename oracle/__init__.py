@@ -27,7 +27,7 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 # model / alpha-mode codes of the oracle's parameter block
 BGK, MRT, ELBM, REG, SMAG = 0, 1, 2, 3, 4
-NEWTON, SERIES_GUARDED, MLP_GUARDED, FIXED2 = 0, 1, 2, 3
+NEWTON, SERIES_GUARDED, MLP_GUARDED, FIXED2, ROOT_GUARDED = 0, 1, 2, 3, 4
 # per-node alpha outcomes
 AL_CONV, AL_SKIP, AL_CLAMP, AL_NOCONV, AL_FIXED, AL_GUARDED = range(6)
 
@@ -96,6 +96,8 @@ def lib():
         L.oracle_elbm_features.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         L.oracle_mlp_guess.argtypes = [dp, dp]
         L.oracle_mlp_guess.restype = ctypes.c_double
+        L.oracle_series_root_guess.argtypes = [dp, ctypes.c_double]
+        L.oracle_series_root_guess.restype = ctypes.c_double
         L.oracle_init.argtypes = [PP, dp, dp, dp]
         L.oracle_bc_node.argtypes = [PP, ctypes.c_int, dp]
         L.oracle_run.argtypes = [PP, dp, dp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
@@ -237,6 +239,13 @@ def elbm_features(D, f, fe):
 def mlp_guess(P, feat) -> float:
     return lib().oracle_mlp_guess(_dp(np.ascontiguousarray(P, dtype=np.float64)),
                                   _dp(np.ascontiguousarray(feat, dtype=np.float64)))
+
+
+def series_root_guess(ak, A1) -> float:
+    """Root of g(alpha)/alpha with g's alpha-series truncated after a_6 (ak =
+    a_0..a_6, A1 = A + a_1): the guess of alpha mode ROOT_GUARDED."""
+    return lib().oracle_series_root_guess(_dp(np.ascontiguousarray(ak, dtype=np.float64)),
+                                          float(A1))
 
 
 def init(p: OracleParams, rho: np.ndarray, u: np.ndarray) -> np.ndarray:

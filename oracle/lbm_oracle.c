@@ -278,17 +278,18 @@ typedef struct {
     int D;            /* 2: D2Q9, 3: D3Q19 */
     int model;        /* 0 LBGK, 1 MRT, 2 ELBM */
     int alpha_mode;   /* ELBM: 0 Newton from 2, 1 series guess + guarded Newton,
-                         2 MLP guess + guarded Newton, 3 alpha fixed at 2 */
+                         2 MLP guess + guarded Newton, 3 alpha fixed at 2,
+                         4 truncated-series root guess + guarded Newton */
     int max_iter;     /* Newton evaluation cap */
     int feq_variant;  /* ELBM: 0 entropic (restored on D3Q19), 1 polynomial */
     int nthreads;     /* OpenMP threads for oracle_run; 0 = runtime default */
-    int guard_steps;  /* guarded modes: Newton steps taken from the guess */
+    int guard_steps;  /* guarded modes: evaluations that may end in early acceptance */
     double tau;
     double force[3];
     double s[19];     /* MRT rates, d'Humieres moment order */
     double tol;       /* Newton: stop when |alpha_{n+1} - alpha_n| <= tol alpha_n */
     double skip_eps;  /* alpha = 2 when max_i |x_i| < skip_eps */
-    double guard_tol; /* guarded modes: accept when the last correction <= guard_tol */
+    double guard_tol; /* guarded modes: accept a correction <= guard_tol alpha */
     const double* mlp;/* MLP parameters for alpha_mode 2 */
     double smag_cs;   /* Smagorinsky constant C_S (model 4) */
     int q;            /* velocity set: 0 = D2Q9 / D3Q19 by D, or 9, 15, 19, 27 */
@@ -357,11 +358,48 @@ static void elbm_features(const olat* L, const double* f, const double* d,
         for (int k = 0; k < 7; ++k) ak[k] = a[k];
 }
 
+/* Second-order small-deviation guess: the root of g(alpha)/alpha expanded
+ * about alpha = 2 to second order in the moments a_k = sum f x^k, for an f_eq
+ * that minimises H (then A = -sum f x ln(1 + x)). */
+static double series2_guess(const double* ak)
+{
+    return 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) + 4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+}
+
+/* Root of g(alpha)/alpha with the series of g truncated after a_6 and the
+ * node's own A (exact for any f_eq, not only the H minimiser):
+ *   h(alpha) = A + a_1 + sum_{k=2}^{6} (-1)^k a_k alpha^(k-1) / (k (k-1)),
+ * three Newton steps on h from the second-order guess. */
+static double series_root_guess(const double* ak, double A1)
+{
+    double a = series2_guess(ak);
+    for (int it = 0; it < 3; ++it) {
+        double h = A1, hp = 0.0;
+        for (int k = 2; k <= 6; ++k) {
+            const double c = ((k % 2) ? -1.0 : 1.0) * ak[k] / (double)(k * (k - 1));
+            h += c * pow(a, k - 1);
+            hp += (k - 1) * c * pow(a, k - 2);
+        }
+        a -= h / hp;
+    }
+    return a;
+}
+
+/* The same second-order guess from the surrogate's features (t_3, t_4 and
+ * eps = sqrt(a_2 / rho)): (a_3 - 2 a_4) / (3 a_2) = (t_3 eps - 2 t_4 eps^2) / 3
+ * and 4 a_3^2 / (9 a_2^2) = 4 t_3^2 eps^2 / 9. */
+static double series2_from_features(const double* feat)
+{
+    const double t3 = feat[0], t4 = feat[1], eps = feat[4];
+    return 2.0 + (t3 * eps - 2.0 * t4 * eps * eps) / 3.0 + 4.0 * t3 * t3 * eps * eps / 9.0;
+}
+
 /* MLP 8 -> 32 -> 32 -> 1, tanh hidden units (parameter layout documented in
- * the Python loader).  Returns alpha guess 2 + scale * out * eps. */
+ * the Python loader).  The network learns what the second-order guess s2
+ * misses: alpha guess = s2 + scale * out. */
 #define MLP_IN 8
 #define MLP_H 32
-static double mlp_guess(const double* P, const double* feat)
+static double mlp_guess(const double* P, const double* feat, double s2)
 {
     const double* mean = P;
     const double* istd = P + 8;
@@ -386,7 +424,7 @@ static double mlp_guess(const double* P, const double* feat)
     }
     double out = b3[0];
     for (int k = 0; k < MLP_H; ++k) out += W3[k] * h2[k];
-    return 2.0 + scale[0] * out * feat[4];
+    return s2 + scale[0] * out;
 }
 
 /* Solve Eq. alpha_cond for the non-trivial root.  out[0] = alpha,
@@ -424,40 +462,30 @@ static void elbm_alpha(const olat* L, const oracle_params* p, const double* f,
     int status = AL_NOCONV;
 
     double feat[8], ak[7];
-    if (p->alpha_mode == 1 || p->alpha_mode == 2) {
+    const int guarded = p->alpha_mode == 1 || p->alpha_mode == 2 || p->alpha_mode == 4;
+    if (guarded) {
         elbm_features(L, f, d, lnfw, rho, feat, ak);
         double guess;
-        if (p->alpha_mode == 1)   /* second-order expansion of g(alpha)/alpha = 0 */
-            guess = 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
-                    4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
-        else
-            guess = mlp_guess(p->mlp, feat);
-        double a = guess;
-        if (!(a > lo)) a = lo;
-        if (!(a < hi)) a = hi;
-        double corr = INFINITY;
-        for (int k = 0; k < p->guard_steps; ++k) {
-            double g, gp;
-            elbm_g(L, f, d, lnfw, a, &g, &gp);
-            ++evals;
-            double an = (gp > 0.0) ? a - g / gp : NAN;
-            if (!(an > lo)) an = lo;
-            if (!(an < hi)) an = hi;
-            corr = fabs(an - a);
-            a = an;
+        if (p->alpha_mode == 1) {
+            guess = series2_guess(ak);
+        } else if (p->alpha_mode == 2) {
+            guess = mlp_guess(p->mlp, feat, series2_guess(ak));
+        } else {
+            double A1 = 0.0;           /* A + a_1, a_1 = sum Delta */
+            for (int i = 0; i < L->Q; ++i) A1 += d[i] * lnfw[i] + d[i];
+            guess = series_root_guess(ak, A1);
         }
-        if (corr <= p->guard_tol * a) {
-            alpha = a;
-            status = AL_GUARDED;
-            goto done;
-        }
-        /* fallback: full Newton below, from 2 */
+        alpha = guess;
+        if (!(alpha > lo)) alpha = lo;
+        if (!(alpha < hi)) alpha = hi;
     }
 
     /* Safeguarded Newton on the convex g (g(0) = 0, g < 0 on (0, alpha*),
-     * g > 0 beyond): keep a bracket [lo, hi], step by Newton when it stays
-     * inside, otherwise bisect. */
-    alpha = 2.0;
+     * g > 0 beyond) from 2, or from the guess: keep a bracket [lo, hi], step
+     * by Newton when it stays inside, otherwise bisect.  The guarded modes
+     * accept the first Newton correction of at most guard_tol alpha within
+     * their first guard_steps evaluations (one more Newton step from there
+     * squares that error); otherwise the solve continues to the tolerance. */
     if (!(alpha < hi)) alpha = 0.5 * (lo + hi);
     for (int it = 0; it < p->max_iter; ++it) {
         double g, gp;
@@ -467,6 +495,12 @@ static void elbm_alpha(const olat* L, const oracle_params* p, const double* f,
         if (g < 0.0) lo = alpha;
         else { hi = alpha; hi_known = 1; }
         double an = (gp > 0.0) ? alpha - g / gp : NAN;
+        if (guarded && it < p->guard_steps && an > lo && an < hi &&
+            fabs(an - alpha) <= p->guard_tol * alpha) {
+            alpha = an;
+            status = AL_GUARDED;
+            break;
+        }
         /* a step already below the tolerance ends the solve; testing the
          * bracket first would reject a sub-ulp step at the root itself */
         if (fabs(an - alpha) <= p->tol * alpha) { alpha = an; status = AL_CONV; break; }
@@ -836,7 +870,13 @@ int oracle_elbm_features(int D, const double* f, const double* feq, double* feat
 /* MLP guess for a feature vector (FP64). */
 double oracle_mlp_guess(const double* P, const double* feat)
 {
-    return mlp_guess(P, feat);
+    return mlp_guess(P, feat, series2_from_features(feat));
+}
+
+/* Truncated-series root guess from the moments a_0..a_6 and A + a_1. */
+double oracle_series_root_guess(const double* ak, double A1)
+{
+    return series_root_guess(ak, A1);
 }
 
 /* F[q][z][y][x] = f_eq(rho, u) with the model's equilibrium (polynomial for

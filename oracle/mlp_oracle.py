@@ -3,7 +3,10 @@
 TEST INFRASTRUCTURE ONLY.  The surrogate is not in the paper; it is an
 8 -> 32 -> 32 -> 1 tanh network that maps eight lattice-symmetry invariants of
 (f, f_eq - f) to a guess of the entropic over-relaxation alpha (Eq.
-alpha_cond), alpha_guess = 2 + scale * out * eps.
+alpha_cond): it learns what the second-order small-deviation guess s2 misses,
+alpha_guess = s2 + scale * out, with s2 written in the features
+(t_3 = feature 0, t_4 = feature 1, eps = feature 4):
+    s2 = 2 + (t_3 eps - 2 t_4 eps^2) / 3 + 4 t_3^2 eps^2 / 9.
 
 Parameter vector layout (float64 here; the CUDA side keeps FP32 masters and a
 BF16 copy of the weight matrices):
@@ -17,7 +20,7 @@ BF16 copy of the weight matrices):
     [1392]       b3
     [1393]       output scale            (fixed)
 Trainable entries: [16:1393].  Loss: mean over the batch of (out - t)^2 with
-t = (alpha* - 2) / (scale * eps).
+t = (alpha* - s2) / scale.
 Adam is Kingma & Ba (2015) with bias correction.
 """
 from __future__ import annotations
@@ -68,14 +71,23 @@ def forward(P, X):
     return out, (Z, H1, H2)
 
 
+def series2(X):
+    """Second-order small-deviation guess of alpha from the features: the
+    expansion 2 + (a_3 - 2 a_4) / (3 a_2) + 4 a_3^2 / (9 a_2^2) with
+    a_k = rho t_k eps^k."""
+    X = np.asarray(X, dtype=np.float64)
+    t3, t4, eps = X[:, 0], X[:, 1], X[:, 4]
+    return 2.0 + (t3 * eps - 2.0 * t4 * eps * eps) / 3.0 + 4.0 * t3 * t3 * eps * eps / 9.0
+
+
 def alpha_guess(P, X):
     out, _ = forward(P, X)
-    return 2.0 + P[O_SCALE] * out * np.asarray(X)[:, 4]
+    return series2(X) + P[O_SCALE] * out
 
 
 def target(P_or_scale, X, alpha):
     scale = P_or_scale if np.isscalar(P_or_scale) else P_or_scale[O_SCALE]
-    return (np.asarray(alpha) - 2.0) / (scale * np.asarray(X)[:, 4])
+    return (np.asarray(alpha) - series2(X)) / scale
 
 
 def loss_and_grad(P, X, t):

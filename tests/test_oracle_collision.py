@@ -13,7 +13,8 @@ import mpmath
 import numpy as np
 import pytest
 
-from oracle import BGK, MRT, ELBM, FIXED2, NEWTON, SERIES_GUARDED, AL_CONV, AL_GUARDED
+from oracle import (BGK, MRT, ELBM, FIXED2, NEWTON, SERIES_GUARDED, ROOT_GUARDED, AL_CONV,
+                    AL_GUARDED)
 
 
 def _dim(code):
@@ -317,3 +318,39 @@ def test_near_equilibrium_skip(oracle_lib):
     fe = oracle_lib.feq(3, f.sum(), u, 2)
     a = oracle_lib.elbm_alpha(p, f, fe)
     assert a[0] == 2.0 and a[1] == 0
+
+
+def test_truncated_series_root_order_and_guarded_mode(oracle_lib):
+    """The ROOT_GUARDED guess: the root of g(alpha)/alpha with g's series in
+    alpha truncated after a_6 and the node's own A.  Truncation drops terms
+    a_k alpha^(k-1) / (k (k-1)) with k >= 7, i.e. x^5 relative to a_2: shrinking
+    a departure threefold must shrink the guess's error about 3^5 = 243-fold.
+    It also covers the restored D3Q19 equilibrium, which is not the H
+    minimiser and on which the second-order guess (derived for the minimiser)
+    keeps an error that only shrinks like the restoration term.  The guarded
+    mode from this guess returns Newton's root within 1e-10 after one
+    evaluation."""
+    rng = np.random.default_rng(12)
+    e, _, _ = oracle_lib.lattice(3)
+    pn = oracle_lib.make_params(D=3, model=ELBM, tau=0.6, skip_eps=0.0, tol=1e-15)
+    pr = oracle_lib.make_params(D=3, model=ELBM, tau=0.6, skip_eps=0.0,
+                                alpha_mode=ROOT_GUARDED, guard_steps=1)
+    for _ in range(8):
+        u = rng.uniform(-0.05, 0.05, 3)
+        fe0 = oracle_lib.feq(3, 1.0, u, 2)
+        xi = rng.standard_normal(19)
+        errs = []
+        for amp in (3e-2, 1e-2):
+            f = fe0 * (1.0 + amp * xi)
+            rho = f.sum()
+            fe = oracle_lib.feq(3, rho, (e.T @ f) / rho, 2)
+            a, *_ = oracle_lib.elbm_alpha(pn, f, fe)
+            _, ak = oracle_lib.elbm_features(3, f, fe)
+            w = oracle_lib.lattice(3)[1]
+            d = fe - f
+            A1 = float((d * np.log(f / w)).sum() + d.sum())
+            errs.append(abs(a - oracle_lib.series_root_guess(ak, A1)))
+            ar, evals, status, resid = oracle_lib.elbm_alpha(pr, f, fe)
+            assert abs(ar - a) < 1e-10 and resid < 1e-12
+            assert status == AL_GUARDED and evals == 1
+        assert errs[1] < errs[0] / 100.0
