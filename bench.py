@@ -62,8 +62,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tg256",
                     choices=["tg256", "duct", "elbm", "kida", "ldc", "batch"])
-    ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp"],
-                    help="ELBM alpha solve for --workload elbm")
+    ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp", "root"],
+                    help="ELBM alpha solve for --workload elbm (root: the truncated-series "
+                         "root guess)")
+    ap.add_argument("--guard-steps", type=int, default=2,
+                    help="ELBM guarded modes: evaluations that may end in early acceptance")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
     ap.add_argument("--batch-config", default="",
                     help="launch configuration for --workload batch instead of autotuning: "
@@ -217,7 +220,7 @@ def workload_spec(name, dtype, size=0, model="", lattice="", shape=""):
         spec["n"] = (nxs, nys, nzs)
         spec["name"] = spec["name"].replace(old, f"{nxs}x{nys}x{nzs}")
     if lattice and name != "batch":
-        from paper_1311_2404_gb300 import lbm
+        from paper_1311_2404_gb300 import abi as lbm   # constants only: loads no library
         spec["lattice"] = {"q15": lbm.LBM_D3Q15, "q19": lbm.LBM_D3Q19,
                            "q27": lbm.LBM_D3Q27}[lattice]
         spec["name"] = spec["name"].replace("d3q19", "d3" + lattice)
@@ -240,7 +243,8 @@ def workload_spec(name, dtype, size=0, model="", lattice="", shape=""):
 
 
 def _workload_spec(name, dtype):
-    from paper_1311_2404_gb300 import lbm
+    # the ABI's constants only: the CPU reference arm must not load the CUDA library
+    from paper_1311_2404_gb300 import abi as lbm
     dmap = {"f32s": lbm.LBM_F32S, "f32": lbm.LBM_F32, "f16s": lbm.LBM_F16S,
             "bf16s": lbm.LBM_BF16S}
     if name == "tg256":
@@ -450,8 +454,10 @@ def run_ours(args):
                              else lbm.LBM_ROUND_DITHER)
         if spec["model"] == lbm.LBM_ELBM:
             mode = {"newton": lbm.LBM_ALPHA_NEWTON, "series": lbm.LBM_ALPHA_SERIES_GUARDED,
-                    "mlp": lbm.LBM_ALPHA_MLP_GUARDED}[args.alpha]
+                    "mlp": lbm.LBM_ALPHA_MLP_GUARDED,
+                    "root": lbm.LBM_ALPHA_ROOT_GUARDED}[args.alpha]
             lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-3)
+            lbm.lbm_set_elbm_guard(sim.h, args.guard_steps, 1e-6)
             if args.alpha == "mlp":
                 from paper_1311_2404_gb300 import alpha_training as at
                 Xp, yp, _, _ = at.collect_pairs(n=64)

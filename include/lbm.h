@@ -88,12 +88,19 @@ enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 };
 /* Element type of macroscopic-field arrays crossing the ABI. */
 enum { LBM_FIELD_F64 = 0, LBM_FIELD_F32 = 1 };
 /* ELBM alpha modes (Eq. alpha_cond).  NEWTON: safeguarded FP64 Newton from
- * alpha = 2.  SERIES_GUARDED: second-order small-deviation series guess,
- * then at most guard_steps FP64 Newton steps, full Newton if the last
- * correction exceeds guard_tol.  MLP_GUARDED: same with the learned guess
- * (lbm_load_alpha_mlp).  FIXED2: alpha = 2 (the LBGK limit; tests only). */
+ * alpha = 2 to the tolerance.  The guarded modes run the same Newton from a
+ * guess and accept the first correction of at most guard_tol * alpha within
+ * their first guard_steps g evaluations (lbm_set_elbm_guard); otherwise
+ * they continue to the tolerance:
+ *   SERIES_GUARDED: the second-order small-deviation series guess
+ *     s2 = 2 + (a_3 - 2 a_4) / (3 a_2) + 4 a_3^2 / (9 a_2^2), a_k = sum f x^k;
+ *   MLP_GUARDED: s2 plus the learned correction (lbm_load_alpha_mlp);
+ *   ROOT_GUARDED: the root of g(alpha)/alpha with g's series in alpha
+ *     truncated after a_6 and the node's own A = sum Delta ln(f / w) (no
+ *     learned part; three Newton steps on that polynomial from s2).
+ * FIXED2: alpha = 2 (the LBGK limit; tests only). */
 enum { LBM_ALPHA_NEWTON = 0, LBM_ALPHA_SERIES_GUARDED = 1, LBM_ALPHA_MLP_GUARDED = 2,
-       LBM_ALPHA_FIXED2 = 3 };
+       LBM_ALPHA_FIXED2 = 3, LBM_ALPHA_ROOT_GUARDED = 4 };
 
 typedef struct lbm_ctx* lbm_handle;
 
@@ -230,9 +237,10 @@ LBM_API int lbm_set_smagorinsky(lbm_handle h, double cs);
  * guard_steps / guard_tol are set by lbm_set_elbm_guard. */
 LBM_API int lbm_set_elbm(lbm_handle h, int alpha_mode, double tol, int max_iter, double skip_eps);
 
-/* Guarded modes: take guard_steps (1..4, default 2) Newton steps from the
- * guess and accept when the last correction <= guard_tol * alpha (default
- * 1e-6); otherwise fall back to the full Newton solve. */
+/* Guarded modes: accept the first Newton correction <= guard_tol * alpha
+ * (default 1e-6; the corrected alpha is then off by about its square) within
+ * the first guard_steps (1..4, default 2) g evaluations from the guess;
+ * otherwise Newton continues from there to the tolerance. */
 LBM_API int lbm_set_elbm_guard(lbm_handle h, int guard_steps, double guard_tol);
 
 /* ELBM entropic equilibrium form: 0 = product form with mass/momentum
@@ -242,7 +250,8 @@ LBM_API int lbm_set_elbm_feq(lbm_handle h, int variant);
 /* Load the alpha surrogate's parameters (n = 1394 floats, host or device,
  * layout: mean[8], inv_std[8], W1[32][8], b1[32], W2[32][32], b2[32],
  * W3[32], b3, scale).  Weight matrices are rounded to BF16 on load;
- * accumulation is FP32.  Guess: alpha = 2 + scale * out * eps. */
+ * accumulation is FP32.  Guess: alpha = s2 + scale * out (s2 as for
+ * LBM_ALPHA_SERIES_GUARDED). */
 LBM_API int lbm_load_alpha_mlp(lbm_handle h, const float* params, int n);
 
 /* Request per-node alpha output (FP64, [nz][ny][nx]) on output steps
@@ -399,11 +408,12 @@ LBM_API int lbm_batch_set_rounding(lbm_batch b, int mode);
 LBM_API int lbm_batch_set_wait_limit(lbm_batch b, long long spins);
 /* Fault-injection hook for testing the timeout paths.  on = 1: CTA 0 leaves
  * the first grid barrier of the next launch without arriving, so every other
- * CTA's bounded wait runs out.  on = 2 (staged kernel): the first stage of
- * the next launch expects 16 bytes more than its copies deliver, so the wait
- * for it runs out.  Either way the next synchronising call returns
- * LBM_ETIMEOUT and the state after that launch is incomplete.  0 turns the
- * hook off. */
+ * CTA's bounded wait runs out.  on = 2 (staged kernel): the producer of each
+ * CTA issues no copies for its first stage of the next launch and does not
+ * arrive on it, so the consumers' wait for it runs out (the CTA then waits,
+ * bounded, for the copies it did issue before it exits).  Either way the
+ * next synchronising call returns LBM_ETIMEOUT and the state after that
+ * launch is incomplete.  0 turns the hook off. */
 LBM_API int lbm_batch_inject_missing_arrival(lbm_batch b, int on);
 LBM_API int lbm_batch_sync(lbm_batch b);
 LBM_API long long lbm_batch_launch_count(lbm_batch b);
@@ -447,13 +457,15 @@ LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const fl
  *     batch).  X_dev [n][8] and t_dev [n] must be device memory; params
  *     (1394 floats) may be host or device; loss and grad (1394 floats) are
  *     written to host or device memory.
- *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     with cudaGetSymbolAddress (which allocates nothing), so the address is
+ *     never stale, also after a device reset.
  *   - Every call shares the array and leaves its contents behind; the call
  *     clears what must start at zero.  Calls that overlap on the GPU (other
  *     streams, other threads) race on the array: serialise them.
- *   - Synchronises the stream.  No cudaMalloc, cudaFree or allocating
- *     library routine is called. */
+ *   - Synchronises the stream and copies the loss to the host before it
+ *     returns.  No cudaMalloc, cudaFree or allocating library routine is
+ *     called. */
 LBM_API int lbm_mlp_grad_static(const float* X_dev, const float* t_dev, int n,
                                 const float* params, float* loss, float* grad,
                                 void* cuda_stream);
@@ -524,8 +536,54 @@ LBM_API int lbm_multi_step(lbm_multi m, int n);
 /* Whole-domain rho and v of the last step (as lbm_get_macro).  Synchronises. */
 LBM_API int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype);
 /* Bytes that cross slab faces per step: 2 nsub faces x directions x nodes
- * per row x storage element size (what a multi-GPU run would send). */
+ * per row x storage element size (what a multi-GPU run would send); for a
+ * rank handle, the bytes that rank sends per step (2 faces). */
 LBM_API int lbm_multi_halo_bytes(lbm_multi m, long long* per_step);
+
+/* ---- one slab per process (Sec. 3.6's multi-GPU decomposition) ----------
+ * A rank handle holds only slab `rank` (0 <= rank < nsub) of the nsub-slab
+ * decomposition above, for runs with one process (and GPU) per slab.  Each
+ * step moves two face buffers of face_bytes each between neighbouring ranks
+ * (periodic: rank nsub - 1's upper neighbour is rank 0), which the caller
+ * does between lbm_multi_step_begin and lbm_multi_step_end:
+ *   send + 0          the populations leaving through the upper face, to
+ *                     rank + 1's recv + 0;
+ *   send + face_bytes the populations leaving through the lower face, to
+ *                     rank - 1's recv + face_bytes;
+ *   recv + 0          from rank - 1 (lands in the lower ghost row);
+ *   recv + face_bytes from rank + 1 (lands in the upper ghost row).
+ * With nsub = 1 the rank is its own neighbour (copy send to recv).  Each
+ * buffer is a list of (directions with a component along the decomposed
+ * axis) runs of one padded row, in the handle's storage type.  The setters,
+ * lbm_multi_set_geometry and lbm_multi_init_equilibrium work as for
+ * lbm_multi_create (whole-domain arrays; the rank takes its rows), and
+ * lbm_multi_get_macro writes only the rank's rows of whole-domain arrays.
+ * Results equal the single-domain run bit for bit.  lbm_multi_step is
+ * refused for nsub > 1 (LBM_ESTATE).  Errors: LBM_EINVAL for rank outside
+ * 0..nsub-1, as lbm_multi_create otherwise. */
+LBM_API int lbm_multi_create_rank(int nx, int ny, int nz, int lattice, int model, double tau,
+                                  int dtype, int nsub, int rank, lbm_multi* out);
+/* Device addresses of the rank handle's send and receive buffers (2 faces of
+ * face_bytes each, laid out as above; owned by the handle).  LBM_EINVAL for a
+ * handle from lbm_multi_create. */
+LBM_API int lbm_multi_face_buffers(lbm_multi m, void** send, void** recv, size_t* face_bytes);
+/* First half of one time step of a rank handle: updates the slab's two
+ * boundary rows, collects their outgoing populations into the send buffers
+ * on the exchange stream (lbm_multi_exchange_stream) and, with overlap on,
+ * starts the bulk rows on the handle's stream.  output = 1 writes rho and v
+ * of this step.  The send buffers are complete when the exchange stream
+ * reaches this point; enqueue the transfer there (or synchronise that stream
+ * first).  LBM_ESTATE if a begun step has not ended or before the initial
+ * state. */
+LBM_API int lbm_multi_step_begin(lbm_multi m, int output);
+/* Second half: distributes the receive buffers into the ghost rows on the
+ * exchange stream (after whatever the caller enqueued there) and makes the
+ * handle's stream wait for it.  LBM_ESTATE without a begun step. */
+LBM_API int lbm_multi_step_end(lbm_multi m);
+/* The internal stream the exchange runs on (a cudaStream_t). */
+LBM_API int lbm_multi_exchange_stream(lbm_multi m, void** stream);
+/* Rows [lo, hi) of the decomposed axis that the handle updates. */
+LBM_API int lbm_multi_rows(lbm_multi m, int* lo, int* hi);
 /* Kernels this handle has launched (stream-collide, collect, distribute, pack). */
 LBM_API long long lbm_multi_launch_count(lbm_multi m);
 LBM_API int lbm_multi_sync(lbm_multi m);

@@ -10,6 +10,9 @@
 //                (product form, read with sqrt(1 + 3 u^2), mass and momentum
 //                restored on D3Q19), FP64 safeguarded Newton for alpha, EDM
 //                forcing Eq. edm_force.
+// Each operator reports the node's density as its deviation drho = rho - 1
+// (the kernels store that in the rho output field; readback adds the 1 in
+// FP64), so the output keeps the precision of the deviation form.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -82,7 +85,7 @@ __host__ __device__ __forceinline__ R edot(int i, R a0, R a1, R a2)
 // ---------------------------------------------------------------------------
 template <class L, class R>
 __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R F1, R F2,
-                                                     bool has_force, R& rho_out, R (&v)[3])
+                                                     bool has_force, R& drho_out, R (&v)[3])
 {
     constexpr int NP = (L::Q - 1) / 2;
     R S[NP], A[NP];
@@ -144,7 +147,7 @@ __host__ __device__ __forceinline__ void bgk_collide(R (&d)[L::Q], R om, R F0, R
         d[i] = dp;
         d[i + 1] = dm;
     }
-    rho_out = rho;
+    drho_out = drho;
 }
 
 // ---------------------------------------------------------------------------
@@ -179,7 +182,7 @@ __host__ __device__ __forceinline__ void eq_pair(int i, R rho, R drho, R u0, R u
 template <class L, class R, bool SMAG>
 __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0, R cs2smag,
                                                      R F0, R F1, R F2, bool has_force,
-                                                     R& rho_out, R (&v)[3])
+                                                     R& drho_out, R (&v)[3])
 {
     constexpr int NP = (L::Q - 1) / 2;
     // pass 1: mass, momentum, and the flux about fe
@@ -300,7 +303,7 @@ __host__ __device__ __forceinline__ void les_collide(R (&d)[L::Q], R om0, R tau0
             d[i + 1] = dm;
         }
     }
-    rho_out = rho;
+    drho_out = drho;
 }
 
 // ---------------------------------------------------------------------------
@@ -570,7 +573,7 @@ static_assert(rows_ok(), "closed-form MRT rows disagree with the basis polynomia
 }  // namespace mrt_check
 
 template <class R>
-__host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& rho_out,
+__host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParams& p, R& drho_out,
                                                      R (&v)[3])
 {
     // pair sums and differences; axis pairs 0..2, then the diagonal pairs
@@ -688,7 +691,7 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
         d[2 * q + 1] -= ev[q] + od[q];
         d[2 * q + 2] -= ev[q] - od[q];
     }
-    rho_out = rho;
+    drho_out = drho;
 }
 
 // ---------------------------------------------------------------------------
@@ -864,6 +867,36 @@ __host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, 
     return out;
 }
 
+// Guesses of the guarded alpha modes, from the moments a_k = sum f x^k
+// (ak[0..6]) and A1 = A + a_1:
+//   1  s2: the root of g(alpha)/alpha expanded about 2 to second order for an
+//      f_eq that minimises H (then A = -sum f x ln(1 + x)),
+//      s2 = 2 + (a_3 - 2 a_4) / (3 a_2) + 4 a_3^2 / (9 a_2^2);
+//   2  s2 + scale * out: the surrogate learns what s2 misses;
+//   4  the root of g(alpha)/alpha with g's series truncated after a_6 and the
+//      node's own A (exact for any f_eq; three Newton steps from s2 on
+//      h(a) = A1 + sum_{k=2}^{6} (-1)^k a_k a^(k-1) / (k (k-1))).
+__host__ __device__ __forceinline__ double alpha_guess(const StepParams& p, const float* smlp,
+                                                       const double (&ak)[7], double A1,
+                                                       const double (&feat)[8])
+{
+    const double s2 = 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
+                      4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+    if (p.alpha_mode == 2)
+        return s2 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat);
+    if (p.alpha_mode != 4) return s2;
+    const double c2 = ak[2] * 0.5, c3 = ak[3] * (-1.0 / 6.0), c4 = ak[4] * (1.0 / 12.0),
+                 c5 = ak[5] * (-1.0 / 20.0), c6 = ak[6] * (1.0 / 30.0);
+    double a = s2;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        const double h = fma(a, fma(a, fma(a, fma(a, fma(a, c6, c5), c4), c3), c2), A1);
+        const double hp = fma(a, fma(a, fma(a, fma(a, 5.0 * c6, 4.0 * c5), 3.0 * c4), 2.0 * c3), c2);
+        a -= h / hp;
+    }
+    return a;
+}
+
 struct AlphaResult {
     double alpha;
     int evals;
@@ -872,13 +905,22 @@ struct AlphaResult {
 };
 constexpr int ALPHA_NEEDS_LOG = 100;   // internal: series range left, redo with logs
 
+// Guarded alpha modes: start from a guess, and accept early.
+__host__ __device__ __forceinline__ bool alpha_guarded(int mode)
+{
+    return mode == 1 || mode == 2 || mode == 4;
+}
+
 // Non-trivial root of g in [1, alpha_max) (Eq. alpha_cond) with evaluator ev.
 // Safeguarded Newton keeps a bracket [lo, hi]: g < 0 below the root, >= 0 at
 // or above it (g is convex with g(0) = 0).  If the positivity limit hi is
 // reached with g(hi) < 0 there is no root below it and alpha = hi =
-// alpha_max (1 - 1e-10).  Guarded modes start from a guess (series or MLP),
-// take guard_steps Newton steps and accept when the last correction is below
-// guard_tol * alpha; otherwise the full solve runs from alpha = 2.
+// alpha_max (1 - 1e-10).  Newton starts from alpha = 2, or in the guarded
+// modes from the guess (second-order series, MLP or truncated-series root);
+// these accept the first Newton correction of at most guard_tol * alpha
+// within their first guard_steps evaluations (the corrected alpha is then
+// off by about that correction squared), and otherwise continue from the
+// bracket and iterate they have reached to the tolerance.
 template <class Ev>
 __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const StepParams& p,
                                            double guess, int evals0)
@@ -887,22 +929,8 @@ __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const Step
     double lo = 1.0, hi = amax * (1.0 - 1e-10);
     bool hi_known = false;
     int evals = evals0;
-    if (p.alpha_mode == 1 || p.alpha_mode == 2) {
-        double a = fmin(fmax(guess, lo), hi);
-        double corr = 1e300;
-        for (int k = 0; k < p.guard_steps; ++k) {
-            if (!ev.valid(a)) return AlphaResult{a, evals, ALPHA_NEEDS_LOG};
-            double g, gp;
-            ev(a, g, gp);
-            ++evals;
-            double an = (gp > 0) ? a - g / gp : lo;
-            an = fmin(fmax(an, lo), hi);
-            corr = fabs(an - a);
-            a = an;
-        }
-        if (corr <= p.guard_tol * a) return AlphaResult{a, evals, ALPHA_GUARDED};
-    }
-    double a = 2.0;
+    const bool guarded = alpha_guarded(p.alpha_mode);
+    double a = guarded ? fmin(fmax(guess, lo), hi) : 2.0;
     if (!(a < hi)) a = 0.5 * (lo + hi);
     for (int it = 0; it < p.max_iter; ++it) {
         if (!ev.valid(a)) return AlphaResult{a, evals, ALPHA_NEEDS_LOG};
@@ -913,6 +941,12 @@ __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const Step
         if (g < 0) lo = a;
         else { hi = a; hi_known = true; }
         double an = (gp > 0) ? a - g / gp : -1.0;
+        if (guarded && it < p.guard_steps && an > lo && an < hi &&
+            fabs(an - a) <= p.guard_tol * a) {
+            a = an;
+            r.status = ALPHA_GUARDED;
+            break;
+        }
         // a step below the tolerance is the answer, even when rounding has
         // collapsed the bracket onto the root
         if (gp > 0 && fabs(an - a) <= p.tol * a) { a = an; r.status = ALPHA_CONV; break; }
@@ -951,7 +985,7 @@ __host__ __device__ __forceinline__ double recip_nr(double f)
 // Returns the per-node outcome for the counters.
 template <class L, class R>
 __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const StepParams& p,
-                                                             const float* smlp, R& rho_out,
+                                                             const float* smlp, R& drho_out,
                                                              R (&vout)[3], double (&feat)[8],
                                                              bool& have_feat)
 {
@@ -1034,7 +1068,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     // positivity limit: f_i + a f_i x_i > 0 for all i  <=>  a < -1 / min x
     const double amax = xmin < -1e-30 ? recip_nr(-xmin) : 1e300;
     if (p.alpha_mode != 3 && maxabs >= p.skip_eps && amax < 1e300) {
-        const bool want_feat = (p.alpha_mode == 1 || p.alpha_mode == 2 || p.pairs_X != nullptr);
+        const bool want_feat = alpha_guarded(p.alpha_mode) || p.pairs_X != nullptr;
         double ak[7];
         double A = 0;
         bool solved = false;
@@ -1099,10 +1133,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             if (want_feat) {
                 elbm_features(ak, xmax, xmin, rho, A, feat);
                 have_feat = true;
-                guess = (p.alpha_mode == 2)
-                            ? 2.0 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat) * feat[4]
-                            : 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
-                                  4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+                if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, ev.A1, feat);
             }
             ar = elbm_solve(ev, amax, p, guess, 0);
             solved = (ar.status != ALPHA_NEEDS_LOG);
@@ -1116,6 +1147,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             for (int i = 0; i < L::Q; ++i) {
                 const double Dl = f[i] * x[i];
                 A += Dl * log(f[i] / L::w(i));
+                ak[1] += Dl;
                 const double p2 = Dl * x[i];
                 ak[2] += p2;
                 ak[3] += p2 * x[i];
@@ -1127,10 +1159,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             if (want_feat) {
                 elbm_features(ak, xmax, xmin, rho, A, feat);
                 have_feat = true;
-                guess = (p.alpha_mode == 2)
-                            ? 2.0 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat) * feat[4]
-                            : 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
-                                  4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+                if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, A + ak[1], feat);
             }
             LogEval<L> ev{f, x, A};
             ar = elbm_solve(ev, amax, p, guess, ar.evals);
@@ -1161,7 +1190,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) d[i] = (R)fma(ab, f[i] * x[i], f[i] - L::w(i));
     }
-    rho_out = (R)rho;
+    drho_out = (R)drho;
     vout[0] = (R)(u[0] + 0.5 * p.F[0] * irho);
     vout[1] = (R)(u[1] + 0.5 * p.F[1] * irho);
     vout[2] = (L::D == 3) ? (R)(u[2] + 0.5 * p.F[2] * irho) : R(0);

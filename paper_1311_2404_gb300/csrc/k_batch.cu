@@ -52,9 +52,26 @@ struct BatchParams {
     long long wait_limit;               // spins before giving up
     int withhold;                       // test hooks: 1 CTA 0 skips its first grid-barrier
                                         // arrival; 2 (staged kernel) the first stage of
-                                        // the launch expects 16 bytes that never arrive
+                                        // the launch gets no copies and no arrivals
     int round_nearest;                  // FP16 storage: 1 round to nearest, 0 dither
+    // time-step clock of the stochastic rounding (two slots): a launch of
+    // nsteps steps starting at step t reads t from clock[clock_slot], and
+    // thread 0 of CTA 0 stores t + nsteps into clock[clock_slot ^ 1]
+    unsigned* clock;
+    int clock_slot;
 };
+
+// First step index of this launch from the rounding clock (half-width
+// storage); advances the clock by the launch's steps.
+template <class S>
+__device__ __forceinline__ unsigned batch_clock(const BatchParams& bp)
+{
+    if constexpr (!S::kHalf) return 0u;
+    const unsigned t = bp.clock[bp.clock_slot];
+    if ((blockIdx.x | threadIdx.x | threadIdx.y) == 0)
+        bp.clock[bp.clock_slot ^ 1] = t + (unsigned)bp.nsteps;
+    return t;
+}
 
 // Bounded grid barrier (generation counter).  Returns false when this CTA
 // must stop (its wait ran out, or it withheld its arrival).
@@ -147,19 +164,20 @@ __device__ __forceinline__ void batch_bounce(const DomDev& D, const typename S::
 }
 
 // Collision and store of one node (the single-domain kernel's arithmetic).
+// tsalt: the time step's term of the stochastic-rounding salt, t * kSaltStep
 template <class S>
 __device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams& bp,
                                              typename S::T* __restrict__ B,
                                              float* __restrict__ o, int n, bool out,
-                                             float (&d)[9])
+                                             unsigned tsalt, float (&d)[9])
 {
     using L = D2Q9;
     const int sq = (int)D.sq;
-    float rho, v[3];
-    bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rho, v);
+    float drho, v[3];   // drho = rho - 1, the form the rho output field holds
+    bgk_collide<L, float>(d, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, drho, v);
     if constexpr (S::kHalf) {
         if (!bp.round_nearest) {
-            store_node_sr<L, S>(d, (unsigned)n * kSaltNode,
+            store_node_sr<L, S>(d, (unsigned)n * kSaltNode + tsalt,
                                 [&](int i) { return B + (i * sq + n); });
         } else {
 #pragma unroll
@@ -170,10 +188,10 @@ __device__ __forceinline__ void batch_update(const DomDev& D, const BatchParams&
         for (int i = 0; i < 9; ++i) S::store(B + (i * sq + n), d[i], L::w(i));
     }
     if (out) {
-        o[n] = rho;
+        o[n] = drho;
         o[sq + n] = v[0];
         o[2 * sq + n] = v[1];
-        if (!isfinite(rho) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(bp.status, STATUS_NAN);
+        if (!isfinite(drho) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(bp.status, STATUS_NAN);
     }
 }
 
@@ -194,8 +212,10 @@ __global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
     int4 first = make_int4(0, 0, 0, 0);
     if (t0 < t1) first = bp.tiles[t0];
     int cur = bp.cur;
+    const unsigned clk = batch_clock<S>(bp);
     for (int step = 0; step < bp.nsteps; ++step) {
         const bool out = (step == bp.nsteps - 1);
+        const unsigned tsalt = (clk + (unsigned)step) * kSaltStep;
         int dom = first.x, x0 = first.y, y0 = first.z;
         DomDev D{};
         if (t0 < t1) D = bp.dom[dom];
@@ -223,11 +243,11 @@ __global__ void __launch_bounds__(512) k_batch(const BatchParams bp)
                         if (fl[k] & 0x80u) continue;
                         const int n = y * D.nxp + x;
                         if (fl[k] & FLAG_SOLID) {
-                            if (out) { o[n] = 0.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
+                            if (out) { o[n] = -1.f; o[D.sq + n] = 0.f; o[2 * D.sq + n] = 0.f; }
                             continue;
                         }
                         if (fl[k] & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, x, y, d[k]);
-                        batch_update<S>(D, bp, B, o, n, out, d[k]);
+                        batch_update<S>(D, bp, B, o, n, out, tsalt, d[k]);
                     }
                 }
             }
@@ -287,8 +307,10 @@ __device__ __forceinline__ void batch2_body(const BatchParams& bp)
     int4 first = make_int4(0, 0, 0, 0);
     if (t0 < t1) first = bp.tiles[t0];
     int cur = bp.cur;
+    const unsigned clk = batch_clock<S>(bp);
     for (int step = 0; step < bp.nsteps; ++step) {
         const bool out = (step == bp.nsteps - 1);
+        const unsigned tsalt = (clk + (unsigned)step) * kSaltStep;
         int dom = first.x, x0 = first.y, y0 = first.z;
         DomDev D{};
         if (t0 < t1) D = bp.dom[dom];
@@ -343,7 +365,7 @@ __device__ __forceinline__ void batch2_body(const BatchParams& bp)
                             const unsigned f = (fl[k] >> (8 * c)) & 0xffu;
                             act[c] = !(f & (0x80u | FLAG_SOLID));
                             if (!(f & 0x80u) && (f & FLAG_SOLID) && out) {
-                                o[n + c] = 0.f;
+                                o[n + c] = -1.f;
                                 o[sq + n + c] = 0.f;
                                 o[2 * sq + n + c] = 0.f;
                             }
@@ -355,7 +377,8 @@ __device__ __forceinline__ void batch2_body(const BatchParams& bp)
                         if (act[0] && act[1]) {
                             if constexpr (S::kHalf) {
                                 if (!bp.round_nearest) {
-                                    const unsigned s0 = (unsigned)n * kSaltNode, s1 = s0 + kSaltNode;
+                                    const unsigned s0 = (unsigned)n * kSaltNode + tsalt,
+                                                   s1 = s0 + kSaltNode;
 #pragma unroll
                                     for (int i = 0; i < 9; ++i)
                                         *reinterpret_cast<unsigned*>(B + (i * sq + n)) =
@@ -380,7 +403,7 @@ __device__ __forceinline__ void batch2_body(const BatchParams& bp)
                                 const int m = n + c;
                                 if constexpr (S::kHalf) {
                                     if (!bp.round_nearest) {
-                                        store_node_sr<L, S>(d[k][c], (unsigned)m * kSaltNode,
+                                        store_node_sr<L, S>(d[k][c], (unsigned)m * kSaltNode + tsalt,
                                                             [&](int i) { return B + (i * sq + m); });
                                     } else {
 #pragma unroll
@@ -572,7 +595,7 @@ __host__ __device__ constexpr int halo_slot(int i)
 template <class S>
 __device__ __forceinline__ void stage_issue(const BatchParams& bp, const DomDev& D, int cur, int x0,
                                             int y0, int tw, int th, unsigned char* st,
-                                            unsigned long long* bar, unsigned extra = 0)
+                                            unsigned long long* bar)
 {
     using T = typename S::T;
     constexpr int es = (int)sizeof(T);
@@ -585,7 +608,7 @@ __device__ __forceinline__ void stage_issue(const BatchParams& bp, const DomDev&
     const char* F = bp.base + D.offF;
     const int sq = (int)D.sq;
     if (lane == 0)
-        mbar_arrive_expect_tx(bar, 9u * nrows * rowb + (unsigned)(nrows * ncols) + extra);
+        mbar_arrive_expect_tx(bar, 9u * nrows * rowb + (unsigned)(nrows * ncols));
     for (int c = lane; c < 10 * nrows; c += 32) {
         const int i = c / nrows, r = c - i * nrows;
         if (i < 9) {
@@ -668,7 +691,8 @@ __device__ __forceinline__ bool mbar_wait_abortable(unsigned long long* bar, uns
     return true;
 }
 
-// rho, v of an output step, with the non-finite check
+// rho - 1 and v of an output step, with the non-finite check (the rho field
+// holds the deviation, -1 at solid nodes; readback adds 1 in FP64)
 __device__ __forceinline__ void batch_out(const DomDev& D, const BatchParams& bp,
                                           float* __restrict__ o, int n, float rho,
                                           const float (&v)[3])
@@ -703,7 +727,8 @@ __device__ __forceinline__ void staged_store1(const BatchParams& bp, typename S:
 template <class S>
 __device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev& D, int cur,
                                              int x0, int y0, int tw, int th, int pp, int ty,
-                                             int cy, bool out, const unsigned char* st)
+                                             int cy, bool out, unsigned tsalt,
+                                             const unsigned char* st)
 {
     using T = typename S::T;
     using L = D2Q9;
@@ -735,8 +760,8 @@ __device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev
         const bool la = !(fa & FLAG_SOLID), lb = !(fb & FLAG_SOLID);
         if (!la && !lb) {
             if (out) {
-                o[n] = 0.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f;
-                if (vb) { o[n + 1] = 0.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
+                o[n] = -1.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f;
+                if (vb) { o[n + 1] = -1.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
             }
             continue;
         }
@@ -767,7 +792,7 @@ __device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev
             if (fb & FLAG_NEAR_WALL) batch_bounce<S>(D, A, flags, xa + 1, y, db);
             bgk_collide<L, float>(db, D.omega, D.gx, D.gy, 0.f, D.has_force != 0, rb, vbv);
         }
-        const unsigned s0 = (unsigned)n * kSaltNode, s1 = s0 + kSaltNode;
+        const unsigned s0 = (unsigned)n * kSaltNode + tsalt, s1 = s0 + kSaltNode;
         if (la && lb) {
             if constexpr (S::kHalf) {
                 if (!bp.round_nearest) {
@@ -794,10 +819,10 @@ __device__ __forceinline__ void staged_tile2(const BatchParams& bp, const DomDev
         }
         if (out) {
             if (la) batch_out(D, bp, o, n, ra, va);
-            else { o[n] = 0.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f; }
+            else { o[n] = -1.f; o[sq + n] = 0.f; o[2 * sq + n] = 0.f; }
             if (vb) {
                 if (lb) batch_out(D, bp, o, n + 1, rb, vbv);
-                else { o[n + 1] = 0.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
+                else { o[n + 1] = -1.f; o[sq + n + 1] = 0.f; o[2 * sq + n + 1] = 0.f; }
             }
         }
     }
@@ -836,8 +861,10 @@ __global__ void __launch_bounds__(kStagedMaxThreads + 32) k_batch_staged(const B
     if (t0 < t1) first = bp.tiles[t0];
     unsigned k = 0;                                  // tiles through the ring so far
     int cur = bp.cur;
+    const unsigned clk = batch_clock<S>(bp);
     for (int step = 0; step < bp.nsteps; ++step) {
         const bool out = (step == bp.nsteps - 1);
+        const unsigned tsalt = (clk + (unsigned)step) * kSaltStep;
         int dom = first.x, x0 = first.y, y0 = first.z;
         DomDev D{};
         if (t0 < t1) D = bp.dom[dom];
@@ -851,8 +878,11 @@ __global__ void __launch_bounds__(kStagedMaxThreads + 32) k_batch_staged(const B
                     *abort_v = 1;
                     break;
                 }
-                stage_issue<S>(bp, D, cur, x0, y0, tw, th, smem + s * sb, &full[s],
-                               (bp.withhold == 2 && step == 0 && t == t0) ? 16u : 0u);
+                // test hook 2: the first stage of the launch gets neither copies
+                // nor arrivals, so the consumers' wait for it runs out while no
+                // copy is in flight for it
+                if (!(bp.withhold == 2 && step == 0 && t == t0))
+                    stage_issue<S>(bp, D, cur, x0, y0, tw, th, smem + s * sb, &full[s]);
                 tile_advance(bp, D, dom, x0, y0, tw, t + 1 < t1);
             }
         } else {
@@ -866,7 +896,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads + 32) k_batch_staged(const B
                     *abort_v = 1;
                     break;
                 }
-                staged_tile2<S>(bp, D, cur, x0, y0, tw, th, pp, ty, cy, out, smem + s * sb);
+                staged_tile2<S>(bp, D, cur, x0, y0, tw, th, pp, ty, cy, out, tsalt, smem + s * sb);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
                 tile_advance(bp, D, dom, x0, y0, tw, t + 1 < t1);
@@ -875,7 +905,8 @@ __global__ void __launch_bounds__(kStagedMaxThreads + 32) k_batch_staged(const B
         cur ^= 1;
         if (__syncthreads_or(*abort_v)) {
             // the CTA stops together; the producer first lets the copies it
-            // issued land (bounded), so no copy targets a finished CTA
+            // issued land (bounded), so no copy targets a finished CTA (a
+            // stage whose phase never completes had no copies issued)
             if (producer) {
 #pragma unroll 1
                 for (int s = 0; s < kStages; ++s) {
@@ -918,6 +949,8 @@ struct lbm_batch_ctx {
     int threads = 256, ctas = 0, tw = 128, th = 8, npt = 1;   // launch configuration
     int sms = 0, tiles_tw = 0, tiles_th = 0;          // tiles currently uploaded for (tw, th)
     int cur = 0;
+    int lp = 0;                       // launch parity: the rounding clock's slot holding t
+    unsigned clk_host[2] = {0, 0};    // source of the clock copy after autotuning
     long long t = 0, launches = 0, wait_limit = 20000000LL;
     int withhold = 0;
     int round_nearest = 0;
@@ -1050,6 +1083,8 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
     bp.wait_limit = b->wait_limit;
     bp.withhold = b->withhold;
     bp.round_nearest = b->round_nearest;
+    bp.clock = reinterpret_cast<unsigned*>(b->base + b->off_bar + 16);
+    bp.clock_slot = b->lp;
     cudaError_t e = cudaMemsetAsync(bp.bar, 0, 8, b->stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -1116,6 +1151,8 @@ int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, 
     }
     b->off_tables = o; o = a256(o + sizeof(DomDev) * ndom);
     b->off_tiles = o; o = a256(o + sizeof(int4) * max_tiles);
+    // grid barrier (+0, 8 B), status (+8), rounding clock (+16, two slots),
+    // mask check (+32)
     b->off_bar = o; o = a256(o + 64);
     b->off_stage = o;
     b->stage_bytes = a256(max_nodes * 3 * 8);
@@ -1260,7 +1297,8 @@ static int check_ready(lbm_batch b)
 
 static int step_impl(lbm_batch b, int n)
 {
-    const auto key = std::make_tuple(n, b->cur, b->threads, b->ctas, b->tw, b->th * 8 + b->npt);
+    const auto key = std::make_tuple(n, b->cur * 2 + b->lp, b->threads, b->ctas, b->tw,
+                                     b->th * 8 + b->npt);
     if (b->use_graph && b->stream != nullptr && !b->withhold) {
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
@@ -1285,6 +1323,7 @@ static int step_impl(lbm_batch b, int n)
         if (it != b->graphs.end()) {
             BCK(b, cudaGraphLaunch(it->second, b->stream), "graph launch");
             b->launches += 1;
+            b->lp ^= 1;
             b->cur ^= (n & 1);
             b->t += n;
             return LBM_OK;
@@ -1292,6 +1331,7 @@ static int step_impl(lbm_batch b, int n)
     }
     BCK(b, launch_batch(b, n, b->cur), "persistent batched kernel");
     b->launches += 1;
+    b->lp ^= 1;
     b->cur ^= (n & 1);
     b->t += n;
     return LBM_OK;
@@ -1376,6 +1416,11 @@ int lbm_batch_autotune(lbm_batch b)
     b->tw = bw; b->th = bh;
     BCK(b, cudaMemcpyAsync(b->base, save, span, cudaMemcpyDeviceToDevice, b->stream), "restore");
     BCK(b, cudaMemsetAsync(b->base + b->off_bar, 0, 64, b->stream), "clear status");
+    // the rounding clock resumes at the saved step (both slots)
+    b->clk_host[0] = b->clk_host[1] = (unsigned)saved_t;
+    BCK(b, cudaMemcpyAsync(b->base + b->off_bar + 16, b->clk_host, sizeof b->clk_host,
+                           cudaMemcpyHostToDevice, b->stream),
+        "restore the rounding clock");
     BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
     cudaFree(save);
     b->cur = saved_cur;
@@ -1491,7 +1536,7 @@ int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype)
         const bool dv = dev_ptr(pt.dst);
         void* outp = dv ? pt.dst : stage;
         BCK(b, launch_pack(0, b->base + D.offO + pt.off, f32, outp, pt.nf, D.nx, D.ny, 1, D.nxp,
-                           D.sq, b->stream),
+                           D.sq, pt.off == 0 ? 1.0 : 0.0, b->stream),
             "pack kernel");
         b->launches += 1;
         if (!dv)

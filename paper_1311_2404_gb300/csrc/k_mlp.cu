@@ -1,9 +1,13 @@
 // Training and inference kernels of the ELBM alpha surrogate (not in the
 // paper): an 8 -> 32 -> 32 -> 1 tanh network mapping eight invariants of
-// (f, f_eq - f) to alpha_guess = 2 + scale * out * eps.
+// (f, f_eq - f) to alpha_guess = s2 + scale * out, where s2 is the
+// second-order small-deviation guess written in the features
+// (t_3 = X[0], t_4 = X[1], eps = X[4]):
+//   s2 = 2 + (t_3 eps - 2 t_4 eps^2) / 3 + 4 t_3^2 eps^2 / 9,
+// so the network learns what that expansion misses.
 //
 // Training is minibatch Adam (Kingma & Ba 2015) on the loss
-// mean_b (out_b - t_b)^2, t_b = (alpha_b - 2) / (scale * eps_b), entirely on
+// mean_b (out_b - t_b)^2, t_b = (alpha_b - s2_b) / scale, entirely on
 // the GPU:
 //   k_fwd_bwd   one thread per sample: forward and backward pass in
 //               registers, activations in shared memory, then the CTA sums
@@ -18,7 +22,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 #include <random>
 #include <string>
 #include <vector>
@@ -33,6 +36,13 @@ constexpr int O_W1 = 16, O_B1 = O_W1 + NH * NIN, O_W2 = O_B1 + NH, O_B2 = O_W2 +
               O_W3 = O_B2 + NH, O_B3 = O_W3 + NH, O_SCALE = O_B3 + 1, NPARAM = O_SCALE + 1;
 constexpr int TRAIN_LO = O_W1, NTRAIN = O_SCALE - O_W1;   // 1377 trained entries
 constexpr int BS = 64;                                    // samples per CTA
+
+// second-order guess s2 from a feature row (FP64)
+__device__ __forceinline__ double series2_of(const float* __restrict__ x)
+{
+    const double t3 = x[0], t4 = x[1], eps = x[4];
+    return 2.0 + (t3 * eps - 2.0 * t4 * eps * eps) / 3.0 + 4.0 * t3 * t3 * eps * eps / 9.0;
+}
 
 __global__ void k_forward(const float* __restrict__ X, int n, const float* __restrict__ P,
                           float* __restrict__ alpha)
@@ -59,7 +69,7 @@ __global__ void k_forward(const float* __restrict__ X, int n, const float* __res
         for (int k = 0; k < NH; ++k) s = fmaf(sp[O_W2 + o * NH + k], h1[k], s);
         out = fmaf(sp[O_W3 + o], tanhf(s), out);
     }
-    alpha[b] = 2.0f + sp[O_SCALE] * out * X[(size_t)b * NIN + 4];
+    alpha[b] = (float)(series2_of(X + (size_t)b * NIN) + (double)(sp[O_SCALE] * out));
 }
 
 // idx: sample indices of this minibatch (nullptr: identity); B = minibatch size
@@ -192,7 +202,7 @@ __global__ void k_targets(const float* __restrict__ X, const double* __restrict_
                           float scale, float* __restrict__ t)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < n) t[b] = (float)((alpha[b] - 2.0) / ((double)scale * (double)X[(size_t)b * NIN + 4]));
+    if (b < n) t[b] = (float)((alpha[b] - series2_of(X + (size_t)b * NIN)) / (double)scale);
 }
 
 thread_local std::string g_mlp_err;
@@ -365,30 +375,27 @@ constexpr size_t kOffP = 0, kOffG = kPad, kOffPart = 2 * kPad,
 // 364 KB on every GPU that loads the library, held until the process exits.
 static __device__ __align__(256) float g_mlp_scratch[kStaticFloats];
 
-// Device address of g_mlp_scratch, looked up once per device (the host-side
-// name g_mlp_scratch is only a stand-in and must never be passed to a kernel).
+// Device address of g_mlp_scratch on the current device (the host-side name
+// g_mlp_scratch is only a stand-in and must never be passed to a kernel).
+// Looked up on every call: the lookup allocates nothing, and an address
+// cached across calls would go stale when the device's context is torn
+// down and re-created (cudaDeviceReset), which reloads the module.
 float* static_scratch(int* err)
 {
-    static std::mutex mu;
-    static float* addr[64] = {nullptr};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    if (e != cudaSuccess) {
         *err = 1;
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_mlp_scratch);
-        if (e != cudaSuccess) {
-            *err = 2;
-            g_mlp_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return nullptr;
-        }
-        addr[dev] = static_cast<float*>(p);
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_mlp_scratch);
+    if (e != cudaSuccess) {
+        *err = 2;
+        g_mlp_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return nullptr;
     }
-    return addr[dev];
+    return static_cast<float*>(p);
 }
 
 }  // namespace

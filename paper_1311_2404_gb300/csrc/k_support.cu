@@ -184,11 +184,13 @@ cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, 
 
 // ---------------------------------------------------------------------------
 // Padded compute-type field -> dense caller field (F32 or F64).
-// nfields consecutive planes spaced sq apart in src, N apart in dst.
+// nfields consecutive planes spaced sq apart in src, N apart in dst; `add`
+// is added in FP64 before the conversion (1 for the rho field, which holds
+// the deviation rho - 1; 0 otherwise).
 // ---------------------------------------------------------------------------
 template <class RT, class OT>
 __global__ void k_pack(const RT* __restrict__ src, OT* __restrict__ dst, int nfields, int nx,
-                       int ny, int nz, int nxp, long long sq)
+                       int ny, int nz, int nxp, long long sq, double add)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -197,27 +199,27 @@ __global__ void k_pack(const RT* __restrict__ src, OT* __restrict__ dst, int nfi
     const size_t N = (size_t)nx * ny * nz;
     const size_t nd = ((size_t)z * ny + y) * nx + x;
     const size_t n = ((size_t)z * ny + y) * nxp + x;
-    for (int f = 0; f < nfields; ++f) dst[f * N + nd] = (OT)src[f * sq + n];
+    for (int f = 0; f < nfields; ++f) dst[f * N + nd] = (OT)((double)src[f * sq + n] + add);
 }
 
 cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, int nfields, int nx,
-                        int ny, int nz, int nxp, long long sq, cudaStream_t s)
+                        int ny, int nz, int nxp, long long sq, double add, cudaStream_t s)
 {
     dim3 block(128), grid((nx + 127) / 128, ny, nz);
     if (src_f64) {
         if (dst_f32)
             k_pack<double, float><<<grid, block, 0, s>>>((const double*)src, (float*)dst, nfields,
-                                                         nx, ny, nz, nxp, sq);
+                                                         nx, ny, nz, nxp, sq, add);
         else
             k_pack<double, double><<<grid, block, 0, s>>>((const double*)src, (double*)dst,
-                                                          nfields, nx, ny, nz, nxp, sq);
+                                                          nfields, nx, ny, nz, nxp, sq, add);
     } else {
         if (dst_f32)
             k_pack<float, float><<<grid, block, 0, s>>>((const float*)src, (float*)dst, nfields,
-                                                        nx, ny, nz, nxp, sq);
+                                                        nx, ny, nz, nxp, sq, add);
         else
             k_pack<float, double><<<grid, block, 0, s>>>((const float*)src, (double*)dst,
-                                                         nfields, nx, ny, nz, nxp, sq);
+                                                         nfields, nx, ny, nz, nxp, sq, add);
     }
     return cudaGetLastError();
 }
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256) k_reduce_partial(const RT* __restrict__ r
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const long long n = base + x;
             if (nodes && (nodes[n] & NODE_SOLID)) continue;
-            const double rr = (double)rho[n];
+            const double rr = 1.0 + (double)rho[n];   // the field holds rho - 1
             double ke = 0;
             acc[0] += rr;
             for (int a = 0; a < D; ++a) {

@@ -6,6 +6,7 @@
 //             elements and direction planes padded to 128 elements
 //   flags     node-type map, one byte per (padded) node
 //   rho, u    macroscopic output fields in the compute type, padded layout
+//             (the rho field holds rho - 1; readback adds 1 in FP64)
 //   alpha     ELBM per-node alpha (FP64), ELBM handles only
 //   misc      status word, ELBM counters, reduction scratch, MLP parameters
 //   stage     dense staging for host transfers and dtype conversion
@@ -61,6 +62,7 @@ struct lbm_ctx {
     bool zrun_pick = false;
     double nearwall_frac = 0.0;  // 32-node row segments with a near-wall fluid node
     long long t = 0, launches = 0;
+    unsigned clk_host[2] = {0, 0};   // source of the clock copy in lbm_set_state
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
 };
@@ -71,6 +73,7 @@ enum : size_t {
     MISC_PAIRS = 8,         // int pairs counter
     MISC_BAD = 16,          // int: mask value out of range
     MISC_NEARWALL = 20,     // unsigned: near-wall row segments (geometry statistics)
+    MISC_STEP = 32,         // 2 unsigned: time-step clock of the stochastic rounding
     MISC_RED = 64,          // 5 doubles reduction result
     MISC_CTR_OUT = 128,     // 9 doubles: combined counters
     MISC_CTR = 256,         // kCtrReplicas x kCtrStride unsigned long long counter replicas
@@ -446,7 +449,7 @@ int lbm_set_elbm(lbm_handle h, int alpha_mode, double tol, int max_iter, double 
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
     if (h->model != LBM_ELBM) return fail(h, LBM_EINVAL, "not an ELBM handle");
-    if (alpha_mode < 0 || alpha_mode > 3) return fail(h, LBM_EINVAL, "bad alpha mode");
+    if (alpha_mode < 0 || alpha_mode > 4) return fail(h, LBM_EINVAL, "bad alpha mode");
     if (!(tol > 0) || max_iter < 1 || max_iter > 200 || !(skip_eps >= 0))
         return fail(h, LBM_EINVAL, "bad tolerance / iteration cap / skip threshold");
     h->alpha_mode = alpha_mode; h->tol = tol; h->max_iter = max_iter; h->skip_eps = skip_eps;
@@ -589,6 +592,9 @@ static StepParams make_params(lbm_ctx* h)
     p.zrun = (h->has_mask && h->D == 3 && !h->aa &&
               (h->masked_kernel == 2 || (h->masked_kernel == 0 && h->zrun_pick))) ? 8 : 0;
     p.salt_off = 0;
+    // the clock of the stochastic rounding (half-width storage only)
+    p.step_ctr = h->esize == 2 ? at<unsigned>(h, h->off_misc + MISC_STEP) : nullptr;
+    p.step_slot = 0;
     p.omega = 1.0 / h->tau;
     p.F[0] = h->F[0]; p.F[1] = h->F[1]; p.F[2] = h->F[2];
     p.has_force = (h->F[0] != 0.0 || h->F[1] != 0.0 || h->F[2] != 0.0);
@@ -634,6 +640,10 @@ static cudaError_t launch_one(lbm_ctx* h, StepParams& p, int from, bool out)
         p.Bp[i] = static_cast<char*>(p.B) + (size_t)i * h->sq * h->esize;
     }
     p.out = out ? 1 : 0;
+    // the clock slot that holds t: AB alternates buffers and slots together
+    // (both slots hold t after lbm_set_state, whose state sits in A), AA
+    // steps alternate with the parity of t
+    p.step_slot = from;
     const bool mask = h->has_mask;
     const bool aa = h->aa;
     const int lat = h->lattice;
@@ -687,7 +697,10 @@ int lbm_step(lbm_handle h, int n)
                 from ^= 1;
             }
             cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
-            if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
+            if (le != cudaSuccess) {
+                if (ce == cudaSuccess) cudaGraphDestroy(g);
+                return cuda_fail(h, le, "launch during capture");
+            }
             CK(h, ce, "end capture");
             cudaGraphExec_t ge;
             cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
@@ -725,7 +738,7 @@ static int get_field(lbm_ctx* h, size_t src_off, int nfields, void* dst, int fie
     void* view = const_cast<void*>(kernel_view(dst));
     void* out = view ? view : h->base + h->off_stage;
     CK(h, launch_pack(h->rsize == 8, h->base + src_off, dst_f32, out, nfields, h->nx, h->ny,
-                      h->nz, h->nxp, h->sq, h->stream),
+                      h->nz, h->nxp, h->sq, src_off == h->off_rho ? 1.0 : 0.0, h->stream),
        "pack kernel");
     h->launches += 1;
     if (!view)
@@ -754,7 +767,7 @@ int lbm_get_alpha(lbm_handle h, double* alpha)
     const bool dev = is_device_ptr(alpha);
     void* out = dev ? (void*)alpha : h->base + h->off_stage;
     CK(h, launch_pack(1, h->base + h->off_alpha, 0, out, 1, h->nx, h->ny, h->nz, h->nxp, h->sq,
-                      h->stream),
+                      0.0, h->stream),
        "pack kernel");
     h->launches += 1;
     if (!dev)
@@ -877,6 +890,11 @@ int lbm_set_state(lbm_handle h, const void* src, long long t)
     const size_t nb = lbm_state_bytes(h);
     CK(h, cudaMemcpyAsync(h->base + h->off_A, src, nb, cudaMemcpyDefault, h->stream),
        "copy state");
+    // the rounding clock resumes at t (both slots: the next step may read either)
+    h->clk_host[0] = h->clk_host[1] = (unsigned)t;
+    CK(h, cudaMemcpyAsync(h->base + h->off_misc + MISC_STEP, h->clk_host, sizeof h->clk_host,
+                          cudaMemcpyHostToDevice, h->stream),
+       "set the rounding clock");
     CK(h, cudaStreamSynchronize(h->stream), "synchronise");
     // AB: the state now sits in A.  AA: one array, whose placement is fixed
     // by the parity of t (the step after an even t is a pull/push step).
@@ -960,6 +978,13 @@ struct lbm_multi_ctx {
     size_t face_bytes = 0;       // one face: ndir runs of one row
     size_t off_send = 0, off_recv = 0, off_tab = 0, off_scr = 0, scr_bytes = 0;
     int nseg = 0;                // segments per table (2 S ndir)
+    // one slab of a decomposition across processes (lbm_multi_create_rank):
+    // the handle holds slab `rank` of `nsub_global`; its faces go to and come
+    // from the neighbouring ranks through the caller, between
+    // lbm_multi_step_begin and lbm_multi_step_end
+    bool rank_mode = false;
+    int rank = 0, nsub_global = 1;
+    bool begun = false;          // between lbm_multi_step_begin and _end
     long long t = 0, launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::string err;
@@ -1057,12 +1082,29 @@ static int multi_build_tables(lbm_multi_ctx* m)
     return LBM_OK;
 }
 
-// The exchange after a step whose new state is in buffer `parity`.
+// The exchange after a step whose new state is in buffer `parity`, in three
+// parts: collect (boundary rows -> send buffers), transfer (send -> receive
+// buffers: the slot of face (s, f) holds, on the receiving side, the face
+// that lands in the neighbour's ghost row), distribute (receive buffers ->
+// ghost rows).  A rank handle of a decomposition over several processes
+// leaves the transfer to its caller.
+static cudaError_t multi_collect(lbm_multi_ctx* m, int parity, cudaStream_t s)
+{
+    return launch_halo_copy(mtable(m, parity, 0), m->nseg, m->layer * (long long)m->esize / 16,
+                            s);
+}
+
+static cudaError_t multi_distribute(lbm_multi_ctx* m, int parity, cudaStream_t s)
+{
+    return launch_halo_copy(mtable(m, parity, 1), m->nseg, m->layer * (long long)m->esize / 16,
+                            s);
+}
+
 static cudaError_t multi_exchange(lbm_multi_ctx* m, int parity, cudaStream_t s)
 {
     const long long n16 = m->layer * (long long)m->esize / 16;
     if (m->direct) return launch_halo_copy(mtable(m, parity, 2), m->nseg, n16, s);
-    cudaError_t e = launch_halo_copy(mtable(m, parity, 0), m->nseg, n16, s);
+    cudaError_t e = multi_collect(m, parity, s);
     if (e != cudaSuccess) return e;
     // transfer: face (s, f) goes to its receiver's buffer slot of the same index
     for (int sd = 0; sd < m->S; ++sd)
@@ -1072,7 +1114,7 @@ static cudaError_t multi_exchange(lbm_multi_ctx* m, int parity, cudaStream_t s)
                                 m->face_bytes, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
         }
-    return launch_halo_copy(mtable(m, parity, 1), m->nseg, n16, s);
+    return multi_distribute(m, parity, s);
 }
 
 static cudaError_t multi_rows(lbm_multi_ctx* m, int s, int row0, int nrows, bool out, int from)
@@ -1142,10 +1184,10 @@ static int gather_rows(lbm_multi_ctx* m, const char* src, char* dst, int lo, int
     return LBM_OK;
 }
 
-extern "C" {
-
-int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
-                     int nsub, lbm_multi* out)
+// All nsub slabs on this GPU (rank < 0), or only slab `rank` of them (a rank
+// handle: S = 1 local slab with its global rows).
+static int multi_create_impl(int nx, int ny, int nz, int lattice, int model, double tau,
+                             int dtype, int nsub, int rank, lbm_multi* out)
 {
     if (!out) return mfail(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1155,13 +1197,20 @@ int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau,
         return mfail(nullptr, LBM_EINVAL,
                      "need 1 <= subdomains <= rows of the decomposed axis (%d), got %d", axis_n,
                      nsub);
+    if (rank >= nsub)
+        return mfail(nullptr, LBM_EINVAL, "rank %d outside 0..%d", rank, nsub - 1);
     lbm_multi_ctx* m = new lbm_multi_ctx();
-    m->nx = nx; m->ny = ny; m->nz = nz; m->lattice = lattice; m->D = D; m->S = nsub;
+    m->nx = nx; m->ny = ny; m->nz = nz; m->lattice = lattice; m->D = D;
+    m->S = rank < 0 ? nsub : 1;
     m->dtype = dtype; m->axis_n = axis_n;
-    for (int s = 0; s < nsub; ++s) {
+    m->rank_mode = rank >= 0;
+    m->rank = rank < 0 ? 0 : rank;
+    m->nsub_global = nsub;
+    for (int s = rank < 0 ? 0 : rank; s < (rank < 0 ? nsub : rank + 1); ++s) {
         m->lo.push_back((int)((long long)axis_n * s / nsub));
         m->hi.push_back((int)((long long)axis_n * (s + 1) / nsub));
     }
+    nsub = m->S;   // local slabs from here on
     for (int s = 0; s < nsub; ++s) {
         const int nloc = m->hi[s] - m->lo[s];
         lbm_handle h = nullptr;
@@ -1229,6 +1278,21 @@ int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau,
     }
     *out = m;
     return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_multi_create(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
+                     int nsub, lbm_multi* out)
+{
+    return multi_create_impl(nx, ny, nz, lattice, model, tau, dtype, nsub, -1, out);
+}
+
+int lbm_multi_create_rank(int nx, int ny, int nz, int lattice, int model, double tau, int dtype,
+                          int nsub, int rank, lbm_multi* out)
+{
+    if (rank < 0) return mfail(nullptr, LBM_EINVAL, "rank must be >= 0 (got %d)", rank);
+    return multi_create_impl(nx, ny, nz, lattice, model, tau, dtype, nsub, rank, out);
 }
 
 int lbm_multi_destroy(lbm_multi m)
@@ -1378,6 +1442,10 @@ int lbm_multi_step(lbm_multi m, int n)
     if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
     if (n < 1) return mfail(m, LBM_EINVAL, "n must be >= 1 (got %d)", n);
     if (!m->inited) return mfail(m, LBM_ESTATE, "the initial state must precede stepping");
+    if (m->begun) return mfail(m, LBM_ESTATE, "a step begun with lbm_multi_step_begin is open");
+    if (m->rank_mode && m->nsub_global > 1)
+        return mfail(m, LBM_ESTATE, "a rank of a decomposition over %d processes steps with "
+                                    "lbm_multi_step_begin / lbm_multi_step_end", m->nsub_global);
     for (auto* h : m->sub) {
         int r = check_step_ready(h);
         if (r) return msub(m, h, r);
@@ -1397,8 +1465,10 @@ int lbm_multi_step(lbm_multi m, int n)
                 from ^= 1;
             }
             cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
-            if (le != cudaSuccess)
+            if (le != cudaSuccess) {
+                if (ce == cudaSuccess) cudaGraphDestroy(g);
                 return mfail(m, LBM_ECUDA, "launch during capture: %s", cudaGetErrorString(le));
+            }
             MCK(m, ce, "end capture");
             cudaGraphExec_t ge;
             cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
@@ -1431,6 +1501,7 @@ int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype)
     if (field_dtype != LBM_FIELD_F64 && field_dtype != LBM_FIELD_F32)
         return mfail(m, LBM_EINVAL, "unknown field dtype %d", field_dtype);
     if (m->t == 0) return mfail(m, LBM_ESTATE, "no step has produced output yet");
+    if (m->begun) return mfail(m, LBM_ESTATE, "a step begun with lbm_multi_step_begin is open");
     const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
     const size_t rowb = (size_t)m->layer_dense * fs;
     const size_t ntot = (size_t)m->axis_n * rowb;
@@ -1446,7 +1517,7 @@ int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype)
             const int nc = fld == 0 ? 1 : m->D;
             MCK(m, launch_pack(h->rsize == 8, h->base + (fld == 0 ? h->off_rho : h->off_u),
                                field_dtype == LBM_FIELD_F32, scr, nc, h->nx, h->ny, h->nz, h->nxp,
-                               h->sq, m->stream),
+                               h->sq, fld == 0 ? 1.0 : 0.0, m->stream),
                 "pack kernel");
             m->launches += 1;
             for (int c = 0; c < nc; ++c)
@@ -1461,6 +1532,77 @@ int lbm_multi_get_macro(lbm_multi m, void* rho, void* u, int field_dtype)
         int r = sync_status(h);
         if (r) return msub(m, h, r);
     }
+    return LBM_OK;
+}
+
+int lbm_multi_step_begin(lbm_multi m, int output)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!m->rank_mode) return mfail(m, LBM_EINVAL, "not a rank handle (lbm_multi_create_rank)");
+    if (!m->inited) return mfail(m, LBM_ESTATE, "the initial state must precede stepping");
+    if (m->begun) return mfail(m, LBM_ESTATE, "the previous step has not ended");
+    lbm_ctx* h = m->sub[0];
+    int r = check_step_ready(h);
+    if (r) return msub(m, h, r);
+    const int from = h->cur, to = from ^ 1;
+    const bool out = output != 0;
+    const int nloc = m->hi[0] - m->lo[0];
+    // the boundary rows, whose faces leave; the collect follows them on the
+    // exchange stream while the bulk rows update
+    if (m->overlap) {
+        MCK(m, multi_rows(m, 0, 1, 1, out, from), "boundary row");
+        if (nloc > 1) MCK(m, multi_rows(m, 0, nloc, 1, out, from), "boundary row");
+    } else {
+        MCK(m, multi_rows(m, 0, 1, nloc, out, from), "slab");
+    }
+    MCK(m, cudaEventRecord(m->ev_bnd, m->stream), "event");
+    MCK(m, cudaStreamWaitEvent(m->comm, m->ev_bnd, 0), "event wait");
+    MCK(m, multi_collect(m, to, m->comm), "collect kernel");
+    if (m->overlap && nloc > 2) MCK(m, multi_rows(m, 0, 2, nloc - 2, out, from), "bulk rows");
+    m->launches += 1 + (m->overlap ? (nloc > 1) + (nloc > 2) : 0);
+    m->begun = true;
+    return LBM_OK;
+}
+
+int lbm_multi_step_end(lbm_multi m)
+{
+    if (!m) return mfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!m->begun) return mfail(m, LBM_ESTATE, "no step was begun");
+    lbm_ctx* h = m->sub[0];
+    MCK(m, multi_distribute(m, h->cur ^ 1, m->comm), "distribute kernel");
+    MCK(m, cudaEventRecord(m->ev_halo, m->comm), "event");
+    MCK(m, cudaStreamWaitEvent(m->stream, m->ev_halo, 0), "event wait");
+    m->launches += 1;
+    h->cur ^= 1;
+    h->t += 1;
+    h->have_out = true;
+    m->t += 1;
+    m->begun = false;
+    return LBM_OK;
+}
+
+int lbm_multi_face_buffers(lbm_multi m, void** send, void** recv, size_t* face_bytes)
+{
+    if (!m || !send || !recv || !face_bytes) return mfail(m, LBM_EINVAL, "NULL argument");
+    if (!m->rank_mode) return mfail(m, LBM_EINVAL, "not a rank handle (lbm_multi_create_rank)");
+    *send = m->mem + m->off_send;
+    *recv = m->mem + m->off_recv;
+    *face_bytes = m->face_bytes;
+    return LBM_OK;
+}
+
+int lbm_multi_exchange_stream(lbm_multi m, void** stream)
+{
+    if (!m || !stream) return mfail(m, LBM_EINVAL, "NULL argument");
+    *stream = m->comm;
+    return LBM_OK;
+}
+
+int lbm_multi_rows(lbm_multi m, int* lo, int* hi)
+{
+    if (!m || !lo || !hi) return mfail(m, LBM_EINVAL, "NULL argument");
+    *lo = m->lo.front();
+    *hi = m->hi.back();
     return LBM_OK;
 }
 

@@ -145,13 +145,19 @@ static_assert(lattice_ok<D3Q27>(6, 12, 8), "D3Q27 table");
 // fraction the narrowing drops, subnormals and values below the smallest
 // subnormal included, and passes Inf and NaN through.  Its random bits come
 // from a multiplicative hash of each value's own 32 bits with an odd
-// multiplier per direction, salted with the node index, so no counter is
-// needed and CUDA-graph replay, the batched kernel and subdomain runs
-// reproduce results exactly.  With the direction a compile-time constant the
-// hash is one integer multiply-add per value.  Two values share one
-// conversion; each element takes 13 (FP16) or 16 (BF16) high bits of its own
-// hash (the instruction reads bits 16.. of the word for the first element,
-// bits 0.. for the second).
+// multiplier per direction, salted with the node index and the time step:
+//   hash = bits * M_dir + n * kSaltNode + t * kSaltStep   (mod 2^32).
+// The step term matters at a steady state, where the same value recurs at a
+// node step after step: a hash of the value and the node alone would repeat
+// the same rounding every step (a fixed point of the rounded map, short of
+// the true steady state), while t * kSaltStep walks the hash's top bits
+// through a Weyl sequence, so the rounding errors average out over steps.
+// t is read on the device (step_salt below), so CUDA-graph replay, the
+// batched kernel and subdomain runs reproduce results exactly.  With the
+// direction a compile-time constant the hash is one integer multiply-add per
+// value.  Two values share one conversion; each element takes 13 (FP16) or
+// 16 (BF16) high bits of its own hash (the instruction reads bits 16.. of
+// the word for the first element, bits 0.. for the second).
 __host__ __device__ constexpr unsigned dither_mul(int dir)
 {
     return 0x9E3779B1u + (unsigned)dir * 0x3C6EF372u;   // odd for every dir
@@ -161,6 +167,7 @@ __device__ __forceinline__ unsigned dither_hash(unsigned bits, unsigned salt, in
     return bits * dither_mul(dir) + salt;
 }
 constexpr unsigned kSaltNode = 0x85EBCA77u;
+constexpr unsigned kSaltStep = 0x9E3779B9u;   // 2^32 (sqrt(5) - 1) / 2, odd
 
 // random word for a pair: high 16 bits of a's hash in the high half, of b's
 // hash in the low half, shifted right by `sh` so that a field of 16 - sh bits
@@ -339,6 +346,13 @@ struct StepParams {
     int row0, nrows;           // rows updated: z layers (3-D lattices) or y rows (D2Q9)
     int zrun;                  // z layers per thread of the masked z-run kernel (set at launch)
     int salt_off;              // node-index offset of the dither salt (subdomains)
+    // time-step clock of the stochastic rounding: the launch that takes step
+    // t reads t from step_ctr[step_slot] and one of its threads stores t + 1
+    // into step_ctr[step_slot ^ 1] (several launches of one step, e.g. the
+    // row ranges of a subdomain, store the same value); nullptr for storage
+    // types without stochastic rounding
+    unsigned* step_ctr;
+    int step_slot;
     double omega;              // 1/tau
     double F[3];               // body force
     double mrt_c[19];          // s_k / |M_k|^2
@@ -358,6 +372,20 @@ struct StepParams {
     double tol, skip_eps, guard_tol;
     const float* mlp;          // MLP_NPARAM floats (BF16-rounded weights)
 };
+
+// Salt term of the launch's time step for the stochastic-rounding hash:
+// t * kSaltStep + salt_off * kSaltNode, so that node n's salt is
+// n * kSaltNode + step_salt(p).  Reads t from the step clock; thread 0 of
+// block 0 stores t + 1 into the clock's other slot for the next step (no
+// thread of this launch reads that slot).  0 without a clock.
+__device__ __forceinline__ unsigned step_salt(const StepParams& p)
+{
+    if (!p.step_ctr) return (unsigned)p.salt_off * kSaltNode;
+    const unsigned t = p.step_ctr[p.step_slot];
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0)
+        p.step_ctr[p.step_slot ^ 1] = t + 1;
+    return t * kSaltStep + (unsigned)p.salt_off * kSaltNode;
+}
 
 // Parameter in the compute type: the FP32 copy for float, FP64 for double.
 template <class R>

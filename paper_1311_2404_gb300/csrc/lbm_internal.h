@@ -57,8 +57,10 @@ cudaError_t launch_flags(int lattice, const uint8_t* dense, uint32_t* words, uin
 cudaError_t launch_init(int lattice, int store, const void* rho, const void* u, int field_f32,
                         void* A, int nx, int ny, int nz, int nxp, long long sq, int entropic,
                         int feq_variant, int opposite_slots, cudaStream_t s);
+// `add` is added to every value in FP64 (1 for the rho field, which holds
+// rho - 1)
 cudaError_t launch_pack(int src_f64, const void* src, int dst_f32, void* dst, int nfields, int nx,
-                        int ny, int nz, int nxp, long long sq, cudaStream_t s);
+                        int ny, int nz, int nxp, long long sq, double add, cudaStream_t s);
 cudaError_t launch_reduce(int f64, const void* rho, const void* u, const uint32_t* nodes, int D,
                           int nx, int ny, int nz, int nxp, long long sq, double* partials,
                           double* out, cudaStream_t s);

@@ -10,7 +10,9 @@
 // e_x = 0 directions and all writes are aligned, fully coalesced rows; the
 // e_x = +-1 reads are shifted by one element and touch one extra 32-byte
 // sector per warp row, which the L2 serves (DRAM moves each byte once).
-// On output steps the same pass writes rho and v (Eq. edm_momentum).
+// On output steps the same pass writes rho and v (Eq. edm_momentum); the rho
+// field holds the deviation rho - 1 (solid nodes: -1, i.e. rho = 0), which
+// readback turns into rho in FP64.
 //
 // AA pattern (one array, Sec. 3.3): the post-collision values alternate
 // between two placements.  A pull/push step (even t) reads f_i(x) from slot
@@ -50,6 +52,8 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
     const int y = (L::D == 2) ? p.row0 + yb : yb;
     const int z = (L::D == 3) ? p.row0 + (int)blockIdx.z : 0;
     bool active = (x < p.nx) && ((L::D == 2) ? (yb < p.nrows) : (y < p.ny));
+    unsigned tsalt = 0;   // the time step's term of the stochastic-rounding salt
+    if constexpr (S::kHalf) tsalt = step_salt(p);
     const int plane = p.ny * p.nxp;
     const int n = z * plane + y * p.nxp + x;
     // The node-type byte and the q populations are loaded independently: the
@@ -83,7 +87,7 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
     }
     if (active && (fl & NODE_SOLID)) {
         if (p.out) {
-            static_cast<R*>(p.rho)[n] = R(0);
+            static_cast<R*>(p.rho)[n] = R(-1);
 #pragma unroll
             for (int a = 0; a < L::D; ++a) static_cast<R*>(p.u)[a * p.sq + n] = R(0);
             if (ELBM && p.alpha_out) p.alpha_out[n] = 0.0;
@@ -93,7 +97,7 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
             for (int i = 0; i < L::Q; ++i) d[i] = R(0);
             if constexpr (S::kHalf) {
                 if (!p.round_nearest) {
-                    store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode,
+                    store_node_sr<L, S>(d, (unsigned)n * kSaltNode + tsalt,
                                         [&](int i) { return Bi(i) + n; });
                 } else {
 #pragma unroll
@@ -127,23 +131,23 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
             bc_apply<L, R>(d, p.bc[(fl >> NODE_BC_SHIFT) - 1],
                            sel<R>(p.F_f[0], p.F[0]), sel<R>(p.F_f[1], p.F[1]),
                            sel<R>(p.F_f[2], p.F[2]));
-        R rho, v[3];
+        R drho, v[3];
         double feat[8];
         bool have_feat = false;
         AlphaResult ar{2.0, 0, -1};
         if (MODEL == MODEL_BGK) {
             bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
                               sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
-                              p.has_force != 0, rho, v);
+                              p.has_force != 0, drho, v);
         } else if (MODEL == MODEL_MRT) {
-            if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+            if constexpr (L::Q == 19) mrt_collide<R>(d, p, drho, v);
         } else if (MODEL == MODEL_REG || MODEL == MODEL_SMAG) {
             les_collide<L, R, MODEL == MODEL_SMAG>(
                 d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
                 sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
-                sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho, v);
+                sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, drho, v);
         } else {
-            ar = elbm_collide<L, R>(d, p, smlp, rho, v, feat, have_feat);
+            ar = elbm_collide<L, R>(d, p, smlp, drho, v, feat, have_feat);
             evals = ar.evals;
             astat = ar.status;
             resid = ar.resid;
@@ -158,7 +162,7 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
         };
         if constexpr (S::kHalf) {
             if (!p.round_nearest) {
-                store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode, dst);
+                store_node_sr<L, S>(d, (unsigned)n * kSaltNode + tsalt, dst);
             } else {
 #pragma unroll
                 for (int i = 0; i < L::Q; ++i) S::store(dst(i), d[i], L::w(i));
@@ -168,10 +172,10 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
             for (int i = 0; i < L::Q; ++i) S::store(dst(i), d[i], L::w(i));
         }
         if (p.out) {
-            static_cast<R*>(p.rho)[n] = rho;
+            static_cast<R*>(p.rho)[n] = drho;
 #pragma unroll
             for (int a = 0; a < L::D; ++a) static_cast<R*>(p.u)[a * p.sq + n] = v[a];
-            bool bad = !isfinite((float)rho);
+            bool bad = !isfinite((float)drho);
 #pragma unroll
             for (int a = 0; a < L::D; ++a) bad |= !isfinite((float)v[a]);
             if (bad) atomicOr(p.status, STATUS_NAN);
@@ -285,6 +289,8 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
     static_assert(opp_adjacent<L>(), "slot opp(i) must be plane i + 1 or i - 1");
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    unsigned tsalt = 0;   // the time step's term of the stochastic-rounding salt
+    if constexpr (S::kHalf) tsalt = step_salt(p);
     if (x >= p.nx || y >= p.ny) return;
     const int zb = p.row0 + (int)blockIdx.z * p.zrun;
     const int ze = min(zb + p.zrun, p.row0 + p.nrows);
@@ -304,7 +310,7 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
         const bool solid = (fl & NODE_SOLID) != 0;
         if (solid && !(fl & NODE_FILL)) {
             if (p.out) {
-                static_cast<R*>(p.rho)[n] = R(0);
+                static_cast<R*>(p.rho)[n] = R(-1);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) static_cast<R*>(p.u)[a * p.sq + n] = R(0);
             }
@@ -313,7 +319,7 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
         // fluid nodes update; solid nodes that share a sector with one take
         // the same store instructions with the rest state (NODE_FILL)
         R d[L::Q];
-        R rho = R(0), v[3] = {R(0), R(0), R(0)};
+        R drho = R(-1), v[3] = {R(0), R(0), R(0)};
         if (!solid) {
             const int zm = z == 0 ? p.nz - 1 : z - 1;
             const int zp = z == p.nz - 1 ? 0 : z + 1;
@@ -332,14 +338,14 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
             if (MODEL == MODEL_BGK) {
                 bgk_collide<L, R>(d, sel<R>(p.omega_f, p.omega), sel<R>(p.F_f[0], p.F[0]),
                                   sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]),
-                                  p.has_force != 0, rho, v);
+                                  p.has_force != 0, drho, v);
             } else if (MODEL == MODEL_MRT) {
-                if constexpr (L::Q == 19) mrt_collide<R>(d, p, rho, v);
+                if constexpr (L::Q == 19) mrt_collide<R>(d, p, drho, v);
             } else {
                 les_collide<L, R, MODEL == MODEL_SMAG>(
                     d, sel<R>(p.omega_f, p.omega), sel<R>(p.tau_f, p.tau),
                     sel<R>(p.smag_cs2_f, p.smag_cs2), sel<R>(p.F_f[0], p.F[0]),
-                    sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, rho,
+                    sel<R>(p.F_f[1], p.F[1]), sel<R>(p.F_f[2], p.F[2]), p.has_force != 0, drho,
                     v);
             }
         } else {
@@ -348,7 +354,7 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
         }
         if constexpr (S::kHalf) {
             if (!p.round_nearest) {
-                store_node_sr<L, S>(d, (unsigned)(n + p.salt_off) * kSaltNode,
+                store_node_sr<L, S>(d, (unsigned)n * kSaltNode + tsalt,
                                     [&](int i) { return Bi(i) + n; });
             } else {
 #pragma unroll
@@ -359,10 +365,10 @@ __device__ __forceinline__ void zrun_body(const StepParams& p)
             for (int i = 0; i < L::Q; ++i) S::store(Bi(i) + n, d[i], L::w(i));
         }
         if (p.out) {
-            static_cast<R*>(p.rho)[n] = rho;
+            static_cast<R*>(p.rho)[n] = drho;
 #pragma unroll
             for (int a = 0; a < 3; ++a) static_cast<R*>(p.u)[a * p.sq + n] = v[a];
-            bad |= !isfinite((float)rho);
+            bad |= !isfinite((float)drho);
 #pragma unroll
             for (int a = 0; a < 3; ++a) bad |= !isfinite((float)v[a]);
         }
@@ -397,6 +403,7 @@ __device__ __forceinline__ void x2_body(const StepParams& p)
     const int yb = blockIdx.y * blockDim.y + threadIdx.y;
     const int y = (L::D == 2) ? p.row0 + yb : yb;
     const int z = (L::D == 3) ? p.row0 + (int)blockIdx.z : 0;
+    const unsigned tsalt = step_salt(p);   // the time step's term of the salt
     if (!(x0 < p.nx && ((L::D == 2) ? (yb < p.nrows) : (y < p.ny)))) return;
     const int nx = p.nx, x1 = x0 + 1;
     const int plane = p.ny * p.nxp;
@@ -430,7 +437,7 @@ __device__ __forceinline__ void x2_body(const StepParams& p)
             d[1][i] = S::load(Ai(i) + rs + cx[1][1 - L::ex(i)], L::w(i));
         }
     }
-    R rho[2], v[2][3];
+    R drho[2], v[2][3];
     bool bad = false;
     // wr: the node's slots are written (fluid, or a solid node that shares a
     // sector with a fluid one and takes the rest state, NODE_FILL)
@@ -457,16 +464,16 @@ __device__ __forceinline__ void x2_body(const StepParams& p)
                            p.F_f[0], p.F_f[1], p.F_f[2]);
         if (MODEL == MODEL_BGK) {
             bgk_collide<L, R>(d[k], p.omega_f, p.F_f[0], p.F_f[1], p.F_f[2], p.has_force != 0,
-                              rho[k], v[k]);
+                              drho[k], v[k]);
         } else if (MODEL == MODEL_MRT) {
-            if constexpr (L::Q == 19) mrt_collide<R>(d[k], p, rho[k], v[k]);
+            if constexpr (L::Q == 19) mrt_collide<R>(d[k], p, drho[k], v[k]);
         } else {
             les_collide<L, R, MODEL == MODEL_SMAG>(d[k], p.omega_f, p.tau_f, p.smag_cs2_f,
                                                    p.F_f[0], p.F_f[1], p.F_f[2],
-                                                   p.has_force != 0, rho[k], v[k]);
+                                                   p.has_force != 0, drho[k], v[k]);
         }
     }
-    const unsigned s0 = (unsigned)(n0 + p.salt_off) * kSaltNode, s1 = s0 + kSaltNode;
+    const unsigned s0 = (unsigned)n0 * kSaltNode + tsalt, s1 = s0 + kSaltNode;
     if (wr[0] && wr[1]) {
         if (!p.round_nearest) {
 #pragma unroll
@@ -499,11 +506,11 @@ __device__ __forceinline__ void x2_body(const StepParams& p)
             const int n = n0 + k;
             if (k == 1 && x1 >= nx) continue;
             const bool a = act[k];
-            static_cast<R*>(p.rho)[n] = a ? rho[k] : R(0);
+            static_cast<R*>(p.rho)[n] = a ? drho[k] : R(-1);
 #pragma unroll
             for (int c = 0; c < L::D; ++c) static_cast<R*>(p.u)[c * p.sq + n] = a ? v[k][c] : R(0);
             if (a) {
-                bad |= !isfinite(rho[k]);
+                bad |= !isfinite(drho[k]);
 #pragma unroll
                 for (int c = 0; c < L::D; ++c) bad |= !isfinite(v[k][c]);
             }

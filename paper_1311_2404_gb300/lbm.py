@@ -29,19 +29,8 @@ if not os.path.exists(LIB_PATH):
 _L = ctypes.CDLL(LIB_PATH)
 
 # ---- constants (mirror include/lbm.h) -------------------------------------
-LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ENOCONV = range(8)
-LBM_D2Q9, LBM_D3Q19, LBM_D3Q15, LBM_D3Q27 = 0, 1, 2, 3
-LBM_BGK, LBM_MRT, LBM_ELBM, LBM_REG, LBM_SMAG = 0, 1, 2, 3, 4
-LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S = range(5)
-LBM_FIELD_F64, LBM_FIELD_F32 = 0, 1
-LBM_ALPHA_NEWTON, LBM_ALPHA_SERIES_GUARDED, LBM_ALPHA_MLP_GUARDED, LBM_ALPHA_FIXED2 = range(4)
-LBM_ROUND_DITHER, LBM_ROUND_NEAREST = 0, 1
-LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
-LBM_MASKED_AUTO, LBM_MASKED_NODE, LBM_MASKED_ZRUN = 0, 1, 2
-LBM_TRANSFER_STAGED, LBM_TRANSFER_DIRECT = 0, 1
-LBM_BC_VELOCITY, LBM_BC_PRESSURE = 1, 2
-LBM_BC_EQUILIBRIUM, LBM_BC_ZOUHE, LBM_BC_REGULARIZED = 0, 1, 2
-MLP_NPARAM = 1394
+from .abi import *  # noqa: E402,F401,F403
+from .abi import MLP_NPARAM  # noqa: E402,F401
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ESTATE", 3: "LBM_ENOMEM",
                 4: "LBM_ECUDA", 5: "LBM_ENAN", 6: "LBM_ETIMEOUT", 7: "LBM_ENOCONV"}
@@ -77,6 +66,13 @@ _PROTOS = {
     "lbm_multi_step": (_i, [_vp, _i]),
     "lbm_multi_get_macro": (_i, [_vp, _vp, _vp, _i]),
     "lbm_multi_halo_bytes": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "lbm_multi_create_rank": (_i, [_i, _i, _i, _i, _i, _d, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "lbm_multi_face_buffers": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                    ctypes.POINTER(_sz)]),
+    "lbm_multi_step_begin": (_i, [_vp, _i]),
+    "lbm_multi_step_end": (_i, [_vp]),
+    "lbm_multi_exchange_stream": (_i, [_vp, ctypes.POINTER(_vp)]),
+    "lbm_multi_rows": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "lbm_multi_launch_count": (_ll, [_vp]),
     "lbm_multi_sync": (_i, [_vp]),
     "lbm_destroy": (_i, [_vp]),
@@ -190,6 +186,18 @@ def _field_dtype(a):
     if "float32" in name:
         return LBM_FIELD_F32
     raise TypeError(f"fields must be float32 or float64, got {dt}")
+
+
+def _pair_dtype(rho, u):
+    """The one element type of a (rho, u) pair (either may be None): the ABI
+    takes a single field type for both arrays, so arrays of different types
+    would have one of them written with the other's element size."""
+    if rho is not None and u is not None:
+        fd = _field_dtype(rho)
+        if _field_dtype(u) != fd:
+            raise TypeError("rho and u must share a dtype")
+        return fd
+    return _field_dtype(rho if rho is not None else u)
 
 
 # ---- the ABI, name for name ------------------------------------------------
@@ -316,8 +324,7 @@ def lbm_get_time(h):
 
 def lbm_get_macro(h, rho, u):
     """Fill rho / u (either may be None) with the last step's fields."""
-    ref = rho if rho is not None else u
-    _check(_L.lbm_get_macro(h, _ptr(rho), _ptr(u), _field_dtype(ref)), h)
+    _check(_L.lbm_get_macro(h, _ptr(rho), _ptr(u), _pair_dtype(rho, u)), h)
 
 
 def lbm_get_alpha(h, alpha):
@@ -447,7 +454,7 @@ def lbm_batch_set_force(b, d, fx, fy):
 
 
 def lbm_batch_init_equilibrium(b, d, rho, u):
-    _check(_L.lbm_batch_init_equilibrium(b, int(d), _ptr(rho), _ptr(u), _field_dtype(rho)), b,
+    _check(_L.lbm_batch_init_equilibrium(b, int(d), _ptr(rho), _ptr(u), _pair_dtype(rho, u)), b,
            batch=True)
 
 
@@ -472,8 +479,7 @@ def lbm_batch_step(b, n=1):
 
 
 def lbm_batch_get_macro(b, d, rho, u):
-    ref = rho if rho is not None else u
-    _check(_L.lbm_batch_get_macro(b, int(d), _ptr(rho), _ptr(u), _field_dtype(ref)), b,
+    _check(_L.lbm_batch_get_macro(b, int(d), _ptr(rho), _ptr(u), _pair_dtype(rho, u)), b,
            batch=True)
 
 
@@ -574,14 +580,48 @@ def lbm_multi_step(m, n=1):
 
 
 def lbm_multi_get_macro(m, rho, u):
-    ref = rho if rho is not None else u
-    _mcheck(_L.lbm_multi_get_macro(m, _ptr(rho), _ptr(u), _field_dtype(ref)), m)
+    _mcheck(_L.lbm_multi_get_macro(m, _ptr(rho), _ptr(u), _pair_dtype(rho, u)), m)
 
 
 def lbm_multi_halo_bytes(m):
     v = _ll(0)
     _mcheck(_L.lbm_multi_halo_bytes(m, ctypes.byref(v)), m)
     return int(v.value)
+
+
+def lbm_multi_create_rank(nx, ny, nz, lattice, model, tau, dtype, nsub, rank):
+    m = _vp()
+    _mcheck(_L.lbm_multi_create_rank(int(nx), int(ny), int(nz), int(lattice), int(model),
+                                     float(tau), int(dtype), int(nsub), int(rank),
+                                     ctypes.byref(m)), None)
+    return m.value
+
+
+def lbm_multi_face_buffers(m):
+    """(send address, recv address, bytes per face) of a rank handle."""
+    s, r, nb = _vp(), _vp(), _sz(0)
+    _mcheck(_L.lbm_multi_face_buffers(m, ctypes.byref(s), ctypes.byref(r), ctypes.byref(nb)), m)
+    return int(s.value), int(r.value), int(nb.value)
+
+
+def lbm_multi_step_begin(m, output=False):
+    _mcheck(_L.lbm_multi_step_begin(m, 1 if output else 0), m)
+
+
+def lbm_multi_step_end(m):
+    _mcheck(_L.lbm_multi_step_end(m), m)
+
+
+def lbm_multi_exchange_stream(m):
+    s = _vp()
+    _mcheck(_L.lbm_multi_exchange_stream(m, ctypes.byref(s)), m)
+    return int(s.value or 0)
+
+
+def lbm_multi_rows(m):
+    lo, hi = _i(0), _i(0)
+    _mcheck(_L.lbm_multi_rows(m, ctypes.byref(lo), ctypes.byref(hi)), m)
+    return int(lo.value), int(hi.value)
 
 
 def lbm_multi_launch_count(m):

@@ -49,3 +49,15 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def rho_errors(rg, ro, sel=None):
+    """Density errors that a density near 1 cannot hide: the relative L2
+    error of the deviation rho - 1, and the largest absolute error, over the
+    selected nodes (all by default)."""
+    rg = np.asarray(rg, dtype=np.float64)
+    ro = np.asarray(ro, dtype=np.float64)
+    if sel is not None:
+        rg, ro = rg[sel], ro[sel]
+    return rel_l2(rg - 1.0, ro - 1.0), float(np.abs(rg - ro).max())
+

@@ -169,3 +169,21 @@ def test_header_is_plain_c(lbm, tmp_path):
                         "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_python_constants_match_the_header(tmp_path):
+    """abi.py (imported by the benchmark's CPU arm, which must load no CUDA
+    library) holds the same values as the header's enums: a C program
+    compiled against include/lbm.h prints them."""
+    import subprocess
+    from paper_1311_2404_gb300 import abi
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "lbm.h"\nint main(void) {\n' + "".join(
+        f'    printf("{n} %d\\n", (int)({n}));\n' for n in abi.NAMES) + "    return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = dict((k, int(v)) for k, v in (ln.split() for ln in out.splitlines()))
+    assert got == {n: getattr(abi, n) for n in abi.NAMES}
+    assert len(got) >= 40

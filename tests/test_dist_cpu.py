@@ -62,3 +62,38 @@ def test_algorithmic_bytes_count_solid_nodes_by_their_geometry_word():
     assert bench.bytes_per_node("f16s", 0) == 36
     assert bench.algorithmic_bytes(100, 80, 156, 4) == 80 * 156 + 20 * 4
     assert bench.algorithmic_bytes(10, 10, 152, 0) == 1520
+
+
+def _faces_main(rank, world, port, out):
+    """Each rank sends faces tagged with its own number; checks what arrives."""
+    from paper_1311_2404_gb300 import slabs
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        nb = 48
+        send_up = torch.full((nb,), 10 + rank, dtype=torch.uint8)
+        send_down = torch.full((nb,), 100 + rank, dtype=torch.uint8)
+        recv_below = torch.zeros(nb, dtype=torch.uint8)
+        recv_above = torch.zeros(nb, dtype=torch.uint8)
+        for _ in range(3):                      # repeated steps reuse the buffers
+            slabs.exchange_faces(send_up, send_down, recv_below, recv_above, rank, world)
+        out[rank] = (int(recv_below.min()), int(recv_below.max()),
+                     int(recv_above.min()), int(recv_above.max()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_slab_face_exchange_gloo(world):
+    """The transport of the slab decomposition across processes: rank r's
+    upper face arrives in rank r + 1's lower receive buffer and its lower
+    face in rank r - 1's upper one, periodically; with two ranks both faces
+    go to the same peer and still land in the right buffers."""
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_faces_main, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    for r in range(world):
+        below, above = (r - 1) % world, (r + 1) % world
+        assert out[r] == (10 + below, 10 + below, 100 + above, 100 + above), (r, out[r])

@@ -93,7 +93,11 @@ def test_batch_vs_oracle_sampled():
                                force=(sp["gx"], 0, 0))
         F = oracle.init(p, rho, u)
         ro, uo, _, _ = oracle.run(p, F, steps, mask)
-        assert an.rel_l2(got[d][1], uo) < 1e-5 and an.rel_l2(got[d][0], ro) < 1e-5
+        fl = mask == 0
+        e_r, e_abs = an.rho_errors(got[d][0], ro, fl)
+        print(f"batch domain {d}: u {an.rel_l2(got[d][1], uo):.2e} rho-1 {e_r:.2e} "
+              f"max|drho| {e_abs:.2e}")
+        assert an.rel_l2(got[d][1], uo) < 1e-5 and e_r < 1e-5 and e_abs < 1e-7
 
 
 def test_autotune_keeps_state_and_graph_equals_direct():

@@ -22,8 +22,11 @@ from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
 LAT = {2: lbm.LBM_D2Q9, 3: lbm.LBM_D3Q19, 15: lbm.LBM_D3Q15, 27: lbm.LBM_D3Q27}
 OMODEL = {lbm.LBM_BGK: oracle.BGK, lbm.LBM_REG: oracle.REG, lbm.LBM_SMAG: oracle.SMAG,
           lbm.LBM_ELBM: oracle.ELBM, lbm.LBM_MRT: oracle.MRT}
-TOL = {lbm.LBM_F64: 1e-11, lbm.LBM_F32S: 2e-5, lbm.LBM_F32: 2e-4, lbm.LBM_F16S: 5e-3,
+TOL = {lbm.LBM_F64: 1e-11, lbm.LBM_F32S: 1e-5, lbm.LBM_F32: 2e-4, lbm.LBM_F16S: 5e-3,
        lbm.LBM_BF16S: 5e-2}
+# largest absolute density error (density units)
+RHO_ABS = {lbm.LBM_F64: 1e-13, lbm.LBM_F32S: 1e-7, lbm.LBM_F32: 1e-6, lbm.LBM_F16S: 2e-4,
+           lbm.LBM_BF16S: 2e-3}
 
 
 def _dim(code):
@@ -81,9 +84,11 @@ def test_new_lattices_vs_oracle(code, model, dtype):
     ro, uo = _oracle(code, model, shape, T, rho, u, mask, force, tau)
     fl = mask == 0
     eu = an.rel_l2(ug[:, fl], uo[:, fl])
-    print(f"D3Q{code} model {model} dtype {dtype}: rel-L2 u {eu:.3e}")
+    e_r, e_abs = an.rho_errors(rg, ro, fl)
+    print(f"D3Q{code} model {model} dtype {dtype}: rel-L2 u {eu:.3e} rho-1 {e_r:.3e} "
+          f"max|drho| {e_abs:.3e}")
     assert eu < TOL[dtype]
-    assert np.abs(rg[fl] - ro[fl]).max() < max(TOL[dtype], 1e-12) * 10
+    assert e_r < TOL[dtype] and e_abs < RHO_ABS[dtype]
 
 
 def _channel(code, nx=40, ny=18, nz=6):
@@ -118,8 +123,11 @@ def test_inlet_outlet_channel_vs_oracle(code, method, dtype):
     ro, uo = _oracle(code, lbm.LBM_BGK, mask.shape, T, rho, u, mask, force, 0.7, bcs)
     fl = mask != 1
     eu = an.rel_l2(ug[:, fl], uo[:, fl])
-    print(f"channel D{code} method {method} dtype {dtype}: rel-L2 u {eu:.3e}")
+    e_r, e_abs = an.rho_errors(rg, ro, fl)
+    print(f"channel D{code} method {method} dtype {dtype}: rel-L2 u {eu:.3e} "
+          f"rho-1 {e_r:.3e} max|drho| {e_abs:.3e}")
     assert eu < TOL[dtype]
+    assert e_abs < RHO_ABS[dtype]
     # the inlet nodes report the prescribed velocity
     inlet = mask == 2
     assert np.abs(ug[0][inlet] - 0.03).max() < (1e-13 if dtype == lbm.LBM_F64 else 1e-6)
@@ -142,8 +150,15 @@ def test_lid_driven_cavity_reduced_copy(dtype, model):
     ro, uo = _oracle(3, model, mask.shape, T, rho, u, mask, (0, 0, 0), tau, bcs, elbm_skip=1e-4)
     fl = mask != 1
     eu = an.rel_l2(ug[:, fl], uo[:, fl])
-    print(f"LDC model {model} dtype {dtype}: rel-L2 u {eu:.3e}")
-    assert eu < TOL[dtype] * (10 if model == lbm.LBM_ELBM else 1)
+    e_r, e_abs = an.rho_errors(rg, ro, fl)
+    print(f"LDC model {model} dtype {dtype}: rel-L2 u {eu:.3e} rho-1 {e_r:.3e} "
+          f"max|drho| {e_abs:.3e}")
+    # ELBM in FP64: the alpha root is fixed by FP64 rounding only to about
+    # |g| noise / g', and the GPU's series / logarithm forms of g round
+    # differently from the oracle's (1e-10, as in the ELBM parity tests)
+    elbm64 = model == lbm.LBM_ELBM and dtype == lbm.LBM_F64
+    assert eu < (1e-10 if elbm64 else TOL[dtype])
+    assert e_abs < (1e-11 if elbm64 else RHO_ABS[dtype])
 
 
 def test_couette_exact_profile_on_gpu():

@@ -2,12 +2,15 @@
 
 - GPU gradient of the surrogate's loss equals the FP64 reference's (which is
   itself pinned to finite differences) within 1e-4 relative; forward within
-  1e-5.
+  1e-5; full-batch Adam steps equal the reference's adam_step.
 - Training on the GPU lowers the loss.
-- End to end: pairs from a Newton-solved ELBM run, GPU training, then the
-  MLP-guarded solve reproduces Newton's alpha (1e-8) with fewer g
-  evaluations per node, and the oracle running the same guarded mode with the
-  same BF16-rounded weights agrees on the fields.
+- End to end: pairs from a Newton-solved ELBM run, GPU training, then every
+  guarded mode reproduces Newton's alpha (1e-8) at the same entropy-condition
+  residual bound, and the g evaluations per node are compared: the learned
+  guess needs fewer than Newton from 2 and than the second-order series it
+  corrects; the analytic truncated-series root (no learned part) needs fewer
+  still.  The oracle running the MLP-guarded mode with the same
+  BF16-rounded weights agrees on the fields.
 """
 import numpy as np
 import pytest
@@ -56,6 +59,45 @@ def test_forward_matches_fp64_reference():
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("steps", [1, 3])
+def test_adam_update_matches_oracle(steps):
+    """Full-batch training (batch = n, so the sample order cannot matter) for
+    one and three Adam steps against the FP64 reference: the oracle's
+    loss_and_grad, then adam_step with bias correction, from the same
+    initial parameters and targets t = (alpha - 2) / (scale eps).  The
+    parameters agree within 1e-5 of their largest magnitude and every
+    update (trained parameters minus initial ones) within 1e-3 of the
+    largest update; untrained entries are unchanged."""
+    rng = np.random.default_rng(17)
+    B = 2048
+    X = (rng.standard_normal((B, 8)) * np.array([1, 2, 3, 4, 1e-2, 2, 2, 1.0])).astype(np.float32)
+    X[:, 4] = np.abs(X[:, 4]) + 1e-3
+    alpha = 2.0 + 0.5 * X[:, 4].astype(np.float64) * (np.tanh(X[:, 0]) + 0.3 * X[:, 1])
+    P0 = mo.init_params(17, X.mean(0), 1.0 / X.std(0), 0.5).astype(np.float32)
+    lr = 1e-3
+    P = P0.copy()
+    loss = np.zeros(steps, dtype=np.float32)
+    lbm.lbm_mlp_train(torch.from_numpy(X).cuda(), torch.from_numpy(alpha).cuda(), B,
+                      [steps, B, lr, 3], P, loss)
+    Xr = X.astype(np.float64)
+    # the GPU forms its targets in FP64 and stores them in FP32
+    t = mo.target(P0.astype(np.float64), Xr, alpha).astype(np.float32).astype(np.float64)
+    Pr = P0.astype(np.float64)
+    m = np.zeros(mo.NPARAM)
+    v = np.zeros(mo.NPARAM)
+    for k in range(1, steps + 1):
+        lref, g = mo.loss_and_grad(Pr, Xr, t)
+        assert abs(loss[k - 1] - lref) <= 1e-5 * lref
+        Pr, m, v = mo.adam_step(Pr, g, m, v, k, lr=lr)
+    sl = slice(mo.TRAIN_LO, mo.TRAIN_HI)
+    dp = np.abs(P.astype(np.float64) - Pr)
+    print(f"Adam x{steps}: max |P - P_ref| {dp.max():.2e}, max |P_ref| {np.abs(Pr).max():.2e}")
+    assert dp.max() <= 1e-5 * np.abs(Pr).max()
+    du = (P.astype(np.float64) - P0) - (Pr - P0)
+    assert np.abs(du[sl]).max() <= 1e-3 * np.abs(Pr - P0)[sl].max()
+    assert np.array_equal(P[:mo.TRAIN_LO], P0[:mo.TRAIN_LO]) and P[mo.O_SCALE] == P0[mo.O_SCALE]
+
+
 def test_training_lowers_loss():
     rng = np.random.default_rng(3)
     X = rng.standard_normal((8192, 8)).astype(np.float32)
@@ -92,38 +134,66 @@ def trained():
     Xa = torch.cat(Xs)
     ya = torch.cat(ys)
     Xh = Xa.cpu().numpy().astype(np.float64)
-    tgt_scale = float(np.std((ya.cpu().numpy() - 2.0) / Xh[:, 4]))
+    tgt_scale = float(np.std(ya.cpu().numpy() - mo.series2(Xh)))
     P = mo.init_params(11, Xh.mean(0), 1.0 / (Xh.std(0) + 1e-12), tgt_scale).astype(np.float32)
     loss = np.zeros(20, dtype=np.float32)
     lbm.lbm_mlp_train(Xa, ya, len(ya), [20, 1024, 2e-3, 13], P, loss)
     return dict(P=P, loss=loss, state=state, t=t, n=n, tau=tau, npairs=len(ya))
 
 
-def test_learned_alpha_gain_and_parity(trained):
+def _solve_modes(trained, guard_steps):
+    """One step from the trained fixture's state in every alpha mode, at the
+    same guard tolerance (the same bound on the accepted correction, hence on
+    the entropy-condition residual): alpha field, g evaluations per solved
+    node, the fraction accepted from the guess, and the residual |g|/a_2."""
     P, n, tau = trained["P"], trained["n"], trained["tau"]
-    assert trained["npairs"] > 10000
-    assert trained["loss"][-1] < trained["loss"][0]
     res = {}
-    for mode in (lbm.LBM_ALPHA_NEWTON, lbm.LBM_ALPHA_SERIES_GUARDED, lbm.LBM_ALPHA_MLP_GUARDED):
+    for name, mode in (("newton", lbm.LBM_ALPHA_NEWTON),
+                       ("series", lbm.LBM_ALPHA_SERIES_GUARDED),
+                       ("mlp", lbm.LBM_ALPHA_MLP_GUARDED),
+                       ("root", lbm.LBM_ALPHA_ROOT_GUARDED)):
         sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
         lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-4)
+        lbm.lbm_set_elbm_guard(sim.h, guard_steps, 1e-6)
         lbm.lbm_load_alpha_mlp(sim.h, P)
         lbm.lbm_set_alpha_output(sim.h, 1)
         sim.set_state(trained["state"], trained["t"])
+        lbm.lbm_set_elbm_diagnostics(sim.h, 1)
         sim.step(1)
         a = np.empty((n, n, n))
         lbm.lbm_get_alpha(sim.h, a)
         st = lbm.lbm_get_elbm_stats(sim.h)
+        mean, mx, _ = lbm.lbm_get_elbm_entropy_error(sim.h)
         sim.close()
-        res[mode] = (a, st[0] / st[5], st[4] / st[5])
-    a_n, ev_n, _ = res[lbm.LBM_ALPHA_NEWTON]
-    a_m, ev_m, acc_m = res[lbm.LBM_ALPHA_MLP_GUARDED]
-    a_s, ev_s, _ = res[lbm.LBM_ALPHA_SERIES_GUARDED]
-    assert np.abs(a_m - a_n).max() < 1e-8
-    assert np.abs(a_s - a_n).max() < 1e-8
-    assert acc_m > 0.9                     # most nodes accepted from the guess
-    assert ev_m < ev_n                     # fewer FP64 g evaluations than Newton from 2
-    print(f"evals/node: newton {ev_n:.3f} series {ev_s:.3f} mlp {ev_m:.3f}; mlp accepted {acc_m:.3f}")
+        solved = st[5] - st[1]
+        res[name] = dict(alpha=a, evals=st[0] / solved, accepted=st[4] / solved,
+                         resid_mean=mean, resid_max=mx)
+    print(f"guard_steps {guard_steps}: " + "; ".join(
+        f"{k} evals/node {v['evals']:.3f} accepted {v['accepted']:.3f} "
+        f"|g|/a2 max {v['resid_max']:.1e}" for k, v in res.items()))
+    return res
+
+
+@pytest.mark.parametrize("guard_steps", [1, 2])
+def test_learned_alpha_gain_and_parity(trained, guard_steps):
+    assert trained["npairs"] > 10000
+    assert trained["loss"][-1] < trained["loss"][0]
+    res = _solve_modes(trained, guard_steps)
+    a_n = res["newton"]["alpha"]
+    for k in ("series", "mlp", "root"):
+        assert np.abs(res[k]["alpha"] - a_n).max() < 1e-8, k
+    for k, v in res.items():
+        assert v["resid_max"] < 1e-9, k          # the same residual bound for every mode
+    assert res["mlp"]["evals"] < res["newton"]["evals"]
+    # the learned correction beats the series it corrects ...
+    assert res["mlp"]["evals"] < res["series"]["evals"]
+    assert res["mlp"]["accepted"] > res["series"]["accepted"]
+    # ... but not the analytic truncated-series root, which uses the same
+    # moments (on this coarse 48^3 field many nodes lie beyond the accuracy of
+    # the truncation after a_6; on the 256^3 benchmark field nearly all are
+    # accepted after one evaluation)
+    assert res["root"]["evals"] < res["mlp"]["evals"]
+    assert res["root"]["accepted"] >= res["mlp"]["accepted"]
 
 
 def test_mlp_guarded_oracle_parity(trained):
@@ -147,16 +217,21 @@ def test_mlp_guarded_oracle_parity(trained):
     F = oracle.init(p, rho, u)
     ro, uo, _, _ = oracle.run(p, F, steps)
     import analytic as an
-    assert an.rel_l2(ug, uo) < 1e-5 and an.rel_l2(rg, ro) < 1e-5
+    e_r, e_abs = an.rho_errors(rg, ro)
+    print(f"MLP-guarded vs oracle: u {an.rel_l2(ug, uo):.2e} rho-1 {e_r:.2e} "
+          f"max|drho| {e_abs:.2e}")
+    assert an.rel_l2(ug, uo) < 1e-5 and e_r < 1e-5 and e_abs < 1e-7
 
 
 def test_entropy_condition_error_newton_vs_guesses(trained):
     """Diagnostic mode measures |g(alpha)| / a_2 at the accepted alpha with the
-    logarithm form: tiny for Newton (tolerance 1e-12 on alpha), bounded by the
-    guard tolerance for guesses accepted after two guarded steps."""
+    logarithm form: tiny for Newton (tolerance 1e-12 on alpha), and for the
+    guesses accepted with a correction below the guard tolerance (their
+    error is about that correction squared)."""
     P, n, tau = trained["P"], trained["n"], trained["tau"]
     res = {}
-    for mode in (lbm.LBM_ALPHA_NEWTON, lbm.LBM_ALPHA_SERIES_GUARDED, lbm.LBM_ALPHA_MLP_GUARDED):
+    for mode in (lbm.LBM_ALPHA_NEWTON, lbm.LBM_ALPHA_SERIES_GUARDED, lbm.LBM_ALPHA_MLP_GUARDED,
+                 lbm.LBM_ALPHA_ROOT_GUARDED):
         sim = lbm.Simulation(n, n, n, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
         lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-4)
         lbm.lbm_load_alpha_mlp(sim.h, P)
@@ -170,6 +245,36 @@ def test_entropy_condition_error_newton_vs_guesses(trained):
     for mode, (mean, mx, cnt, st) in res.items():
         print(f"mode {mode}: |g|/a2 mean {mean:.3e} max {mx:.3e} over {cnt} nodes")
         assert cnt > 0.5 * st[5]
-    assert res[lbm.LBM_ALPHA_NEWTON][1] < 1e-8
-    assert res[lbm.LBM_ALPHA_MLP_GUARDED][1] < 1e-4
-    assert res[lbm.LBM_ALPHA_SERIES_GUARDED][1] < 1e-4
+    for mode in res:
+        assert res[mode][1] < 1e-9, mode
+
+
+def test_elbm_taylor_green_vs_analytic(trained):
+    """The entropic model with each alpha solve on the Taylor-Green vortex
+    (D3Q19, 256 x 256 x 1 -- the vortex is z-independent --, u0 0.05,
+    tau 0.6, 1000 steps, FP32S storage, skip threshold 1e-4 so that most
+    nodes solve for alpha): velocity within 1e-3 of the analytic field
+    (the FP64 oracle's own run is at 4.3e-4 here, LBGK's at 4.9e-4), and the
+    guarded forms within 1e-6 of the Newton run."""
+    import analytic as an
+    n, tau, u0, T = 256, 0.6, 0.05, 1000
+    rho, u = wl.taylor_green(n, u0, nz=1, D=3)
+    ref = an.taylor_green_u(n, u0, an.nu_of_tau(tau), T, D=3, nz=1)
+    out = {}
+    for name, mode in (("newton", lbm.LBM_ALPHA_NEWTON), ("mlp", lbm.LBM_ALPHA_MLP_GUARDED),
+                       ("root", lbm.LBM_ALPHA_ROOT_GUARDED),
+                       ("series", lbm.LBM_ALPHA_SERIES_GUARDED)):
+        sim = lbm.Simulation(n, n, 1, lbm.LBM_D3Q19, lbm.LBM_ELBM, tau, lbm.LBM_F32S)
+        lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-4)
+        lbm.lbm_load_alpha_mlp(sim.h, trained["P"])
+        sim.init(rho, u)
+        sim.step(T)
+        _, ug = sim.macro()
+        st = lbm.lbm_get_elbm_stats(sim.h)
+        sim.close()
+        out[name] = (ug, an.rel_l2(ug, ref), st[0] / max(st[5] - st[1], 1), st[1] / st[5])
+    print("ELBM Taylor-Green 256^2, rel-L2 u vs analytic (evals per solved node, skipped): " +
+          "; ".join(f"{k} {v[1]:.3e} ({v[2]:.2f}, {v[3]:.2f})" for k, v in out.items()))
+    for k, v in out.items():
+        assert v[1] < 1e-3, k
+        assert an.rel_l2(v[0], out["newton"][0]) < 1e-6, k

@@ -1,6 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element (needs a GB300).
 
-Tolerances (relative L2 over all nodes, rho and v):
+Tolerances (relative L2 over all nodes of v and of the density deviation
+rho - 1, so that a density error cannot hide behind rho ~ 1; plus the
+largest absolute density error):
   LBM_F64                      1e-12 (same arithmetic up to rounding order)
   LBM_F32 / LBM_F32S           1e-5  (the stated FP32 parity bar)
   LBM_F16S / LBM_BF16S         reported, bounded loosely (storage-limited)
@@ -25,12 +27,16 @@ from paper_1311_2404_gb300 import workloads as wl  # noqa: E402
 
 TOL = {lbm.LBM_F64: 1e-12, lbm.LBM_F32: 1e-5, lbm.LBM_F32S: 1e-5,
        lbm.LBM_F16S: 2e-2, lbm.LBM_BF16S: 2e-1}
+# relative L2 of rho - 1: the FP32 bar for shifted storage; FP64 to
+# rounding-order noise on a deviation of ~1e-2 (the deviation is ~1e-2 of rho,
+# so 1e-10 of it is ~1e-12 of rho); plain FP32 keeps f itself, whose rounding
+# is 1e-8 of w_i per value (Sec. 3.7), 1e-4 of the deviation here
+RHO_DEV = {lbm.LBM_F64: 1e-10, lbm.LBM_F32: 1e-4, lbm.LBM_F32S: 1e-5,
+           lbm.LBM_F16S: 2e-2, lbm.LBM_BF16S: 2e-1}
+# largest absolute density error (density units)
+RHO_ABS = {lbm.LBM_F64: 1e-13, lbm.LBM_F32: 1e-7, lbm.LBM_F32S: 1e-7,
+           lbm.LBM_F16S: 2e-4, lbm.LBM_BF16S: 2e-3}
 OMODEL = {lbm.LBM_BGK: oracle.BGK, lbm.LBM_MRT: oracle.MRT, lbm.LBM_ELBM: oracle.ELBM}
-
-
-def _dev_err(a, b):
-    """Relative L2 of the deviation from rest (rho - 1 for densities)."""
-    return an.rel_l2(a, b)
 
 
 def run_pair(D, model, dtype, shape, steps, tau=0.6, force=(0.0, 0.0, 0.0), mask=None,
@@ -73,10 +79,13 @@ def test_parity_ragged_grid_with_walls_and_force(D, model, dtype):
     rg, ug, ro, uo = run_pair(D, model, dtype, shape, 40, tau=0.7, force=force, mask=mask)
     fl = mask == 0
     assert np.all(rg[~fl] == 0) and np.all(ug[:, ~fl] == 0)
-    e_u, e_r = an.rel_l2(ug, uo), an.rel_l2(rg - 1 * fl, ro - 1 * fl)
+    e_u = an.rel_l2(ug, uo)
+    e_r, e_abs = an.rho_errors(rg, ro, fl)
+    print(f"ragged D{D} model {model} dtype {dtype}: u {e_u:.2e} rho-1 {e_r:.2e} "
+          f"max|drho| {e_abs:.2e}")
     tol = TOL[dtype]
     assert e_u < tol, (e_u, e_r)
-    assert an.rel_l2(rg, ro) < tol
+    assert e_r < RHO_DEV[dtype] and e_abs < RHO_ABS[dtype], (e_r, e_abs)
 
 
 @pytest.mark.parametrize("dtype", [lbm.LBM_F64, lbm.LBM_F32S])
@@ -91,7 +100,11 @@ def test_parity_elbm(D, dtype):
     rg, ug, ro, uo = run_pair(D, lbm.LBM_ELBM, dtype, shape, 12, tau=0.505,
                               force=(1e-5, 0.0, 0.0), elbm=dict(mode=0, skip=0.0))
     tol = 1e-10 if dtype == lbm.LBM_F64 else TOL[dtype]
-    assert an.rel_l2(ug, uo) < tol and an.rel_l2(rg, ro) < tol
+    e_r, e_abs = an.rho_errors(rg, ro)
+    print(f"ELBM D{D} dtype {dtype}: u {an.rel_l2(ug, uo):.2e} rho-1 {e_r:.2e} "
+          f"max|drho| {e_abs:.2e}")
+    assert an.rel_l2(ug, uo) < tol and e_r < tol
+    assert e_abs < (1e-11 if dtype == lbm.LBM_F64 else RHO_ABS[dtype])
 
 
 def test_elbm_alpha_field_parity():
@@ -148,9 +161,14 @@ def tg256_oracle():
 
 def test_taylor_green_256_full_size(tg256_oracle):
     """The bench workload: D3Q19 LBGK FP32S, 256^3, tau 0.6, u0 0.05, 1000
-    steps.  Every z plane equals the oracle within 1e-5 (rho, u), planes are
+    steps.  Every z plane equals the oracle within 1e-5 in v; planes are
     bitwise identical, mass is conserved, kinetic energy decays as
-    exp(-4 nu k^2 t) within 1e-4."""
+    exp(-4 nu k^2 t) within 1e-4.  The density deviation of this flow is the
+    pressure, rho - 1 = 3 p ~ u0^2 (1.7e-3 here): its FP32 error is a tenth of
+    the velocity's in absolute terms (4e-8 rms against 4e-7) but, relative to
+    a field of order u0^2, about twice the velocity's relative error
+    (2.6e-5 measured with 7.9e-6 in v), so it is held to 5e-5, and to 2e-7
+    in density units at every node."""
     n, tau, u0, T = 256, 0.6, 0.05, 1000
     ro, uo = tg256_oracle
     rho, u = wl.taylor_green(n, u0, nz=n, D=3)
@@ -158,17 +176,19 @@ def test_taylor_green_256_full_size(tg256_oracle):
     sim.init(rho.astype(np.float32), u.astype(np.float32))
     sim.step(T)
     sums = sim.reduce()
-    rg = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
-    ug = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+    # FP64 fields: the rho - 1 check needs more than FP32's resolution near 1
+    rg = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    ug = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
     lbm.lbm_get_macro(sim.h, rg, ug)
     sim.close()
     # all planes identical
     assert torch.equal(rg, rg[:1].expand_as(rg)) and torch.equal(ug, ug[:, :1].expand_as(ug))
     r0 = rg[0:1].double().cpu().numpy()
     u0g = ug[:, 0:1].double().cpu().numpy()
+    e_r, e_abs = an.rho_errors(r0, ro)
+    print(f"TG256 FP32S: u {an.rel_l2(u0g, uo):.2e} rho-1 {e_r:.2e} max|drho| {e_abs:.2e}")
     assert an.rel_l2(u0g, uo) < 1e-5
-    assert an.rel_l2(r0, ro) < 1e-5
-    assert an.rel_l2(r0 - 1, ro - 1) < 1e-3       # the deviation from rest, too
+    assert e_r < 5e-5 and e_abs < 2e-7
     # FP64 reductions: mass, KE decay
     nu = an.nu_of_tau(tau)
     k = 2 * math.pi / n
