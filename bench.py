@@ -67,6 +67,13 @@ def parse():
                          "root guess)")
     ap.add_argument("--guard-steps", type=int, default=2,
                     help="ELBM guarded modes: evaluations that may end in early acceptance")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1 ranks: independent replicas (weak scaling), or one slab of the "
+                         "workload per rank with the faces exchanged every step (Sec. 3.6; "
+                         "strong scaling)")
+    ap.add_argument("--dist-backend", default="",
+                    help="torch.distributed backend of --decomp slab (default nccl; gloo "
+                         "stages the faces through host memory)")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
     ap.add_argument("--batch-config", default="",
                     help="launch configuration for --workload batch instead of autotuning: "
@@ -110,16 +117,33 @@ def peaks():
 # the sources of the headline kernel (LBGK stream-collide): its translation
 # unit and the headers it includes
 KERNEL_SOURCES = ("k_bgk.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh")
+# the ELBM kernel's
+ELBM_SOURCES = ("k_elbm.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh")
 
 
-def source_sha():
-    """Hash of the headline kernel's sources; a recorded DRAM traffic figure
-    is reported only while they are unchanged."""
+def source_sha(names=KERNEL_SOURCES):
+    """Hash of a kernel's sources; a recorded profiler figure is reported
+    only while they are unchanged."""
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_1311_2404_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def fp64_inst_for(alpha, dtype):
+    """FP64-pipe warp instructions per node of the ELBM kernel from the
+    committed ncu record (profiles/fp64_elbm.json), if the ELBM sources are
+    unchanged since that capture; else None."""
+    path = os.path.join(ROOT, "profiles", "fp64_elbm.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(f"elbm:{alpha}:{dtype}")
+    if not e or e.get("source_sha") != source_sha(ELBM_SOURCES):
+        return None
+    return float(e["fp64_warp_inst_per_node"])
 
 
 def traffic_for(workload, dtype):
@@ -393,6 +417,113 @@ def run_multi(args):
     print(json.dumps(line), flush=True)
 
 
+def run_slabs(args):
+    """The workload cut into one slab per rank (Sec. 3.6): every step each
+    rank updates its slab and exchanges its two faces with its neighbours
+    (NCCL point-to-point on the exchange stream, overlapped with the bulk
+    rows).  The whole domain is fixed, so this is strong scaling."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    backend = args.dist_backend or "nccl"
+    if world > 1:
+        dist.init_process_group(backend)
+    from paper_1311_2404_gb300 import lbm, slabs
+    spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice, args.shape)
+    nx, ny, nz = spec["n"]
+    nodes = nx * ny * nz
+    rho, u, mask = workload_inputs(spec)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sl = slabs.RankSlab(nx, ny, nz, spec["lattice"], spec["model"], spec["tau"],
+                            spec["dtype"], rank, world, stream=stream.cuda_stream,
+                            overlap=not args.no_overlap)
+        for b in spec.get("bcs", ()):
+            sl.set_boundary(*b)
+        if mask is not None:
+            sl.set_geometry(mask)
+        if any(spec["force"]):
+            sl.set_force(*spec["force"])
+        sl.set_rounding(lbm.LBM_ROUND_NEAREST if args.round == "nearest"
+                        else lbm.LBM_ROUND_DITHER)
+        sl.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        sl.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = lbm.lbm_multi_launch_count(sl.m)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sl.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = lbm.lbm_multi_launch_count(sl.m) - l0
+        clocks = sampler.stop() if sampler else None
+        lo, hi = sl.rows
+        local_nodes = nodes * (hi - lo) // (nz if spec["lattice"] != lbm.LBM_D2Q9 else ny)
+        hb = sl.halo_bytes()
+        # end to end: the rank's whole-domain inputs from pinned host memory,
+        # one step, its rows back to pinned host memory
+        pin_r = torch.from_numpy(rho).pin_memory()
+        pin_u = torch.from_numpy(u).pin_memory()
+        out_r = torch.zeros_like(pin_r).pin_memory()
+        out_u = torch.zeros_like(pin_u).pin_memory()
+        e2e_steps = max(1, min(args.e2e_steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sl.init(pin_r, pin_u)
+            sl.step(1)
+            lbm.lbm_multi_get_macro(sl.m, out_r, out_u)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        sl.close()
+    ms_max, e2e_ms = max_over_ranks([ms, e2e_s * 1e3], world, "cuda")
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    glups = nodes * args.steps / (ms_max * 1e-3) / 1e9
+    bpn = bytes_per_node(args.dtype, spec["lattice"]) + (4 if mask is not None else 0)
+    achieved = local_nodes * bpn / (ms / 1e3 / args.steps) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
+        "value": round(glups, 4), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max / args.steps, 6),
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded analytic/random initial fields; no dataset)",
+        "config": {"workload": spec["name"], "lattice": LATTICE_NAME[spec["lattice"]],
+                   "model": {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG", 4: "SMAG"}[spec["model"]],
+                   "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
+                   "parallelism": f"slab{world}", "backend": backend if world > 1 else None,
+                   "overlap": not args.no_overlap, "halo_bytes_per_step_per_rank": hb,
+                   "l2": "working set > 129 MB L2 per rank (inputs larger than L2, no flush)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_kind, "bytes_per_node": bpn,
+                     "note": "rank 0's slab updates per its own kernel time; the exchange "
+                             "moves halo_bytes_per_step_per_rank more"},
+        "e2e": {"value": round(nodes / (e2e_ms * 1e-3) / 1e9, 4), "unit": "GLUPS",
+                "h2d_bytes_per_step": int(rho.nbytes + u.nbytes),
+                "d2h_bytes_per_step": int((rho.nbytes + u.nbytes) * (hi - lo) //
+                                          (nz if spec["lattice"] != lbm.LBM_D2Q9 else ny))},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def elbm_compare(lbm, sim, spec, rho, u, args, stream):
     """After the timed steps: kinetic energy of this run against a Newton run
     of the same steps from the same state, and the entropy-condition residual
@@ -456,13 +587,18 @@ def run_ours(args):
             mode = {"newton": lbm.LBM_ALPHA_NEWTON, "series": lbm.LBM_ALPHA_SERIES_GUARDED,
                     "mlp": lbm.LBM_ALPHA_MLP_GUARDED,
                     "root": lbm.LBM_ALPHA_ROOT_GUARDED}[args.alpha]
-            lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-3)
-            lbm.lbm_set_elbm_guard(sim.h, args.guard_steps, 1e-6)
             if args.alpha == "mlp":
+                # the surrogate learns from Newton-solved steps of this very
+                # workload (its field sets the distribution of the invariants)
                 from paper_1311_2404_gb300 import alpha_training as at
-                Xp, yp, _, _ = at.collect_pairs(n=64)
+                lbm.lbm_set_elbm(sim.h, lbm.LBM_ALPHA_NEWTON, 1e-12, 20, 1e-3)
+                lbm.lbm_init_equilibrium(sim.h, torch.from_numpy(rho).cuda(),
+                                         torch.from_numpy(u).cuda())
+                Xp, yp = at.collect_pairs_from(sim, rounds=3, steps_between=2, stride=16)
                 P, _ = at.train(Xp, yp)
                 lbm.lbm_load_alpha_mlp(sim.h, P)
+            lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-3)
+            lbm.lbm_set_elbm_guard(sim.h, args.guard_steps, 1e-6)
         rho_d = torch.from_numpy(rho).cuda()
         u_d = torch.from_numpy(u).cuda()
         lbm.lbm_init_equilibrium(sim.h, rho_d, u_d)      # inputs resident in HBM
@@ -586,6 +722,23 @@ def run_ours(args):
         line["elbm"] = elbm_stats
         if elbm_cmp:
             line["elbm"].update(elbm_cmp)
+        # the entropic kernel is bound by the FP64 pipe (the alpha solve of
+        # Eq. alpha_cond runs in FP64): its roofline is that pipe's measured
+        # warp-instruction rate, its work the ncu count of FP64-pipe
+        # instructions per node; the HBM figures stay beside it
+        w_rate, f_rate = lbm.lbm_probe_fp64_rate(stream.cuda_stream)
+        ipn = fp64_inst_for(args.alpha, args.dtype)
+        hbm = line["roofline"]
+        line["roofline"] = {
+            "bound": "fp64", "unit": "G warp-inst/s",
+            "achieved": round(ipn * nodes / per_launch_s / 1e9, 3) if ipn else None,
+            "peak": round(w_rate / 1e9, 3),
+            "frac": round(ipn * nodes / per_launch_s / w_rate, 4) if ipn else None,
+            "peak_source": "measured (lbm_probe_fp64_rate: FP64 FMA chains, CUDA events, "
+                           "this run)",
+            "peak_fp64_tflops": round(f_rate / 1e12, 4),
+            "fp64_warp_inst_per_node": ipn, "traffic": None,
+            "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "bytes_per_node")}}
     if diag:
         line["kida"] = diag
     if world == 1 and not args.no_cpu_baseline:
@@ -854,6 +1007,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.decomp == "slab":
+        run_slabs(args)
     elif args.subdomains > 0:
         run_multi(args)
     elif args.workload == "batch":

@@ -470,6 +470,15 @@ LBM_API int lbm_mlp_grad_static(const float* X_dev, const float* t_dev, int n,
                                 const float* params, float* loss, float* grad,
                                 void* cuda_stream);
 
+/* Measured rate of the FP64 pipe of the current GPU (no counterpart in the
+ * paper; the denominator of the ELBM kernel's roofline, whose FP64 alpha
+ * solve of Eq. alpha_cond is bound by that pipe): every thread of a full
+ * grid runs independent chains of FP64 fused multiply-adds for tens of
+ * milliseconds; the best of three timed runs (CUDA events on cuda_stream)
+ * gives FP64 warp instructions per second and FLOP/s (2 per FMA).
+ * Synchronises the stream.  LBM_ECUDA on a CUDA error. */
+LBM_API int lbm_probe_fp64_rate(void* cuda_stream, double* warp_inst_per_s, double* flops);
+
 /* Message of the last failed lbm_mlp_* call on this thread. */
 LBM_API const char* lbm_mlp_last_error(void);
 

@@ -63,6 +63,24 @@ def series2(Xh):
     return 2.0 + (t3 * eps - 2.0 * t4 * eps * eps) / 3.0 + 4.0 * t3 * t3 * eps * eps / 9.0
 
 
+def collect_pairs_from(sim, rounds=3, steps_between=2, stride=16, cap=1 << 21):
+    """Pairs from an ELBM Simulation in its current state: `rounds` times,
+    `steps_between` steps then one captured step (every stride-th eligible
+    node).  The handle's alpha mode is used as set (Newton gives exact
+    targets).  Returns (X, alpha) CUDA tensors."""
+    import torch
+    X = torch.empty((cap, 8), dtype=torch.float32, device="cuda")
+    y = torch.empty(cap, dtype=torch.float64, device="cuda")
+    Xs, ys = [], []
+    for _ in range(rounds):
+        if steps_between:
+            sim.step(steps_between)
+        cnt = lbm.lbm_elbm_collect_pairs(sim.h, stride, X, y)
+        Xs.append(X[:cnt].clone())
+        ys.append(y[:cnt].clone())
+    return torch.cat(Xs), torch.cat(ys)
+
+
 def train(X, alpha, epochs=20, batch=1024, lr=2e-3, seed=13):
     """Parameters (float32, 1394) trained on the GPU; returns (params, loss per epoch).
     The output scale is the spread of the targets alpha - series2."""

@@ -135,6 +135,7 @@ _PROTOS = {
     "lbm_mlp_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
     "lbm_mlp_last_error": (ctypes.c_char_p, []),
     "lbm_mlp_grad_static": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "lbm_probe_fp64_rate": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_L, _name)
@@ -414,6 +415,15 @@ def lbm_mlp_grad_static(X_dev, t_dev, n, params, stream=None):
     _check(_L.lbm_mlp_grad_static(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss),
                                   _ptr(grad), stream), mlp=True)
     return float(loss[0]), grad
+
+
+def lbm_probe_fp64_rate(stream=None):
+    """(FP64 warp instructions per second, FP64 FLOP/s) of the current GPU."""
+    w, f = _d(0.0), _d(0.0)
+    code = _L.lbm_probe_fp64_rate(stream, ctypes.byref(w), ctypes.byref(f))
+    if code:
+        raise LBMError(code, "FP64 rate probe failed")
+    return float(w.value), float(f.value)
 
 
 def lbm_mlp_last_error():

@@ -104,6 +104,9 @@ class RankSlab:
     def set_rounding(self, mode):
         self.lbm.lbm_multi_set_rounding(self.m, mode)
 
+    def set_boundary(self, cid, kind, method, normal, value):
+        self.lbm.lbm_multi_set_boundary(self.m, cid, kind, method, normal, value)
+
     def init(self, rho, u):
         if isinstance(rho, np.ndarray):
             rho = np.ascontiguousarray(rho)
