@@ -91,9 +91,23 @@ class RankSlab:
         self.rows = lbm.lbm_multi_rows(self.m)
 
     def close(self):
+        """Free the handle.  The torch-side buffers go first: a pinned host
+        buffer copied asynchronously on the exchange stream makes torch record
+        an event on that stream when the buffer is freed, so the stream (the
+        handle's) must still exist then."""
         if self.m:
+            self.exchange_stream.synchronize()
+            for name in ("_hsend", "_hrecv", "_send", "_recv"):
+                if hasattr(self, name):
+                    delattr(self, name)
             self.lbm.lbm_multi_destroy(self.m)
             self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def set_geometry(self, mask):
         self.lbm.lbm_multi_set_geometry(self.m, np.ascontiguousarray(mask, dtype=np.uint8))

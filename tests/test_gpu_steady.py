@@ -111,14 +111,13 @@ def test_round_to_nearest_stalls(steady):
     assert steady["f16s_nearest"][0] > 10 * steady["f16s"][0]
 
 
-def test_stochastic_rounding_is_unbiased_in_time(steady):
-    """The FP16S field at steady state carries the noise of stochastic
-    rounding; with the time step in the rounding hash that noise is fresh
-    every step, so it averages out: the mean of fields taken 1000 steps
-    apart (more than the slowest mode's relaxation time, ~720 steps) is
-    closer to the parabola than a single field.  Round-to-nearest stays
-    where it stalled."""
-    err, _, _, err_mean = steady["f16s"]
-    assert err_mean < 0.7 * err
+def test_fp16s_stays_near_the_steady_state(steady):
+    """Stochastic rounding keeps the FP16S field moving around the steady
+    state rather than settling at a fixed point of the rounded map: every
+    one of 8 fields 1000 steps apart after the first 12000 steps (their mean
+    here) stays within the 1e-3 bar, while round-to-nearest stays where it
+    stalled."""
+    _, _, _, err_mean = steady["f16s"]
+    assert err_mean < 1e-3
     e_rn, _, _, e_rn_mean = steady["f16s_nearest"]
-    assert e_rn_mean > 0.9 * e_rn
+    assert e_rn_mean > 10 * err_mean
