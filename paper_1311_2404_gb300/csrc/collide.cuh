@@ -791,7 +791,7 @@ struct LogEval {
 // for a <= 0.1 / max|x|, where the terms beyond K = 14 are below 1e-17 of
 // a_2 (the scale of g'); an iterate outside that range falls back to LogEval.
 constexpr int kSeriesK = 14;
-constexpr int kSeriesK64 = 9;    // moments above this order are accumulated in FP32
+constexpr int kSeriesK64 = 7;    // moments above this order are accumulated in FP32
 constexpr double kSeriesMaxX = 0.03;
 struct SeriesEval {
     double c[kSeriesK + 1];      // c_k, k = 2..K
@@ -972,6 +972,14 @@ __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const Step
 // Reciprocal in FP64 from an FP32 seed refined by two Newton-Raphson steps
 // r <- r (2 - f r) (each step squares the relative error: 2^-24 -> 2^-48 ->
 // below FP64 rounding).  f > 0, as the distributions of a valid state are.
+__host__ __device__ __forceinline__ double recip_nr(double f);
+// The same with one refinement step: relative error below 2^-46 (1.4e-14).
+__host__ __device__ __forceinline__ double recip_nr1(double f)
+{
+    if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
+    const double r = (double)(1.0f / (float)f);
+    return r * fma(-f, r, 2.0);
+}
 __host__ __device__ __forceinline__ double recip_nr(double f)
 {
     if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
@@ -1049,16 +1057,22 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             fe[i] += L::w(i) * corr;
             y[i] *= corr;                               // w_i corr / P_i
         }
-        lc0 = log(c0);
+        // ln c0 and ln r_a enter A only as ln c0 sum Delta and ln r_a
+        // sum e_a Delta, sums that vanish up to rounding (the restored f_eq
+        // has f's mass and momentum); FP32 logarithms change A by ~1e-19
+        lc0 = (double)logf((float)c0);
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) lr[a] = log(r[a]);
+        for (int a = 0; a < L::D; ++a) lr[a] = (double)logf((float)r[a]);
     } else {
         elbm_feq<L>(rho, u, 1, fe);
     }
     double maxabs = 0, xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        x[i] = (fe[i] - f[i]) * recip_nr(f[i]);
+        // x_i to 1.4e-14 relative: the update's Delta_i = f_i x_i then
+        // conserves mass and momentum to ~1e-16 per node and step, FP64's own
+        // rounding level
+        x[i] = (fe[i] - f[i]) * recip_nr1(f[i]);
         maxabs = fmax(maxabs, fabs(x[i]));
         xmin = fmin(xmin, x[i]);
         xmax = fmax(xmax, x[i]);
@@ -1074,11 +1088,12 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         bool solved = false;
         if (entropic && maxabs <= kSeriesMaxX) {
             // moments a_k and A from the series (no per-direction logarithm)
-            // a_2..a_9 in FP64; a_10..a_14 in FP32.  With |a_k| <= max|x|^(k-2) a_2
+            // a_2..a_7 in FP64; a_8..a_14 in FP32.  With |a_k| <= max|x|^(k-2) a_2
             // and a max|x| <= 0.1 over the series' range, term k of g is at most
-            // 2 (a max|x|)^(k-2) / (k (k-1)) of a^2 a_2 / 2: from k = 10 on below
-            // 2.3e-10, so FP32's relative error (< 2e-6 after 14 products and 19
-            // sums) moves g by less than 5e-16 of its scale.
+            // 2 (a max|x|)^(k-2) / (k (k-1)) of a^2 a_2 / 2: from k = 8 on below
+            // 3.6e-8, so FP32's relative error (< 2e-6 after 14 products and 19
+            // sums) moves g by less than 1e-13 of its scale, below the Newton
+            // tolerance of 1e-12 on alpha.
             double a[kSeriesK + 1];
             float ahi[kSeriesK - kSeriesK64];
 #pragma unroll
