@@ -39,6 +39,8 @@ B_PER_NODE = {"f32s": 152, "f32": 152, "f16s": 76, "bf16s": 76, "f64": 304}   # 
 ESIZE = {"f32s": 4, "f32": 4, "f16s": 2, "bf16s": 2, "f64": 8}
 LATTICE_NAME = {0: "D2Q9", 1: "D3Q19", 2: "D3Q15", 3: "D3Q27"}
 LATTICE_Q = {0: 9, 1: 19, 2: 15, 3: 27}
+# lbm_set_masked_kernel modes (LBM_MASKED_AUTO, _NODE, _ZRUN)
+MASKED_KERNEL = {"auto": 0, "node": 1, "zrun": 2}
 
 
 def bytes_per_node(dtype, lattice=1):
@@ -61,7 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tg256",
-                    choices=["tg256", "duct", "elbm", "kida", "ldc", "batch"])
+                    choices=["tg256", "duct", "elbm", "kida", "ldc", "batch", "mlp"])
     ap.add_argument("--alpha", default="newton", choices=["newton", "series", "mlp", "root"],
                     help="ELBM alpha solve for --workload elbm (root: the truncated-series "
                          "root guess)")
@@ -75,6 +77,9 @@ def parse():
                     help="torch.distributed backend of --decomp slab (default nccl; gloo "
                          "stages the faces through host memory)")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
+    ap.add_argument("--mlp-kernel", default="tc", choices=["tc", "fp32"],
+                    help="--workload mlp: BF16 tensor-core or FP32 training kernel")
+    ap.add_argument("--mlp-batch", type=int, default=16384, help="--workload mlp: minibatch")
     ap.add_argument("--batch-config", default="",
                     help="launch configuration for --workload batch instead of autotuning: "
                          "threads,ctas,tile_width,tile_rows,variant")
@@ -98,6 +103,8 @@ def parse():
                     help="with --subdomains: store straight into the neighbour's ghost row")
     ap.add_argument("--no-overlap", action="store_true",
                     help="with --subdomains: exchange after whole slabs, no bulk/boundary split")
+    ap.add_argument("--masked-kernel", default="auto", choices=["auto", "node", "zrun"],
+                    help="kernel of masked 3-D AB steps (lbm_set_masked_kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="time K direct launches instead of replaying the K steps as one CUDA "
@@ -579,6 +586,7 @@ def run_ours(args):
             lbm.lbm_set_boundary(sim.h, *b)
         if mask is not None:
             sim.set_geometry(mask)
+        lbm.lbm_set_masked_kernel(sim.h, MASKED_KERNEL[args.masked_kernel])
         if any(spec["force"]):
             sim.set_force(*spec["force"])
         lbm.lbm_set_rounding(sim.h, lbm.LBM_ROUND_NEAREST if args.round == "nearest"
@@ -700,6 +708,7 @@ def run_ours(args):
                    **({"rounding": args.round} if args.dtype in ("f16s", "bf16s") else {}),
                    **({"pattern": "AA"} if args.pattern == "aa" else {}),
                    "launch": "cuda_graph" if args.graph else "direct",
+                   **({"masked_kernel": args.masked_kernel} if mask is not None else {}),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "AB working set %.2f GB > 129 MB L2 (inputs larger than L2, no flush)"
                          % (bytes_per_node(args.dtype, spec["lattice"]) * nodes / 1e9)},
@@ -834,9 +843,63 @@ def batch_cpu_baseline(specs, budget_s=10.0):
                       f"{t_used:.1f} s"}
 
 
+def _blas_threads():
+    """Threads numpy's BLAS uses (the oracle's matrix products), else the
+    host's cores."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = sum(int(p.get("num_threads", 0)) for p in threadpool_info()
+                if p.get("user_api") == "blas")
+        if n > 0:
+            return n
+    except ImportError:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference_mlp(args):
+    """The FP64 oracle's minibatch Adam (loss_and_grad, adam_step) on a
+    sample of the synthetic pairs, timed on the host."""
+    import oracle.mlp_oracle as mo
+    from paper_1311_2404_gb300 import workloads as wl
+    from paper_1311_2404_gb300.alpha_training import init_params, series2
+    n = 1 << 16
+    X, alpha = wl.mlp_pairs(n)
+    Xr = X.astype(np.float64)
+    scale = float(np.std(alpha - series2(Xr)))
+    P = init_params(13, X.mean(0), 1.0 / (X.std(0) + 1e-12), scale).astype(np.float64)
+    t = mo.target(P, Xr, alpha)
+    B = min(args.mlp_batch, n)
+    m = np.zeros(mo.NPARAM)
+    v = np.zeros(mo.NPARAM)
+    k = 0
+    steps = max(args.steps, 1) + max(args.warmup, 0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        off = (k * B) % (n - B + 1)
+        _, g = mo.loss_and_grad(P, Xr[off:off + B], t[off:off + B])
+        k += 1
+        P, m, v = mo.adam_step(P, g, m, v, k, lr=2e-3)
+    el = time.perf_counter() - t0
+    sps = steps * B / el
+    print(json.dumps({
+        "impl": "reference", "metric": "alpha-surrogate training throughput (minibatch Adam on the GPU)",
+        "value": round(sps, 1), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / steps * 1e3, 3),
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded features and alpha)",
+        "config": {"workload": "mlp_8_32_32_1_train_%d_pairs" % (1 << 20), "batch": B},
+        "cpu_baseline": {"value": round(sps, 1), "unit": "samples/s", "cores": _blas_threads(),
+                         "kind": "oracle", "sample": "%d minibatches of %d from %d pairs" % (steps, B, n)},
+        "e2e": {"value": round(sps, 1), "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "mlp":
+        run_reference_mlp(args)
         return
     spec = workload_spec(args.workload, args.dtype, args.size, args.model, args.lattice, args.shape)
     import oracle
@@ -1003,6 +1066,92 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# forward and backward multiply-adds of one sample through the 8-32-32-1
+# surrogate: forward 8*32 + 32*32 + 32, backward D2 W2 (32*32), dW2
+# (32*32), dW1 (32*8), dW3 (32)
+MLP_FLOP_PER_SAMPLE = 2 * (8 * 32 + 32 * 32 + 32 + 32 * 32 + 32 * 32 + 32 * 8 + 32)
+
+
+def run_mlp(args):
+    """Training throughput of the alpha surrogate (minibatch Adam, all on the
+    GPU) on 2^20 synthetic pairs: K epochs after W warm-up epochs, both
+    kernels timed; the line reports the chosen one (--mlp-kernel)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1311_2404_gb300 import lbm
+    from paper_1311_2404_gb300 import workloads as wl
+    from paper_1311_2404_gb300.alpha_training import init_params, series2
+    X, alpha = wl.mlp_pairs()
+    n = len(alpha)
+    Xd = torch.from_numpy(X).cuda()
+    ad = torch.from_numpy(alpha).cuda()
+    scale = float(np.std(alpha - series2(X.astype(np.float64))))
+    P0 = init_params(13, X.mean(0), 1.0 / (X.std(0) + 1e-12), scale)
+    kern = {"tc": lbm.LBM_MLP_BF16_TC, "fp32": lbm.LBM_MLP_FP32}
+    res = {}
+    steps, warm = max(1, args.steps), max(3, args.warmup)
+    sampler = ClockSampler(0)
+    for name in ("fp32", "tc") if args.mlp_kernel == "tc" else ("tc", "fp32"):
+        P = P0.copy()
+        loss = np.zeros(warm, dtype=np.float32)
+        lbm.lbm_mlp_train_cfg(Xd, ad, n, warm, args.mlp_batch, 2e-3, 1, kern[name], P, loss)
+        P = P0.copy()
+        loss = np.zeros(steps, dtype=np.float32)
+        if name == args.mlp_kernel:
+            sampler.start()
+        st = lbm.lbm_mlp_train_cfg(Xd, ad, n, steps, args.mlp_batch, 2e-3, 1, kern[name], P,
+                                   loss)
+        if name == args.mlp_kernel:
+            clocks = sampler.stop()
+        res[name] = (st, float(loss[-1]))
+    # end to end: the pairs from pinned host memory, the trained parameters back
+    Xh = torch.from_numpy(X).pin_memory()
+    ah = torch.from_numpy(alpha).pin_memory()
+    P = P0.copy()
+    loss = np.zeros(1, dtype=np.float32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xe = Xh.cuda(non_blocking=True)
+    ae = ah.cuda(non_blocking=True)
+    st_e = lbm.lbm_mlp_train_cfg(Xe, ae, n, 1, args.mlp_batch, 2e-3, 1, kern[args.mlp_kernel], P,
+                                 loss)
+    e2e_s = time.perf_counter() - t0
+    st, final = res[args.mlp_kernel]
+    sps = st["samples_per_s"]
+    peak, _ = peaks()
+    bf16_peak = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            bf16_peak = float(json.load(fh).get("bf16_tflops", 0.0)) or None
+    achieved = sps * MLP_FLOP_PER_SAMPLE / 1e12
+    line = {
+        "metric": "alpha-surrogate training throughput (minibatch Adam on the GPU)",
+        "value": round(sps, 1), "unit": "samples/s", "n_gpus": 1, "steps": steps,
+        "warmup": warm, "ms_per_step": round(st["gpu_ms"] / st["steps"], 6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.mlp_kernel == "tc" else "f32",
+        "data": "synthetic (seeded features and alpha; no dataset)",
+        "config": {"workload": "mlp_8_32_32_1_train_%d_pairs" % n, "batch": args.mlp_batch,
+                   "epochs": steps, "kernel": args.mlp_kernel,
+                   "l2": "pairs %.1f MB, resident" % ((X.nbytes + alpha.nbytes) / 1e6)},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 3),
+                     "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / bf16_peak, 6) if bf16_peak else None,
+                     "traffic": None, "flop_per_sample": MLP_FLOP_PER_SAMPLE,
+                     "peak_source": "measured bf16 (cuBLAS, burst)" if bf16_peak else None},
+        "e2e": {"value": round(n / e2e_s, 1), "unit": "samples/s",
+                "h2d_bytes_per_step": int(X.nbytes + alpha.nbytes),
+                "d2h_bytes_per_step": int(P.nbytes)},
+        "gpu_launches": int(st["steps"] * 3),
+        "clocks": clocks,
+        "final_loss": final,
+        "compare": {k: {"samples_per_s": round(v[0]["samples_per_s"], 1), "final_loss": v[1]}
+                    for k, v in res.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1013,6 +1162,8 @@ def main():
         run_multi(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_ours(args)
 

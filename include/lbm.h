@@ -439,11 +439,56 @@ LBM_API int lbm_elbm_collect_pairs(lbm_handle h, int stride, float* X_dev, doubl
 LBM_API int lbm_mlp_train(const float* X_dev, const double* alpha_dev, int n, const double* cfg,
                   float* params, float* loss_out, void* cuda_stream);
 
+/* Forward/backward kernels of the surrogate's training. */
+#define LBM_MLP_FP32 0     /* FP32 CUDA-core kernel, one thread per sample */
+#define LBM_MLP_BF16_TC 1  /* BF16 tensor-core MMA (FP32 accumulation) on the
+                              network with entries 16 .. 1392 rounded to BF16
+                              as lbm_load_alpha_mlp rounds them: the gradient
+                              of the rounded network's loss updates the FP32
+                              master copy.  Activations and back-propagated
+                              gradients enter the MMAs as BF16 pairs hi + lo
+                              (16 significant bits). */
+
+/* Training configuration: epochs >= 1, batch >= 1 (clamped to n), lr > 0,
+ * seed of the per-epoch shuffle, kernel LBM_MLP_*; reserved must be 0. */
+typedef struct lbm_mlp_cfg {
+    int epochs;
+    int batch;
+    double lr;
+    unsigned long long seed;
+    int kernel;
+    int reserved;
+} lbm_mlp_cfg;
+
+/* Filled by lbm_mlp_train_cfg: Adam steps taken, device time of the
+ * training launches (CUDA events around each epoch's forward/backward,
+ * reduction and update launches), samples through forward and backward per
+ * second of that time, and the last epoch's mean loss. */
+typedef struct lbm_train_stats {
+    int steps;
+    int reserved;
+    double gpu_ms;
+    double samples_per_s;
+    double final_loss;
+} lbm_train_stats;
+
+/* lbm_mlp_train with the configuration as a struct and the kernel choice;
+ * stats may be NULL.  LBM_EINVAL for a bad configuration.  Synchronises.
+ * lbm_mlp_train is this call with kernel LBM_MLP_FP32. */
+LBM_API int lbm_mlp_train_cfg(const float* X_dev, const double* alpha_dev, int n,
+                              const lbm_mlp_cfg* cfg, float* params, float* loss_out,
+                              lbm_train_stats* stats, void* cuda_stream);
+
 /* One forward+backward pass on a batch (device X [n][8], device targets
  * t [n]), for checking gradients: writes the loss and the gradient of every
  * parameter (host, 1394 floats; zeros for fixed entries).  Synchronises. */
 LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const float* params,
                  float* loss, float* grad, void* cuda_stream);
+
+/* lbm_mlp_grad with the LBM_MLP_BF16_TC kernel: the loss and gradient of the
+ * network whose entries 16 .. 1392 are rounded to BF16. */
+LBM_API int lbm_mlp_grad_tc(const float* X_dev, const float* t_dev, int n, const float* params,
+                            float* loss, float* grad, void* cuda_stream);
 
 /* Same as lbm_mlp_grad, but allocates nothing.  The paper has no
  * counterpart; this exists for callers that cannot call cudaMalloc, such as

@@ -17,6 +17,7 @@ LBM_MASKED_AUTO, LBM_MASKED_NODE, LBM_MASKED_ZRUN = 0, 1, 2
 LBM_TRANSFER_STAGED, LBM_TRANSFER_DIRECT = 0, 1
 LBM_BC_VELOCITY, LBM_BC_PRESSURE = 1, 2
 LBM_BC_EQUILIBRIUM, LBM_BC_ZOUHE, LBM_BC_REGULARIZED = 0, 1, 2
+LBM_MLP_FP32, LBM_MLP_BF16_TC = 0, 1
 MLP_NPARAM = 1394
 
 NAMES = [k for k in dir() if k.startswith("LBM_")]

@@ -135,6 +135,8 @@ _PROTOS = {
     "lbm_mlp_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
     "lbm_mlp_last_error": (ctypes.c_char_p, []),
     "lbm_mlp_grad_static": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "lbm_mlp_grad_tc": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "lbm_mlp_train_cfg": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "lbm_probe_fp64_rate": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
 }
 for _name, (_res, _args) in _PROTOS.items():
@@ -398,12 +400,46 @@ def lbm_mlp_train(X_dev, alpha_dev, n, cfg, params, loss_out, stream=None):
                             _ptr(loss_out), stream), mlp=True)
 
 
+class MlpCfg(ctypes.Structure):
+    """struct lbm_mlp_cfg."""
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("kernel", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class TrainStats(ctypes.Structure):
+    """struct lbm_train_stats."""
+    _fields_ = [("steps", ctypes.c_int), ("reserved", ctypes.c_int), ("gpu_ms", ctypes.c_double),
+                ("samples_per_s", ctypes.c_double), ("final_loss", ctypes.c_double)]
+
+
+def lbm_mlp_train_cfg(X_dev, alpha_dev, n, epochs, batch, lr, seed, kernel, params, loss_out,
+                      stream=None):
+    """Training with the kernel choice (LBM_MLP_FP32 / LBM_MLP_BF16_TC);
+    returns the stats as a dict."""
+    cfg = MlpCfg(int(epochs), int(batch), float(lr), int(seed), int(kernel), 0)
+    st = TrainStats()
+    _check(_L.lbm_mlp_train_cfg(_ptr(X_dev), _ptr(alpha_dev), int(n), ctypes.byref(cfg),
+                                _ptr(params), _ptr(loss_out), ctypes.byref(st), stream), mlp=True)
+    return {"steps": st.steps, "gpu_ms": st.gpu_ms, "samples_per_s": st.samples_per_s,
+            "final_loss": st.final_loss}
+
+
 def lbm_mlp_grad(X_dev, t_dev, n, params, stream=None):
     p = np.ascontiguousarray(params, dtype=np.float32)
     loss = np.zeros(1, dtype=np.float32)
     grad = np.zeros(MLP_NPARAM, dtype=np.float32)
     _check(_L.lbm_mlp_grad(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss), _ptr(grad),
                            stream), mlp=True)
+    return float(loss[0]), grad
+
+
+def lbm_mlp_grad_tc(X_dev, t_dev, n, params, stream=None):
+    """lbm_mlp_grad on the BF16 tensor-core kernel (weights rounded to BF16)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(_L.lbm_mlp_grad_tc(_ptr(X_dev), _ptr(t_dev), int(n), _ptr(p), _ptr(loss), _ptr(grad),
+                              stream), mlp=True)
     return float(loss[0]), grad
 
 

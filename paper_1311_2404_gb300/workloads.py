@@ -250,3 +250,18 @@ def random_state(nx: int, ny: int, nz: int, D: int, u_amp: float = 0.05,
     rho = 1.0 + field(rho_amp)
     u = np.stack([field(u_amp) for _ in range(D)])
     return rho, u
+
+
+# --------------------------------------------------------------------------
+# Synthetic training pairs for the alpha surrogate's training throughput
+# --------------------------------------------------------------------------
+def mlp_pairs(n: int = 1 << 20, seed: int = 1393):
+    """n (features, alpha) pairs shaped like the ELBM kernel's: 8 FP32
+    features of the spreads the invariants take (the fifth, eps, positive
+    and small) and alpha near 2 varying smoothly with them.  A throughput
+    workload: the values carry no physics."""
+    rng = _rng(seed)
+    X = rng.standard_normal((n, 8)) * np.array([1.0, 2.0, 3.0, 4.0, 1e-2, 2.0, 2.0, 1.0])
+    X[:, 4] = np.abs(X[:, 4]) + 1e-3
+    alpha = 2.0 + 0.5 * X[:, 4] * (np.tanh(X[:, 0]) + 0.3 * X[:, 1])
+    return X.astype(np.float32), alpha

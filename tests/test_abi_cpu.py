@@ -187,3 +187,33 @@ def test_python_constants_match_the_header(tmp_path):
     got = dict((k, int(v)) for k, v in (ln.split() for ln in out.splitlines()))
     assert got == {n: getattr(abi, n) for n in abi.NAMES}
     assert len(got) >= 40
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of lbm_mlp_cfg and lbm_train_stats have the C
+    structs' sizes and field offsets (a C program compiled against the
+    header prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_1311_2404_gb300 import lbm as m
+    pairs = (("lbm_mlp_cfg", m.MlpCfg), ("lbm_train_stats", m.TrainStats))
+    lines = []
+    for cname, cls in pairs:
+        lines.append(f'    printf("{cname} sizeof %d\\n", (int)sizeof({cname}));\n')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {f} %d\\n", (int)offsetof({cname}, {f}));\n')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
+                   "int main(void) {\n" + "".join(lines) + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for cname, cls in pairs:
+        assert int(got[f"{cname} sizeof"]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname} {f}"]) == getattr(cls, f).offset, (cname, f)

@@ -3,6 +3,9 @@
 - GPU gradient of the surrogate's loss equals the FP64 reference's (which is
   itself pinned to finite differences) within 1e-4 relative; forward within
   1e-5; full-batch Adam steps equal the reference's adam_step.
+- The BF16 tensor-core kernel's gradient equals the FP64 reference gradient
+  of the BF16-rounded network within 1e-3 relative (the BF16 bar), and its
+  Adam step the reference's.
 - Training on the GPU lowers the loss.
 - End to end: pairs from a Newton-solved ELBM run, GPU training, then every
   guarded mode reproduces Newton's alpha (1e-8) at the same entropy-condition
@@ -96,6 +99,106 @@ def test_adam_update_matches_oracle(steps):
     du = (P.astype(np.float64) - P0) - (Pr - P0)
     assert np.abs(du[sl]).max() <= 1e-3 * np.abs(Pr - P0)[sl].max()
     assert np.array_equal(P[:mo.TRAIN_LO], P0[:mo.TRAIN_LO]) and P[mo.O_SCALE] == P0[mo.O_SCALE]
+
+
+def _bf16(P):
+    """Entries 16 .. 1392 rounded to BF16 (round to nearest even), as the
+    tensor-core kernel and lbm_load_alpha_mlp round them."""
+    Pq = np.asarray(P, dtype=np.float32).copy()
+    Pq[mo.TRAIN_LO:mo.TRAIN_HI] = torch.from_numpy(Pq[mo.TRAIN_LO:mo.TRAIN_HI]).bfloat16().float().numpy()
+    return Pq
+
+
+@pytest.mark.parametrize("B", [1000, 64, 7])
+def test_tensor_core_gradient_matches_fp64_reference(B):
+    """The BF16 tensor-core kernel (MMA with the network rounded to BF16,
+    activations as hi + lo BF16 pairs) against the FP64 reference gradient
+    of the same rounded network: within 1e-3 relative (the BF16 bar), over
+    batches that fill several CTAs and end inside a warp's tile."""
+    X, P, t = _rand(2, B)
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    loss, g = lbm.lbm_mlp_grad_tc(Xd, td, B, P)
+    Pq = _bf16(P).astype(np.float64)
+    lref, gref = mo.loss_and_grad(Pq, X.astype(np.float64), t.astype(np.float64))
+    sl = slice(mo.TRAIN_LO, mo.TRAIN_HI)
+    rel = np.abs(g[sl] - gref[sl]).max() / np.abs(gref[sl]).max()
+    per_block = {name: np.abs(g[a:b] - gref[a:b]).max() / np.abs(gref[a:b]).max()
+                 for name, a, b in (("W1", mo.O_W1, mo.O_B1), ("b1", mo.O_B1, mo.O_W2),
+                                    ("W2", mo.O_W2, mo.O_B2), ("b2", mo.O_B2, mo.O_W3),
+                                    ("W3", mo.O_W3, mo.O_B3), ("b3", mo.O_B3, mo.O_B3 + 1))}
+    print(f"tensor-core gradient B={B}: loss rel {abs(loss - lref) / lref:.2e}, max rel {rel:.2e}, "
+          + ", ".join(f"{k} {v:.1e}" for k, v in per_block.items()))
+    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    assert rel < 1e-3 and max(per_block.values()) < 1e-3
+    assert np.all(g[:mo.TRAIN_LO] == 0) and g[mo.O_SCALE] == 0
+
+
+def test_tensor_core_gradient_equals_fp32_kernel_on_rounded_weights():
+    """Both kernels differentiate the same network when the FP32 kernel is
+    given the BF16-rounded parameters: they agree within 1e-3."""
+    X, P, t = _rand(4, 4096)
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    l_tc, g_tc = lbm.lbm_mlp_grad_tc(Xd, td, len(t), P)
+    l_32, g_32 = lbm.lbm_mlp_grad(Xd, td, len(t), _bf16(P))
+    sl = slice(mo.TRAIN_LO, mo.TRAIN_HI)
+    assert abs(l_tc - l_32) <= 1e-4 * l_32
+    assert np.abs(g_tc[sl] - g_32[sl]).max() < 1e-3 * np.abs(g_32[sl]).max()
+
+
+def test_tensor_core_adam_step_matches_oracle():
+    """One full-batch Adam step with the tensor-core kernel: the oracle's
+    adam_step on the FP64 gradient of the BF16-rounded network, applied to
+    the FP32 master parameters."""
+    rng = np.random.default_rng(19)
+    B = 2048
+    X = (rng.standard_normal((B, 8)) * np.array([1, 2, 3, 4, 1e-2, 2, 2, 1.0])).astype(np.float32)
+    X[:, 4] = np.abs(X[:, 4]) + 1e-3
+    alpha = 2.0 + 0.5 * X[:, 4].astype(np.float64) * (np.tanh(X[:, 0]) + 0.3 * X[:, 1])
+    P0 = mo.init_params(19, X.mean(0), 1.0 / X.std(0), 0.5).astype(np.float32)
+    lr = 1e-3
+    P = P0.copy()
+    loss = np.zeros(1, dtype=np.float32)
+    st = lbm.lbm_mlp_train_cfg(torch.from_numpy(X).cuda(), torch.from_numpy(alpha).cuda(), B,
+                               1, B, lr, 3, lbm.LBM_MLP_BF16_TC, P, loss)
+    assert st["steps"] == 1 and st["gpu_ms"] > 0
+    Xr = X.astype(np.float64)
+    t = mo.target(P0.astype(np.float64), Xr, alpha).astype(np.float32).astype(np.float64)
+    lref, g = mo.loss_and_grad(_bf16(P0).astype(np.float64), Xr, t)
+    assert abs(loss[0] - lref) <= 1e-4 * lref
+    Pr, _, _ = mo.adam_step(P0.astype(np.float64), g, np.zeros(mo.NPARAM), np.zeros(mo.NPARAM),
+                            1, lr=lr)
+    sl = slice(mo.TRAIN_LO, mo.TRAIN_HI)
+    du = (P.astype(np.float64) - P0) - (Pr - P0)
+    print(f"tensor-core Adam step: max |dP - dP_ref| {np.abs(du[sl]).max():.2e} "
+          f"of max |dP_ref| {np.abs(Pr - P0)[sl].max():.2e}")
+    # the first Adam step moves each entry by lr g / (|g| + eps): it only
+    # differs where |g| is comparable to eps
+    assert np.abs(du[sl]).max() <= 1e-3 * np.abs(Pr - P0)[sl].max()
+    assert np.array_equal(P[:mo.TRAIN_LO], P0[:mo.TRAIN_LO]) and P[mo.O_SCALE] == P0[mo.O_SCALE]
+
+
+def test_tensor_core_training_lowers_loss_and_reports_throughput():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((8192, 8)).astype(np.float32)
+    X[:, 4] = np.abs(X[:, 4]) + 0.1
+    alpha = 2.0 + 0.5 * X[:, 4] * (np.tanh(X[:, 0]) * 0.5 + 0.2 * X[:, 1])
+    Xd = torch.from_numpy(X).cuda()
+    ad = torch.from_numpy(alpha.astype(np.float64)).cuda()
+    out = {}
+    for name, kern in (("fp32", lbm.LBM_MLP_FP32), ("bf16_tc", lbm.LBM_MLP_BF16_TC)):
+        P = mo.init_params(3, X.mean(0), 1.0 / X.std(0), 0.5).astype(np.float32)
+        loss = np.zeros(30, dtype=np.float32)
+        st = lbm.lbm_mlp_train_cfg(Xd, ad, len(X), 30, 256, 3e-3, 5, kern, P, loss)
+        out[name] = (loss, st)
+        assert loss[-1] < 0.05 * loss[0], name
+        assert st["steps"] == 30 * (8192 // 256) and abs(st["final_loss"] - loss[-1]) < 1e-6
+    print("training 30 epochs x 32 steps of 256: " + "; ".join(
+        f"{k} final loss {v[0][-1]:.3e}, {v[1]['samples_per_s'] / 1e6:.1f} M samples/s"
+        for k, v in out.items()))
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_train_cfg(Xd, ad, len(X), 1, 256, 1e-3, 5, 7, np.zeros(1394, np.float32), None)
 
 
 def test_training_lowers_loss():
