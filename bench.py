@@ -78,7 +78,8 @@ def parse():
                          "stages the faces through host memory)")
     ap.add_argument("--ndom", type=int, default=512, help="domains for --workload batch")
     ap.add_argument("--mlp-kernel", default="tc", choices=["tc", "fp32"],
-                    help="--workload mlp: BF16 tensor-core or FP32 training kernel")
+                    help="--workload mlp (and the surrogate of --alpha mlp): BF16 "
+                         "tensor-core or FP32 training kernel")
     ap.add_argument("--mlp-batch", type=int, default=16384, help="--workload mlp: minibatch")
     ap.add_argument("--batch-config", default="",
                     help="launch configuration for --workload batch instead of autotuning: "
@@ -603,7 +604,8 @@ def run_ours(args):
                 lbm.lbm_init_equilibrium(sim.h, torch.from_numpy(rho).cuda(),
                                          torch.from_numpy(u).cuda())
                 Xp, yp = at.collect_pairs_from(sim, rounds=3, steps_between=2, stride=16)
-                P, _ = at.train(Xp, yp)
+                P, _ = at.train(Xp, yp, kernel=lbm.LBM_MLP_BF16_TC if args.mlp_kernel == "tc"
+                                else lbm.LBM_MLP_FP32)
                 lbm.lbm_load_alpha_mlp(sim.h, P)
             lbm.lbm_set_elbm(sim.h, mode, 1e-12, 20, 1e-3)
             lbm.lbm_set_elbm_guard(sim.h, args.guard_steps, 1e-6)
@@ -705,6 +707,8 @@ def run_ours(args):
                    **({"smagorinsky_cs": 0.1} if spec["model"] == 4 else {}),
                    "storage": args.dtype, "tau": spec["tau"], "nodes": nodes,
                    **({"alpha": args.alpha} if spec["model"] == 2 else {}),
+                   **({"mlp_training": args.mlp_kernel} if spec["model"] == 2
+                      and args.alpha == "mlp" else {}),
                    **({"rounding": args.round} if args.dtype in ("f16s", "bf16s") else {}),
                    **({"pattern": "AA"} if args.pattern == "aa" else {}),
                    "launch": "cuda_graph" if args.graph else "direct",

@@ -355,12 +355,14 @@ LBM_API long long lbm_launch_count(lbm_handle h);
 
 typedef struct lbm_batch_ctx* lbm_batch;
 
-/* ndom independent periodic D2Q9 LBGK domains of sizes nx[d] x ny[d] with
- * relaxation times tau[d], storage dtype LBM_F32S or LBM_F16S.  All domains
- * advance together in one persistent cooperative launch per lbm_batch_step
- * call; that launch is captured in a CUDA graph and replayed. */
-LBM_API int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, int dtype,
-                     lbm_batch* out);
+/* ndom independent periodic LBGK domains of sizes nx[d] x ny[d] with
+ * relaxation times tau[d] on lattice LBM_D2Q9 (the batched kernels are
+ * D2Q9; other lattices give LBM_EINVAL), storage dtype LBM_F32S or
+ * LBM_F16S.  All domains advance together in one persistent cooperative
+ * launch per lbm_batch_step call; that launch is captured in a CUDA graph
+ * and replayed. */
+LBM_API int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau,
+                     int lattice, int dtype, lbm_batch* out);
 LBM_API int lbm_batch_destroy(lbm_batch b);
 LBM_API const char* lbm_batch_last_error(lbm_batch b);
 LBM_API int lbm_batch_set_stream(lbm_batch b, void* cuda_stream);

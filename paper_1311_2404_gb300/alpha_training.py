@@ -81,13 +81,17 @@ def collect_pairs_from(sim, rounds=3, steps_between=2, stride=16, cap=1 << 21):
     return torch.cat(Xs), torch.cat(ys)
 
 
-def train(X, alpha, epochs=20, batch=1024, lr=2e-3, seed=13):
+def train(X, alpha, epochs=20, batch=1024, lr=2e-3, seed=13, kernel=None):
     """Parameters (float32, 1394) trained on the GPU; returns (params, loss per epoch).
-    The output scale is the spread of the targets alpha - series2."""
+    The output scale is the spread of the targets alpha - series2.  kernel:
+    lbm.LBM_MLP_FP32 or lbm.LBM_MLP_BF16_TC (the default: trains the network
+    with the BF16 rounding lbm_load_alpha_mlp applies for inference)."""
     Xh = X.double().cpu().numpy()
     ah = alpha.cpu().numpy()
     scale = float(np.std(ah - series2(Xh)))
     P = init_params(seed, Xh.mean(0), 1.0 / (Xh.std(0) + 1e-12), scale)
     loss = np.zeros(epochs, dtype=np.float32)
-    lbm.lbm_mlp_train(X, alpha, int(alpha.numel()), [epochs, batch, lr, seed], P, loss)
+    if kernel is None:
+        kernel = lbm.LBM_MLP_BF16_TC
+    lbm.lbm_mlp_train_cfg(X, alpha, int(alpha.numel()), epochs, batch, lr, seed, kernel, P, loss)
     return P, loss

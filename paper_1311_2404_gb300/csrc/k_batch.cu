@@ -1107,12 +1107,13 @@ static cudaError_t launch_batch(lbm_batch b, int nsteps, int from)
 
 extern "C" {
 
-int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, int dtype,
-                     lbm_batch* out)
+int lbm_batch_create(int ndom, const int* nx, const int* ny, const double* tau, int lattice,
+                     int dtype, lbm_batch* out)
 {
     if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (ndom < 1 || !nx || !ny || !tau) return bfail(nullptr, LBM_EINVAL, "bad arguments");
+    if (lattice != LBM_D2Q9) return bfail(nullptr, LBM_EINVAL, "batched domains are LBM_D2Q9");
     if (dtype != LBM_F32S && dtype != LBM_F16S)
         return bfail(nullptr, LBM_EINVAL, "batch storage must be LBM_F32S or LBM_F16S");
     lbm_batch b = new lbm_batch_ctx();

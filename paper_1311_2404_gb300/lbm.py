@@ -111,7 +111,7 @@ _PROTOS = {
     "lbm_set_state": (_i, [_vp, _vp, _ll]),
     "lbm_sync": (_i, [_vp]),
     "lbm_launch_count": (_ll, [_vp]),
-    "lbm_batch_create": (_i, [_i, _vp, _vp, _vp, _i, ctypes.POINTER(_vp)]),
+    "lbm_batch_create": (_i, [_i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp)]),
     "lbm_batch_destroy": (_i, [_vp]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_batch_set_stream": (_i, [_vp, _vp]),
@@ -472,12 +472,12 @@ def lbm_mlp_forward(X_dev, n, params, alpha_dev, stream=None):
 
 
 # ---- batch ABI --------------------------------------------------------------
-def lbm_batch_create(nx, ny, tau, dtype):
+def lbm_batch_create(nx, ny, tau, dtype, lattice=LBM_D2Q9):
     nx = np.ascontiguousarray(nx, dtype=np.int32)
     ny = np.ascontiguousarray(ny, dtype=np.int32)
     tau = np.ascontiguousarray(tau, dtype=np.float64)
     b = _vp()
-    code = _L.lbm_batch_create(int(nx.size), _ptr(nx), _ptr(ny), _ptr(tau), dtype,
+    code = _L.lbm_batch_create(int(nx.size), _ptr(nx), _ptr(ny), _ptr(tau), int(lattice), dtype,
                                ctypes.byref(b))
     _check(code, None, batch=True)
     return b.value

@@ -217,3 +217,11 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[f"{cname} sizeof"]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname} {f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_batch_create_validates_on_host(lbm):
+    """The batched ensemble is D2Q9 with FP32S / FP16S storage: other
+    lattices and storage types are refused before any device work."""
+    for lat, dt in ((lbm.LBM_D3Q19, lbm.LBM_F32S), (7, lbm.LBM_F32S), (lbm.LBM_D2Q9, lbm.LBM_F64)):
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_batch_create([8], [8], [0.6], dt, lattice=lat)

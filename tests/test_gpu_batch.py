@@ -144,6 +144,8 @@ def test_batch_errors():
     assert ei.value.code == lbm.LBM_EINVAL
     with pytest.raises(lbm.LBMError):
         lbm.lbm_batch_create([10], [10], [0.6], lbm.LBM_F64)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_batch_create([10], [10], [0.6], lbm.LBM_F32S, lattice=lbm.LBM_D3Q19)
     b = lbm.lbm_batch_create([40, 50], [30, 20], [0.6, 0.7], lbm.LBM_F32S)
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_batch_step(b, 1)                  # domains not initialised
