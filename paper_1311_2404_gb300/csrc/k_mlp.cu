@@ -494,19 +494,37 @@ __global__ void __launch_bounds__(TC_WARPS * 32) k_fwd_bwd_tc(const float* __res
     if (tid == 0) part_loss[blockIdx.x] = sRow[NTRAIN];
 }
 
-__global__ void k_reduce(const float* __restrict__ part, const float* __restrict__ part_loss,
-                         int nblk, int B, float* __restrict__ grad, float* __restrict__ loss_acc)
+// Sum of the partial rows, in a fixed order: a CTA of RED_GROUPS x 32
+// threads takes 32 consecutive entries; group k of a column sums rows k,
+// k + RED_GROUPS, ... (the 32 columns of one row are one coalesced read),
+// then the column's group sums are added in group order.  CTA 0 also sums
+// the partial losses (row order).
+constexpr int RED_GROUPS = 8;
+constexpr int RED_THREADS = 32 * RED_GROUPS;
+constexpr int RED_BLOCKS = (NTRAIN + 31) / 32;
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const float* __restrict__ part,
+                                                        const float* __restrict__ part_loss,
+                                                        int nblk, int B, float* __restrict__ grad,
+                                                        float* __restrict__ loss_acc)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < NTRAIN) {
-        float s = 0.f;
-        for (int k = 0; k < nblk; ++k) s += part[(size_t)k * NTRAIN + e];
-        grad[TRAIN_LO + e] = s;
+    __shared__ float sg[RED_GROUPS][32];
+    const int col = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + col;
+    float s = 0.f;
+    if (e < NTRAIN)
+        for (int k = grp; k < nblk; k += RED_GROUPS) s += part[(size_t)k * NTRAIN + e];
+    sg[grp][col] = s;
+    __syncthreads();
+    if (grp == 0 && e < NTRAIN) {
+        float t = sg[0][col];
+        for (int k = 1; k < RED_GROUPS; ++k) t += sg[k][col];
+        grad[TRAIN_LO + e] = t;
     }
-    if (e == 0) {
-        float s = 0.f;
-        for (int k = 0; k < nblk; ++k) s += part_loss[k];
-        loss_acc[0] += s / (float)B;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        float l = 0.f;
+        for (int k = 0; k < nblk; ++k) l += part_loss[k];
+        loss_acc[0] += l / (float)B;
         loss_acc[1] += 1.0f;
     }
 }
@@ -623,7 +641,7 @@ static int mlp_grad_impl(const float* X_dev, const float* t_dev, int n, const fl
     else
         k_fwd_bwd<<<nblk, BS, 0, s>>>(X_dev, t_dev, nullptr, n, P.as<float>(), part.as<float>(),
                                       pl.as<float>());
-    k_reduce<<<(NTRAIN + 255) / 256, 256, 0, s>>>(part.as<float>(), pl.as<float>(), nblk, n,
+    k_reduce<<<RED_BLOCKS, RED_THREADS, 0, s>>>(part.as<float>(), pl.as<float>(), nblk, n,
                                                   G.as<float>(), la.as<float>());
     MCK(cudaGetLastError(), "gradient kernels");
     float lh[2];
@@ -705,7 +723,7 @@ int lbm_mlp_train_cfg(const float* X_dev, const double* alpha_dev, int n, const 
             else
                 k_fwd_bwd<<<nblk, BS, 0, s>>>(X_dev, T.as<float>(), I.as<int>() + off, B,
                                               P.as<float>(), part.as<float>(), pl.as<float>());
-            k_reduce<<<(NTRAIN + 255) / 256, 256, 0, s>>>(part.as<float>(), pl.as<float>(), nblk,
+            k_reduce<<<RED_BLOCKS, RED_THREADS, 0, s>>>(part.as<float>(), pl.as<float>(), nblk,
                                                           B, G.as<float>(), la.as<float>());
             const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
             k_adam<<<(NTRAIN + 255) / 256, 256, 0, s>>>(P.as<float>(), G.as<float>(),
@@ -823,7 +841,7 @@ extern "C" int lbm_mlp_grad_static(const float* X_dev, const float* t_dev, int n
     MCK(cudaMemsetAsync(G, 0, NPARAM * 4, s), "clear gradient");
     MCK(cudaMemsetAsync(la, 0, 8, s), "clear loss");
     k_fwd_bwd<<<nblk, BS, 0, s>>>(X_dev, t_dev, nullptr, n, P, part, pl);
-    k_reduce<<<(NTRAIN + 255) / 256, 256, 0, s>>>(part, pl, nblk, n, G, la);
+    k_reduce<<<RED_BLOCKS, RED_THREADS, 0, s>>>(part, pl, nblk, n, G, la);
     MCK(cudaGetLastError(), "gradient kernels");
     float lh[2];
     MCK(cudaMemcpyAsync(grad, G, NPARAM * 4, cudaMemcpyDefault, s), "copy gradient");
