@@ -791,7 +791,7 @@ struct LogEval {
 // for a <= 0.1 / max|x|, where the terms beyond K = 14 are below 1e-17 of
 // a_2 (the scale of g'); an iterate outside that range falls back to LogEval.
 constexpr int kSeriesK = 14;
-constexpr int kSeriesK64 = 7;    // moments above this order are accumulated in FP32
+constexpr int kSeriesK64 = 6;    // moments above this order are accumulated in FP32
 constexpr double kSeriesMaxX = 0.03;
 struct SeriesEval {
     double c[kSeriesK + 1];      // c_k, k = 2..K
@@ -980,6 +980,17 @@ __host__ __device__ __forceinline__ double recip_nr1(double f)
     const double r = (double)(1.0f / (float)f);
     return r * fma(-f, r, 2.0);
 }
+// The same from an FP32 value fs of f formed without an FP64 conversion (the
+// stored FP32 deviation plus the weight, in FP32): fs is within
+// 2^-24 (1 + w / f) of f and the seed 1/fs within one more 2^-24, so one step
+// leaves a relative error below (2 + w / f)^2 2^-48: 5.7e-14 where f >= w / 2,
+// 5e-13 where f >= w / 10.
+__host__ __device__ __forceinline__ double recip_nr1_seeded(double f, float fs)
+{
+    if (!(fs > 1e-30f && fs < 1e30f)) return 1.0 / f;   // outside the FP32 seed's range
+    const double r = (double)(1.0f / fs);
+    return r * fma(-f, r, 2.0);
+}
 __host__ __device__ __forceinline__ double recip_nr(double f)
 {
     if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
@@ -1069,10 +1080,15 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     double maxabs = 0, xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        // x_i to 1.4e-14 relative: the update's Delta_i = f_i x_i then
-        // conserves mass and momentum to ~1e-16 per node and step, FP64's own
-        // rounding level
-        x[i] = (fe[i] - f[i]) * recip_nr1(f[i]);
+        // x_i to 1.4e-14 relative with FP64 storage: the update's
+        // Delta_i = f_i x_i then conserves mass and momentum to ~1e-16 per
+        // node and step, FP64's own rounding level.  With FP32 storage, whose
+        // stored values round at 6e-8, to ~6e-14 from an FP32 seed that needs
+        // no FP64 conversion.
+        if constexpr (sizeof(R) == 4)   // FP32 storage: seed from the FP32 deviation
+            x[i] = (fe[i] - f[i]) * recip_nr1_seeded(f[i], (float)L::w(i) + d[i]);
+        else
+            x[i] = (fe[i] - f[i]) * recip_nr1(f[i]);
         maxabs = fmax(maxabs, fabs(x[i]));
         xmin = fmin(xmin, x[i]);
         xmax = fmax(xmax, x[i]);
@@ -1088,12 +1104,13 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         bool solved = false;
         if (entropic && maxabs <= kSeriesMaxX) {
             // moments a_k and A from the series (no per-direction logarithm)
-            // a_2..a_7 in FP64; a_8..a_14 in FP32.  With |a_k| <= max|x|^(k-2) a_2
+            // a_2..a_6 in FP64; a_7..a_14 in FP32.  With |a_k| <= max|x|^(k-2) a_2
             // and a max|x| <= 0.1 over the series' range, term k of g is at most
-            // 2 (a max|x|)^(k-2) / (k (k-1)) of a^2 a_2 / 2: from k = 8 on below
-            // 3.6e-8, so FP32's relative error (< 2e-6 after 14 products and 19
-            // sums) moves g by less than 1e-13 of its scale, below the Newton
-            // tolerance of 1e-12 on alpha.
+            // 2 (a max|x|)^(k-2) / (k (k-1)) of a^2 a_2 / 2: from k = 7 on below
+            // 4.8e-7, so FP32's relative error (< 2e-6 after 14 products and 19
+            // sums) moves g by less than 1e-12 of its scale, the Newton tolerance
+            // on alpha, and by about 1e-13 at the roots met (alpha near 2 with
+            // max|x| <= 0.03: a max|x| <= 0.07, term 7 below 4e-8).
             double a[kSeriesK + 1];
             float ahi[kSeriesK - kSeriesK64];
 #pragma unroll

@@ -675,6 +675,7 @@ int lbm_mlp_train_cfg(const float* X_dev, const double* alpha_dev, int n, const 
     if (epochs < 1 || batch < 1 || !(lr > 0)) return mfail(LBM_EINVAL, "bad training config");
     if (cfg->kernel != LBM_MLP_FP32 && cfg->kernel != LBM_MLP_BF16_TC)
         return mfail(LBM_EINVAL, "kernel is LBM_MLP_FP32 or LBM_MLP_BF16_TC");
+    if (cfg->reserved != 0) return mfail(LBM_EINVAL, "lbm_mlp_cfg.reserved must be 0");
     const bool tc = cfg->kernel == LBM_MLP_BF16_TC;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int B = batch < n ? batch : n;

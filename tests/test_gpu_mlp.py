@@ -199,6 +199,9 @@ def test_tensor_core_training_lowers_loss_and_reports_throughput():
         for k, v in out.items()))
     with pytest.raises(lbm.LBMError):
         lbm.lbm_mlp_train_cfg(Xd, ad, len(X), 1, 256, 1e-3, 5, 7, np.zeros(1394, np.float32), None)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_train_cfg(Xd, ad, len(X), 0, 256, 1e-3, 5, lbm.LBM_MLP_BF16_TC,
+                              np.zeros(1394, np.float32), None)
 
 
 def test_training_lowers_loss():
