@@ -39,6 +39,7 @@ B_PER_NODE = {"f32s": 152, "f32": 152, "f16s": 76, "bf16s": 76, "f64": 304}   # 
 ESIZE = {"f32s": 4, "f32": 4, "f16s": 2, "bf16s": 2, "f64": 8}
 LATTICE_NAME = {0: "D2Q9", 1: "D3Q19", 2: "D3Q15", 3: "D3Q27"}
 LATTICE_Q = {0: 9, 1: 19, 2: 15, 3: 27}
+MODEL_NAME = {0: "LBGK", 1: "MRT", 2: "ELBM", 3: "REG", 4: "SMAG"}
 # lbm_set_masked_kernel modes (LBM_MASKED_AUTO, _NODE, _ZRUN)
 MASKED_KERNEL = {"auto": 0, "node": 1, "zrun": 2}
 
@@ -154,15 +155,21 @@ def fp64_inst_for(alpha, dtype):
     return float(e["fp64_warp_inst_per_node"])
 
 
-def traffic_for(workload, dtype):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    sources are unchanged since that capture; else None."""
+def traffic_key(workload, dtype, model, lattice):
+    """Key of a kernel's DRAM-traffic record: workload, storage, collision
+    model and lattice (a record holds for that kernel only)."""
+    return f"{workload}:{dtype}:{MODEL_NAME[model]}:{LATTICE_NAME[lattice]}"
+
+
+def traffic_for(workload, dtype, model, lattice):
+    """DRAM bytes per launch from the committed ncu summary for this kernel,
+    if its sources are unchanged since that capture; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(f"{workload}:{dtype}")
+    e = d.get(traffic_key(workload, dtype, model, lattice))
     if not e or e.get("source_sha") != source_sha():
         return None
     return float(e["bytes_per_launch"])
@@ -687,7 +694,7 @@ def run_ours(args):
     alg = algorithmic_bytes(nodes, fluid, bpn, 4)
     achieved = alg / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(args.workload, args.dtype)
+    traffic = traffic_for(args.workload, args.dtype, spec["model"], spec["lattice"])
     line = {
         "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
         "value": round(glups, 4),
