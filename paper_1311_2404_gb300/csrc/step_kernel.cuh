@@ -525,7 +525,10 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
     x2_body<L, S, MODEL, MASK>(p);
 }
 // MRT needs ~90 registers for two nodes; capped for 6 CTAs per SM it takes 80
-// without spilling and runs 6% faster on the FP16S vortex (61.7 -> 65.2 GLUPS)
+// without spilling and runs 6% faster on the FP16S vortex (61.7 -> 65.2 GLUPS).
+// Smagorinsky takes 80 uncapped; capped for 7 CTAs per SM (72 registers, a
+// 12-byte spill) the FP16S Kida vortex runs 14% faster (46.9 -> 53.6 GLUPS);
+// the regularized operator fits 72 either way.
 template <class L, class S, int MODEL, bool MASK, int MINB>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_stream_collide_x2_occ(const StepParams p)
 {
@@ -574,6 +577,8 @@ cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t 
                 k_stream_collide_x2<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
             else if constexpr (MODEL == MODEL_MRT)
                 k_stream_collide_x2_occ<L, S, MODEL, false, 6><<<grid, block, 0, s>>>(p);
+            else if constexpr (MODEL == MODEL_SMAG || MODEL == MODEL_REG)
+                k_stream_collide_x2_occ<L, S, MODEL, false, 7><<<grid, block, 0, s>>>(p);
             else
                 k_stream_collide_x2<L, S, MODEL, false><<<grid, block, 0, s>>>(p);
             return cudaGetLastError();
