@@ -528,7 +528,11 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
 // without spilling and runs 6% faster on the FP16S vortex (61.7 -> 65.2 GLUPS).
 // Smagorinsky takes 80 uncapped; capped for 7 CTAs per SM (72 registers, a
 // 12-byte spill) the FP16S Kida vortex runs 14% faster (46.9 -> 53.6 GLUPS);
-// the regularized operator fits 72 either way.
+// the regularized operator fits 72 either way.  The masked LBGK pair takes 95
+// (5 CTAs); capped for 6 (80 registers, a 16-byte spill in FP16S) the FP16S
+// cavity runs 8.5% faster (51.1 -> 55.5 GLUPS).  The unmasked LBGK pair at 69
+// registers gains nothing from a cap for 8 CTAs (64 registers: FP16S vortex
+// 73.5 -> 72.6, BF16S 67.4 -> 68.8 GLUPS).
 template <class L, class S, int MODEL, bool MASK, int MINB>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_stream_collide_x2_occ(const StepParams p)
 {
@@ -573,14 +577,18 @@ cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t 
             const dim3 block = step_block_x2(p.nxp);
             const dim3 grid(((p.nx + 1) / 2 + block.x - 1) / block.x,
                             ((d2 ? p.nrows : p.ny) + block.y - 1) / block.y, d2 ? 1 : p.nrows);
-            if (mask)
-                k_stream_collide_x2<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
-            else if constexpr (MODEL == MODEL_MRT)
+            if (mask) {
+                if constexpr (MODEL == MODEL_BGK)
+                    k_stream_collide_x2_occ<L, S, MODEL, true, 6><<<grid, block, 0, s>>>(p);
+                else
+                    k_stream_collide_x2<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
+            } else if constexpr (MODEL == MODEL_MRT) {
                 k_stream_collide_x2_occ<L, S, MODEL, false, 6><<<grid, block, 0, s>>>(p);
-            else if constexpr (MODEL == MODEL_SMAG || MODEL == MODEL_REG)
+            } else if constexpr (MODEL == MODEL_SMAG || MODEL == MODEL_REG) {
                 k_stream_collide_x2_occ<L, S, MODEL, false, 7><<<grid, block, 0, s>>>(p);
-            else
+            } else {
                 k_stream_collide_x2<L, S, MODEL, false><<<grid, block, 0, s>>>(p);
+            }
             return cudaGetLastError();
         }
     }
