@@ -454,7 +454,11 @@ __device__ __forceinline__ void batch2_body(const BatchParams& bp)
 
 // Register budgets per instance (launches of up to 512 threads would allow
 // 128; the compiler then spends them and occupancy drops): the largest
-// budget without spills, measured with -Xptxas -v.
+// budget without spills, measured with -Xptxas -v, except the one-row FP16S
+// instance: capped at 64 (84 bytes of spill) it runs two 512-thread CTAs per
+// SM and the 512-channel ensemble 87.0 -> 89.9 GLUPS; at 72 the autotuner
+// takes 128-thread CTAs (88.0), at 56 it falls back to the two-row kernel
+// (83.7).
 template <class S, int NPT, int MAXR>
 __global__ void __maxnreg__(MAXR) k_batch2(const BatchParams bp)
 {
@@ -1005,7 +1009,7 @@ static const void* kernel_for(int dtype, int npt)
     if (npt < 0) {
         if (dtype == LBM_F16S)
             return npt == -2 ? batch2_kernel_ptr<StoreF16S, 2, 104>()
-                             : batch2_kernel_ptr<StoreF16S, 1, 80>();
+                             : batch2_kernel_ptr<StoreF16S, 1, 64>();
         return npt == -2 ? batch2_kernel_ptr<StoreF32S, 2, 128>()
                          : batch2_kernel_ptr<StoreF32S, 1, 96>();
     }
