@@ -475,7 +475,9 @@ typedef struct lbm_train_stats {
 } lbm_train_stats;
 
 /* lbm_mlp_train with the configuration as a struct and the kernel choice;
- * stats may be NULL.  LBM_EINVAL for a bad configuration.  Synchronises.
+ * stats may be NULL.  LBM_EINVAL for a bad configuration, and with
+ * LBM_MLP_BF16_TC for an X_dev that is not 8-byte aligned (the kernel reads
+ * feature pairs).  Synchronises.
  * lbm_mlp_train is this call with kernel LBM_MLP_FP32. */
 LBM_API int lbm_mlp_train_cfg(const float* X_dev, const double* alpha_dev, int n,
                               const lbm_mlp_cfg* cfg, float* params, float* loss_out,
@@ -488,7 +490,8 @@ LBM_API int lbm_mlp_grad(const float* X_dev, const float* t_dev, int n, const fl
                  float* loss, float* grad, void* cuda_stream);
 
 /* lbm_mlp_grad with the LBM_MLP_BF16_TC kernel: the loss and gradient of the
- * network whose entries 16 .. 1392 are rounded to BF16. */
+ * network whose entries 16 .. 1392 are rounded to BF16.  X_dev must be
+ * 8-byte aligned (LBM_EINVAL otherwise). */
 LBM_API int lbm_mlp_grad_tc(const float* X_dev, const float* t_dev, int n, const float* params,
                             float* loss, float* grad, void* cuda_stream);
 

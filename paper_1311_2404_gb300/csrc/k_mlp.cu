@@ -624,6 +624,8 @@ static int mlp_grad_impl(const float* X_dev, const float* t_dev, int n, const fl
     if (!X_dev || !t_dev || !params || !loss || !grad || n < 1)
         return mfail(LBM_EINVAL, "bad arguments");
     if (!is_dev(X_dev) || !is_dev(t_dev)) return mfail(LBM_EINVAL, "X, t must be device memory");
+    if (tc && (reinterpret_cast<uintptr_t>(X_dev) & 7u))
+        return mfail(LBM_EINVAL, "X must be 8-byte aligned for the tensor-core kernel");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nblk = (n + BS - 1) / BS;
     DevBuf P, G, part, pl, la;
@@ -677,6 +679,9 @@ int lbm_mlp_train_cfg(const float* X_dev, const double* alpha_dev, int n, const 
         return mfail(LBM_EINVAL, "kernel is LBM_MLP_FP32 or LBM_MLP_BF16_TC");
     if (cfg->reserved != 0) return mfail(LBM_EINVAL, "lbm_mlp_cfg.reserved must be 0");
     const bool tc = cfg->kernel == LBM_MLP_BF16_TC;
+    // the tensor-core kernel reads each sample's feature pairs as 8-byte loads
+    if (tc && (reinterpret_cast<uintptr_t>(X_dev) & 7u))
+        return mfail(LBM_EINVAL, "X must be 8-byte aligned for the tensor-core kernel");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int B = batch < n ? batch : n;
     const int nblk = (B + BS - 1) / BS;

@@ -202,6 +202,14 @@ def test_tensor_core_training_lowers_loss_and_reports_throughput():
     with pytest.raises(lbm.LBMError):
         lbm.lbm_mlp_train_cfg(Xd, ad, len(X), 0, 256, 1e-3, 5, lbm.LBM_MLP_BF16_TC,
                               np.zeros(1394, np.float32), None)
+    # a feature array one float off an 8-byte boundary is refused, not read
+    Xo = torch.zeros(len(X) * 8 + 1, dtype=torch.float32, device="cuda")[1:]
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_train_cfg(Xo.data_ptr(), ad, len(X), 1, 256, 1e-3, 5, lbm.LBM_MLP_BF16_TC,
+                              np.zeros(1394, np.float32), None)
+    td = torch.zeros(len(X), dtype=torch.float32, device="cuda")
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_grad_tc(Xo.data_ptr(), td, len(X), np.zeros(1394, np.float32))
 
 
 def test_training_lowers_loss():
