@@ -1270,13 +1270,15 @@ int lbm_batch_init_equilibrium(lbm_batch b, int d, const void* rho, const void* 
     const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
     const size_t nb = (size_t)D.nx * D.ny * fs;
     char* stage = b->base + b->off_stage;
-    const void* dr = rho;
-    const void* du = u;
-    if (!dev_ptr(rho)) {
+    // device memory and pinned host memory are read in place by the init
+    // kernel; pageable host memory is staged
+    const void* dr = kernel_view(rho);
+    const void* du = kernel_view(u);
+    if (!dr) {
         BCK(b, cudaMemcpyAsync(stage, rho, nb, cudaMemcpyHostToDevice, b->stream), "copy rho");
         dr = stage;
     }
-    if (!dev_ptr(u)) {
+    if (!du) {
         BCK(b, cudaMemcpyAsync(stage + nb, u, 2 * nb, cudaMemcpyHostToDevice, b->stream),
             "copy u");
         du = stage + nb;
@@ -1535,19 +1537,23 @@ int lbm_batch_get_macro(lbm_batch b, int d, void* rho, void* u, int field_dtype)
     const size_t fs = f32 ? 4 : 8;
     const size_t nb = (size_t)D.nx * D.ny * fs;
     char* stage = b->base + b->off_stage;
-    struct { void* dst; long long off; int nf; } parts[2] = {{rho, 0, 1}, {u, D.sq * 4, 2}};
+    // device memory and pinned host memory are written in place by the pack
+    // kernel; pageable host memory is staged (rho at the start of the staging
+    // area, u after it) and copied out.  One synchronisation, in
+    // lbm_batch_sync, covers both fields and the status word.
+    struct { void* dst; long long off; int nf; size_t soff; } parts[2] = {
+        {rho, 0, 1, 0}, {u, D.sq * 4, 2, nb}};
     for (auto& pt : parts) {
         if (!pt.dst) continue;
-        const bool dv = dev_ptr(pt.dst);
-        void* outp = dv ? pt.dst : stage;
+        void* view = const_cast<void*>(kernel_view(pt.dst));
+        void* outp = view ? view : stage + pt.soff;
         BCK(b, launch_pack(0, b->base + D.offO + pt.off, f32, outp, pt.nf, D.nx, D.ny, 1, D.nxp,
                            D.sq, pt.off == 0 ? 1.0 : 0.0, b->stream),
             "pack kernel");
         b->launches += 1;
-        if (!dv)
+        if (!view)
             BCK(b, cudaMemcpyAsync(pt.dst, outp, nb * pt.nf, cudaMemcpyDeviceToHost, b->stream),
                 "copy out");
-        BCK(b, cudaStreamSynchronize(b->stream), "synchronise");
     }
     return lbm_batch_sync(b);
 }

@@ -124,23 +124,6 @@ static bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// An address the kernels can use for p: p itself for device or managed
-// memory, the mapped device address of pinned host memory (read or written
-// in place over the CPU-GPU link, no staging copy), or nullptr for pageable
-// host memory, which goes through the staging area.
-static const void* kernel_view(const void* p)
-{
-    cudaPointerAttributes a;
-    cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
-    return nullptr;
-}
-
 static void default_rates(double tau, double* s)
 {
     for (int k = 0; k < 19; ++k) s[k] = 0.0;
@@ -180,6 +163,23 @@ static T* at(lbm_ctx* h, size_t off) { return reinterpret_cast<T*>(h->base + off
 static std::atomic<int> g_fail_allocs{0};
 
 namespace lbm {
+// An address the kernels can use for p: p itself for device or managed
+// memory, the mapped device address of pinned host memory (read or written
+// in place over the CPU-GPU link, no staging copy), or nullptr for pageable
+// host memory, which goes through a staging area.
+const void* kernel_view(const void* p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes)
 {
     int n = g_fail_allocs.load();
@@ -545,8 +545,8 @@ int lbm_init_equilibrium(lbm_handle h, const void* rho, const void* u, int field
     if (r) return r;
     const size_t fs = field_dtype == LBM_FIELD_F64 ? 8 : 4;
     const size_t nb = (size_t)h->N * fs;
-    const void* drho = kernel_view(rho);
-    const void* du = kernel_view(u);
+    const void* drho = lbm::kernel_view(rho);
+    const void* du = lbm::kernel_view(u);
     char* stage = at<char>(h, h->off_stage);
     // host memory (pinned: read in place; pageable: staged) is released to the
     // caller only after the init kernel has read it
@@ -735,7 +735,7 @@ static int get_field(lbm_ctx* h, size_t src_off, int nfields, void* dst, int fie
     const size_t fs = dst_f32 ? 4 : 8;
     const size_t nb = (size_t)h->N * fs * nfields;
     // device or pinned host memory is written in place; pageable memory is staged
-    void* view = const_cast<void*>(kernel_view(dst));
+    void* view = const_cast<void*>(lbm::kernel_view(dst));
     void* out = view ? view : h->base + h->off_stage;
     CK(h, launch_pack(h->rsize == 8, h->base + src_off, dst_f32, out, nfields, h->nx, h->ny,
                       h->nz, h->nxp, h->sq, src_off == h->off_rho ? 1.0 : 0.0, h->stream),

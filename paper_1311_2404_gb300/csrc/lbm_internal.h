@@ -14,6 +14,9 @@ constexpr int kReduceBlocks = 1024;   // FP64 partial sums: kReduceBlocks x 5 do
 // lbm_debug_fail_allocations can make the next ones fail (out of memory)
 // without calling cudaMalloc: the error paths are tested on the host.
 cudaError_t dev_alloc(void** p, size_t bytes);
+// p for device memory, the mapped device address of pinned host memory, or
+// nullptr for pageable host memory (which must be staged)
+const void* kernel_view(const void* p);
 
 cudaError_t launch_step_bgk(int lattice, int store, const StepParams& p, bool mask, bool aa,
                             cudaStream_t s);

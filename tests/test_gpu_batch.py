@@ -269,3 +269,43 @@ def test_set_config_rejects_bad_values():
         assert ei.value.code == lbm.LBM_EINVAL
         assert list(lbm.lbm_batch_get_config(b)) == before
     lbm.lbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("dtype", [lbm.LBM_F32S, lbm.LBM_F16S])
+def test_host_buffer_kinds_agree(dtype):
+    """Initial fields and read-back through pageable (staged), pinned (read
+    and written in place by the kernels) and device buffers give the same
+    bits, for FP32 and FP64 fields."""
+    specs = _specs(4, seed=17)
+    results = []
+    for kind in ("pageable", "pinned", "device"):
+        b = lbm.lbm_batch_create([s["nx"] for s in specs], [s["ny"] for s in specs],
+                                 [s["tau"] for s in specs], dtype)
+        for d, s in enumerate(specs):
+            lbm.lbm_batch_set_geometry(b, d, wl.batch_channel_mask(s))
+            lbm.lbm_batch_set_force(b, d, s["gx"], 0.0)
+            rho, u = _init_state(s, 100 + d)
+            r = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32))
+            v = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32))
+            if kind == "pinned":
+                r, v = r.pin_memory(), v.pin_memory()
+            elif kind == "device":
+                r, v = r.cuda(), v.cuda()
+            lbm.lbm_batch_init_equilibrium(b, d, r, v)
+        lbm.lbm_batch_step(b, 6)
+        out = []
+        for d, s in enumerate(specs):
+            for fdt in (torch.float32, torch.float64):
+                ro = torch.empty((1, s["ny"], s["nx"]), dtype=fdt)
+                uo = torch.empty((2, 1, s["ny"], s["nx"]), dtype=fdt)
+                if kind == "pinned":
+                    ro, uo = ro.pin_memory(), uo.pin_memory()
+                elif kind == "device":
+                    ro, uo = ro.cuda(), uo.cuda()
+                lbm.lbm_batch_get_macro(b, d, ro, uo)
+                out.append((ro.cpu().numpy(), uo.cpu().numpy()))
+        lbm.lbm_batch_destroy(b)
+        results.append(out)
+    for other in results[1:]:
+        for (r1, u1), (r2, u2) in zip(results[0], other):
+            assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
