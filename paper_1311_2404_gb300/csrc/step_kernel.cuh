@@ -530,7 +530,9 @@ __global__ void __launch_bounds__(kStepThreads) k_stream_collide_x2(const StepPa
 // 12-byte spill) the FP16S Kida vortex runs 14% faster (46.9 -> 53.6 GLUPS);
 // the regularized operator fits 72 either way.  The masked LBGK pair takes 95
 // (5 CTAs); capped for 6 (80 registers, a 16-byte spill in FP16S) the FP16S
-// cavity runs 8.5% faster (51.1 -> 55.5 GLUPS).  The unmasked LBGK pair at 69
+// cavity runs 8.5% faster (51.1 -> 55.5 GLUPS).  Both caps hold for up to 19
+// directions: D3Q27 pairs need ~95-114 registers and would spill 300-400
+// bytes under them.  The unmasked LBGK pair at 69
 // registers gains nothing from a cap for 8 CTAs (64 registers: FP16S vortex
 // 73.5 -> 72.6, BF16S 67.4 -> 68.8 GLUPS).
 template <class L, class S, int MODEL, bool MASK, int MINB>
@@ -578,13 +580,13 @@ cudaError_t launch_step_t(const StepParams& p, bool mask, bool aa, cudaStream_t 
             const dim3 grid(((p.nx + 1) / 2 + block.x - 1) / block.x,
                             ((d2 ? p.nrows : p.ny) + block.y - 1) / block.y, d2 ? 1 : p.nrows);
             if (mask) {
-                if constexpr (MODEL == MODEL_BGK)
+                if constexpr (MODEL == MODEL_BGK && L::Q <= 19)
                     k_stream_collide_x2_occ<L, S, MODEL, true, 6><<<grid, block, 0, s>>>(p);
                 else
                     k_stream_collide_x2<L, S, MODEL, true><<<grid, block, 0, s>>>(p);
             } else if constexpr (MODEL == MODEL_MRT) {
                 k_stream_collide_x2_occ<L, S, MODEL, false, 6><<<grid, block, 0, s>>>(p);
-            } else if constexpr (MODEL == MODEL_SMAG || MODEL == MODEL_REG) {
+            } else if constexpr ((MODEL == MODEL_SMAG || MODEL == MODEL_REG) && L::Q <= 19) {
                 k_stream_collide_x2_occ<L, S, MODEL, false, 7><<<grid, block, 0, s>>>(p);
             } else {
                 k_stream_collide_x2<L, S, MODEL, false><<<grid, block, 0, s>>>(p);
