@@ -697,6 +697,15 @@ __host__ __device__ __forceinline__ void mrt_collide(R (&d)[19], const StepParam
 // ---------------------------------------------------------------------------
 // ELBM
 // ---------------------------------------------------------------------------
+// FP64 sum of the lattice weights in index order, folded at compile time.
+template <class L>
+__host__ __device__ constexpr double weight_sum()
+{
+    double s = 0.0;
+    for (int i = 0; i < L::Q; ++i) s += L::w(i);
+    return s;
+}
+
 // Entropic equilibrium, Sec. 2.1.3, with the first factor read as
 // 2 - sqrt(1 + 3 u^2) and mass and momentum put back along the zeroth and
 // first Hermite directions (variant 0); or the polynomial equilibrium
@@ -1025,7 +1034,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     // equilibrium; for the entropic form also its pieces: f_eq_i = P_i (1 + y_i)
     // with P_i = c0 w_i prod_a r_a^e_ia (ln(P_i / w_i) affine in e_i) and y_i the
     // relative mass/momentum restoration
-    double lc0 = 0, lr[3] = {0, 0, 0};
+    double lc0 = 0;
     const bool entropic = (p.feq_variant == 0);
     if (entropic) {
         double c[3], r[3], ri[3];
@@ -1069,11 +1078,12 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             y[i] *= corr;                               // w_i corr / P_i
         }
         // ln c0 and ln r_a enter A only as ln c0 sum Delta and ln r_a
-        // sum e_a Delta, sums that vanish up to rounding (the restored f_eq
-        // has f's mass and momentum); FP32 logarithms change A by ~1e-19
+        // sum e_a Delta.  The restored f_eq carries f's momentum, so
+        // sum e_a Delta vanishes up to rounding (~1e-19); its mass is
+        // 1 + drho while f_i = w_i + d_i carries sum w_i + drho, so
+        // sum Delta = 1 - sum w_i (an ulp of the FP64 weights) up to rounding.
+        // A keeps ln c0 (1 - sum w_i); an FP32 logarithm changes it by ~1e-26.
         lc0 = (double)logf((float)c0);
-#pragma unroll
-        for (int a = 0; a < L::D; ++a) lr[a] = (double)logf((float)r[a]);
     } else {
         elbm_feq<L>(rho, u, 1, fe);
     }
@@ -1117,7 +1127,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             for (int k = 0; k <= kSeriesK; ++k) a[k] = 0;
 #pragma unroll
             for (int k = 0; k < kSeriesK - kSeriesK64; ++k) ahi[k] = 0.f;
-            double s0 = 0, s1[3] = {0, 0, 0}, sy = 0;
+            double sy = 0;
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
                 const double Dl = f[i] * x[i];
@@ -1135,23 +1145,20 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                     pwf *= xf;
                     ahi[k] += pwf;
                 }
-                s0 += Dl;
-                s1[0] += L::ex(i) * Dl;
-                s1[1] += L::ey(i) * Dl;
-                s1[2] += L::ez(i) * Dl;
                 const double yi = y[i];
                 sy = fma(Dl, yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
             }
 #pragma unroll
             for (int k = 0; k < kSeriesK - kSeriesK64; ++k) a[kSeriesK64 + 1 + k] = (double)ahi[k];
             // A = sum Delta ln(f_eq/w) - sum Delta log1p(x), with
-            // sum Delta ln(f_eq/w) = ln c0 s0 + sum_a ln r_a s1_a + sum Delta log1p(y)
-            // and sum Delta log1p(x) = sum_{n>=1} (-1)^(n+1) a_(n+1) / n
+            // sum Delta ln(f_eq/w) = ln c0 (1 - sum w) + sum Delta log1p(y)
+            // (the ln r_a sum e_a Delta terms vanish, see above) and
+            // sum Delta log1p(x) = sum_{n>=1} (-1)^(n+1) a_(n+1) / n
             double sl = 0;
 #pragma unroll
             for (int n = kSeriesK - 1; n >= 1; --n)
                 sl = fma(a[n + 1], ((n & 1) ? 1.0 : -1.0) * (1.0 / n), sl);
-            A = fma(lc0, s0, fma(lr[0], s1[0], fma(lr[1], s1[1], fma(lr[2], s1[2], sy - sl))));
+            A = fma(lc0, 1.0 - weight_sum<L>(), sy - sl);
             SeriesEval ev;
 #pragma unroll
             for (int k = 2; k <= kSeriesK; ++k)
