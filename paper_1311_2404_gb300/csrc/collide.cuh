@@ -885,12 +885,16 @@ __host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, 
 //   4  the root of g(alpha)/alpha with g's series truncated after a_6 and the
 //      node's own A (exact for any f_eq; three Newton steps from s2 on
 //      h(a) = A1 + sum_{k=2}^{6} (-1)^k a_k a^(k-1) / (k (k-1))).
+__host__ __device__ __forceinline__ double recip_nr1(double f);   // defined below
+
 __host__ __device__ __forceinline__ double alpha_guess(const StepParams& p, const float* smlp,
                                                        const double (&ak)[7], double A1,
                                                        const double (&feat)[8])
 {
-    const double s2 = 2.0 + (ak[3] - 2.0 * ak[4]) / (3.0 * ak[2]) +
-                      4.0 * ak[3] * ak[3] / (9.0 * ak[2] * ak[2]);
+    // one division: (a_3 - 2 a_4) / (3 a_2) + 4 a_3^2 / (9 a_2^2) with q = a_3 / a_2
+    const double ia2 = 1.0 / ak[2];
+    const double q = ak[3] * ia2;
+    const double s2 = 2.0 + (ak[3] - 2.0 * ak[4]) * ia2 * (1.0 / 3.0) + (4.0 / 9.0) * q * q;
     if (p.alpha_mode == 2)
         return s2 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat);
     if (p.alpha_mode != 4) return s2;
@@ -901,7 +905,7 @@ __host__ __device__ __forceinline__ double alpha_guess(const StepParams& p, cons
     for (int it = 0; it < 3; ++it) {
         const double h = fma(a, fma(a, fma(a, fma(a, fma(a, c6, c5), c4), c3), c2), A1);
         const double hp = fma(a, fma(a, fma(a, fma(a, 5.0 * c6, 4.0 * c5), 3.0 * c4), 2.0 * c3), c2);
-        a -= h / hp;
+        a -= h * recip_nr1(hp);   // Newton corrects the reciprocal's 1e-14 itself
     }
     return a;
 }
@@ -1108,7 +1112,9 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     // positivity limit: f_i + a f_i x_i > 0 for all i  <=>  a < -1 / min x
     const double amax = xmin < -1e-30 ? recip_nr(-xmin) : 1e300;
     if (p.alpha_mode != 3 && maxabs >= p.skip_eps && amax < 1e300) {
-        const bool want_feat = alpha_guarded(p.alpha_mode) || p.pairs_X != nullptr;
+        // the invariant features feed the learned guess and the pair collection
+        // only; the series and root guesses use the moments themselves
+        const bool want_feat = p.alpha_mode == 2 || p.pairs_X != nullptr;
         double ak[7];
         double A = 0;
         bool solved = false;
@@ -1172,8 +1178,8 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             if (want_feat) {
                 elbm_features(ak, xmax, xmin, rho, A, feat);
                 have_feat = true;
-                if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, ev.A1, feat);
             }
+            if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, ev.A1, feat);
             ar = elbm_solve(ev, amax, p, guess, 0);
             solved = (ar.status != ALPHA_NEEDS_LOG);
         }
@@ -1198,8 +1204,8 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             if (want_feat) {
                 elbm_features(ak, xmax, xmin, rho, A, feat);
                 have_feat = true;
-                if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, A + ak[1], feat);
             }
+            if (alpha_guarded(p.alpha_mode)) guess = alpha_guess(p, smlp, ak, A + ak[1], feat);
             LogEval<L> ev{f, x, A};
             ar = elbm_solve(ev, amax, p, guess, ar.evals);
         }
