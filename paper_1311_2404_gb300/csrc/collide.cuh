@@ -1073,12 +1073,12 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         // put the residual mass and momentum back (zero up to rounding on
         // D2Q9, O(u^3) on D3Q19): the root of g shifts with f_eq's mass defect
         const double dr = rho - m0;
-        const double dj0 = rho * u[0] - m1[0], dj1 = rho * u[1] - m1[1],
-                     dj2 = rho * u[2] - m1[2];
+        const double dj0 = fma(rho, u[0], -m1[0]), dj1 = fma(rho, u[1], -m1[1]),
+                     dj2 = fma(rho, u[2], -m1[2]);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const double corr = dr + 3.0 * (L::ex(i) * dj0 + L::ey(i) * dj1 + L::ez(i) * dj2);
-            fe[i] += L::w(i) * corr;
+            const double corr = fma(3.0, L::ex(i) * dj0 + L::ey(i) * dj1 + L::ez(i) * dj2, dr);
+            fe[i] = fma(L::w(i), corr, fe[i]);
             y[i] *= corr;                               // w_i corr / P_i
         }
         // ln c0 and ln r_a enter A only as ln c0 sum Delta and ln r_a
@@ -1091,7 +1091,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     } else {
         elbm_feq<L>(rho, u, 1, fe);
     }
-    double maxabs = 0, xmin = 1e300, xmax = -1e300;
+    double xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         // x_i to 1.4e-14 relative with FP64 storage: the update's
@@ -1103,10 +1103,10 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             x[i] = (fe[i] - f[i]) * recip_nr1_seeded(f[i], (float)L::w(i) + d[i]);
         else
             x[i] = (fe[i] - f[i]) * recip_nr1(f[i]);
-        maxabs = fmax(maxabs, fabs(x[i]));
         xmin = fmin(xmin, x[i]);
         xmax = fmax(xmax, x[i]);
     }
+    const double maxabs = fmax(-xmin, xmax);   // max |x_i|, exactly
     AlphaResult ar{2.0, 0, ALPHA_SKIP};
     have_feat = false;
     // positivity limit: f_i + a f_i x_i > 0 for all i  <=>  a < -1 / min x
@@ -1145,7 +1145,16 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                     a[k] += pw;
                 }
                 const float xf = (float)x[i];
-                float pwf = (float)pw;
+                // f x^6 in FP32; with FP32 storage from the stored deviation,
+                // which needs no FP64 conversion (FP32 rounding of these high
+                // orders stays within the bound above)
+                float pwf;
+                if constexpr (sizeof(R) == 4) {
+                    const float x3 = xf * xf * xf;
+                    pwf = ((float)L::w(i) + d[i]) * (x3 * x3);
+                } else {
+                    pwf = (float)pw;
+                }
 #pragma unroll
                 for (int k = 0; k < kSeriesK - kSeriesK64; ++k) {
                     pwf *= xf;
