@@ -885,29 +885,34 @@ __host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, 
 //   4  the root of g(alpha)/alpha with g's series truncated after a_6 and the
 //      node's own A (exact for any f_eq; three Newton steps from s2 on
 //      h(a) = A1 + sum_{k=2}^{6} (-1)^k a_k a^(k-1) / (k (k-1))).
-__host__ __device__ __forceinline__ double recip_nr1(double f);   // defined below
-
+// A guess only seeds the FP64 Newton solve, which takes it after one FP64
+// correction of at most guard_tol * alpha, so it is formed in FP32, on the
+// moments divided by a_2: its rounding (~1e-7 of alpha) is well inside that
+// bound, and the corrected alpha is off by about the correction squared.
+// Below a_2 = 1e-30 (FP32's normal range ends at 1.2e-38) the guess is 2.
 __host__ __device__ __forceinline__ double alpha_guess(const StepParams& p, const float* smlp,
                                                        const double (&ak)[7], double A1,
                                                        const double (&feat)[8])
 {
-    // one division: (a_3 - 2 a_4) / (3 a_2) + 4 a_3^2 / (9 a_2^2) with q = a_3 / a_2
-    const double ia2 = 1.0 / ak[2];
-    const double q = ak[3] * ia2;
-    const double s2 = 2.0 + (ak[3] - 2.0 * ak[4]) * ia2 * (1.0 / 3.0) + (4.0 / 9.0) * q * q;
-    if (p.alpha_mode == 2)
-        return s2 + (double)smlp[MLP_NPARAM - 1] * (double)mlp_eval(smlp, feat);
-    if (p.alpha_mode != 4) return s2;
-    const double c2 = ak[2] * 0.5, c3 = ak[3] * (-1.0 / 6.0), c4 = ak[4] * (1.0 / 12.0),
-                 c5 = ak[5] * (-1.0 / 20.0), c6 = ak[6] * (1.0 / 30.0);
-    double a = s2;
+    const float a2 = (float)ak[2];
+    if (!(a2 > 1e-30f)) return 2.0;
+    const float ia2 = 1.0f / a2;
+    const float q3 = (float)ak[3] * ia2, q4 = (float)ak[4] * ia2;
+    const float s2 = fmaf(4.0f / 9.0f, q3 * q3, fmaf(fmaf(-2.0f, q4, q3), 1.0f / 3.0f, 2.0f));
+    if (p.alpha_mode == 2) return (double)fmaf(smlp[MLP_NPARAM - 1], mlp_eval(smlp, feat), s2);
+    if (p.alpha_mode != 4) return (double)s2;
+    // h / a_2 with c_2 / a_2 = 1/2
+    const float c1 = (float)A1 * ia2, c3 = q3 * (-1.0f / 6.0f), c4 = q4 * (1.0f / 12.0f),
+                c5 = (float)ak[5] * ia2 * (-1.0f / 20.0f), c6 = (float)ak[6] * ia2 * (1.0f / 30.0f);
+    float a = s2;
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
-        const double h = fma(a, fma(a, fma(a, fma(a, fma(a, c6, c5), c4), c3), c2), A1);
-        const double hp = fma(a, fma(a, fma(a, fma(a, 5.0 * c6, 4.0 * c5), 3.0 * c4), 2.0 * c3), c2);
-        a -= h * recip_nr1(hp);   // Newton corrects the reciprocal's 1e-14 itself
+        const float h = fmaf(a, fmaf(a, fmaf(a, fmaf(a, fmaf(a, c6, c5), c4), c3), 0.5f), c1);
+        const float hp =
+            fmaf(a, fmaf(a, fmaf(a, fmaf(a, 5.0f * c6, 4.0f * c5), 3.0f * c4), 2.0f * c3), 0.5f);
+        a -= h / hp;
     }
-    return a;
+    return (double)a;
 }
 
 struct AlphaResult {
@@ -1091,18 +1096,21 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     } else {
         elbm_feq<L>(rho, u, 1, fe);
     }
+    // Delta_i = f_eq,i - f_i replaces f_eq in its registers; the update, A and
+    // the moments take it as it is, and x_i = Delta_i / f_i
+    double (&Dl)[L::Q] = fe;
     double xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        // x_i to 1.4e-14 relative with FP64 storage: the update's
-        // Delta_i = f_i x_i then conserves mass and momentum to ~1e-16 per
-        // node and step, FP64's own rounding level.  With FP32 storage, whose
+        // x_i to 1.4e-14 relative with FP64 storage: Delta_i = f_i x_i then
+        // holds to FP64's own rounding level.  With FP32 storage, whose
         // stored values round at 6e-8, to ~6e-14 from an FP32 seed that needs
         // no FP64 conversion.
+        Dl[i] = fe[i] - f[i];
         if constexpr (sizeof(R) == 4)   // FP32 storage: seed from the FP32 deviation
-            x[i] = (fe[i] - f[i]) * recip_nr1_seeded(f[i], (float)L::w(i) + d[i]);
+            x[i] = Dl[i] * recip_nr1_seeded(f[i], (float)L::w(i) + d[i]);
         else
-            x[i] = (fe[i] - f[i]) * recip_nr1(f[i]);
+            x[i] = Dl[i] * recip_nr1(f[i]);
         xmin = fmin(xmin, x[i]);
         xmax = fmax(xmax, x[i]);
     }
@@ -1136,8 +1144,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             double sy = 0;
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const double Dl = f[i] * x[i];
-                double pw = Dl;
+                double pw = Dl[i];
                 a[1] += pw;
 #pragma unroll
                 for (int k = 2; k <= kSeriesK64; ++k) {
@@ -1161,7 +1168,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                     ahi[k] += pwf;
                 }
                 const double yi = y[i];
-                sy = fma(Dl, yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
+                sy = fma(Dl[i], yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
             }
 #pragma unroll
             for (int k = 0; k < kSeriesK - kSeriesK64; ++k) a[kSeriesK64 + 1 + k] = (double)ahi[k];
@@ -1199,10 +1206,9 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             for (int k = 0; k < 7; ++k) ak[k] = 0;
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const double Dl = f[i] * x[i];
-                A += Dl * log(f[i] / L::w(i));
-                ak[1] += Dl;
-                const double p2 = Dl * x[i];
+                A += Dl[i] * log(f[i] / L::w(i));
+                ak[1] += Dl[i];
+                const double p2 = Dl[i] * x[i];
                 ak[2] += p2;
                 ak[3] += p2 * x[i];
                 ak[4] += p2 * x[i] * x[i];
@@ -1223,7 +1229,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
             // (per-direction logarithms): also measures the series truncation
             double Al = 0;
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) Al = fma(f[i] * x[i], log(f[i] / L::w(i)), Al);
+            for (int i = 0; i < L::Q; ++i) Al = fma(Dl[i], log(f[i] / L::w(i)), Al);
             LogEval<L> evd{f, x, Al};
             double g, gp;
             evd(ar.alpha, g, gp);
@@ -1238,11 +1244,11 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         double fs[L::Q];
         elbm_feq<L>(rho, us, p.feq_variant, fs);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i)
-            d[i] = (R)(fma(ab, f[i] * x[i], f[i] - L::w(i)) + (fs[i] - fe[i]));
+        for (int i = 0; i < L::Q; ++i)   // f_eq(u + F/rho) - f_eq(u) added
+            d[i] = (R)(fma(ab, Dl[i], f[i] - L::w(i)) + (fs[i] - (f[i] + Dl[i])));
     } else {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) d[i] = (R)fma(ab, f[i] * x[i], f[i] - L::w(i));
+        for (int i = 0; i < L::Q; ++i) d[i] = (R)fma(ab, Dl[i], f[i] - L::w(i));
     }
     drho_out = (R)drho;
     vout[0] = (R)(u[0] + 0.5 * p.F[0] * irho);
