@@ -125,9 +125,10 @@ def peaks():
 
 # the sources of the headline kernel (LBGK stream-collide): its translation
 # unit and the headers it includes
-KERNEL_SOURCES = ("k_bgk.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh")
+KERNEL_SOURCES = ("k_bgk.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh",
+                  "fp_bits.cuh")
 # the ELBM kernel's
-ELBM_SOURCES = ("k_elbm.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh")
+ELBM_SOURCES = ("k_elbm.cu", "step_kernel.cuh", "collide.cuh", "lbm_device.cuh", "fp_bits.cuh")
 
 
 def source_sha(names=KERNEL_SOURCES):

@@ -15,6 +15,7 @@
 // FP64), so the output keeps the precision of the deviation form.
 #pragma once
 
+#include "fp_bits.cuh"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -988,14 +989,19 @@ __host__ __device__ AlphaResult elbm_solve(const Ev& ev, double amax, const Step
 }
 
 // Reciprocal in FP64 from an FP32 seed refined by two Newton-Raphson steps
-// r <- r (2 - f r) (each step squares the relative error: 2^-24 -> 2^-48 ->
+// r <- r (2 - f r).  The seed, the FP32 reciprocal of f truncated to 24 bits,
+// is within 2^-22 of 1/f; each step squares the relative error (2^-44, then
 // below FP64 rounding).  f > 0, as the distributions of a valid state are.
 __host__ __device__ __forceinline__ double recip_nr(double f);
 // The same with one refinement step: relative error below 2^-46 (1.4e-14).
+// The range is checked on the FP32 value the seed starts from, and the seed
+// (a normal FP32 number there) is widened by integer operations: neither
+// takes the FP64 pipe.
 __host__ __device__ __forceinline__ double recip_nr1(double f)
 {
-    if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
-    const double r = (double)(1.0f / (float)f);
+    const float ff = (float)f;
+    if (!(ff > 1e-30f && ff < 1e30f)) return 1.0 / f;   // outside the FP32 seed's range
+    const double r = widen_normal(1.0f / ff);
     return r * fma(-f, r, 2.0);
 }
 // The same from an FP32 value fs of f formed without an FP64 conversion (the
@@ -1006,13 +1012,14 @@ __host__ __device__ __forceinline__ double recip_nr1(double f)
 __host__ __device__ __forceinline__ double recip_nr1_seeded(double f, float fs)
 {
     if (!(fs > 1e-30f && fs < 1e30f)) return 1.0 / f;   // outside the FP32 seed's range
-    const double r = (double)(1.0f / fs);
+    const double r = widen_normal(1.0f / fs);
     return r * fma(-f, r, 2.0);
 }
 __host__ __device__ __forceinline__ double recip_nr(double f)
 {
-    if (!(f > 1e-30 && f < 1e30)) return 1.0 / f;     // outside the FP32 seed's range
-    double r = (double)(1.0f / (float)f);
+    const float ff = narrow_trunc(f);   // 2^-23: two steps still reach FP64 rounding
+    if (!(ff > 1e-30f && ff < 1e30f)) return 1.0 / f;   // outside the FP32 seed's range
+    double r = widen_normal(1.0f / ff);
     r = r * fma(-f, r, 2.0);
     r = r * fma(-f, r, 2.0);
     return r;
@@ -1030,7 +1037,8 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     double drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const double di = (double)d[i];
+        double di;
+        di = (double)d[i];
         f[i] = L::w(i) + di;
         drho += di;
         j[0] += L::ex(i) * di;
@@ -1099,6 +1107,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
     // Delta_i = f_eq,i - f_i replaces f_eq in its registers; the update, A and
     // the moments take it as it is, and x_i = Delta_i / f_i
     double (&Dl)[L::Q] = fe;
+    // extremes of x through integer order keys (exact; no FP64 comparisons)
     double xmin = 1e300, xmax = -1e300;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -1151,10 +1160,11 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                     pw *= x[i];
                     a[k] += pw;
                 }
-                const float xf = (float)x[i];
-                // f x^6 in FP32; with FP32 storage from the stored deviation,
-                // which needs no FP64 conversion (FP32 rounding of these high
-                // orders stays within the bound above)
+                // x_i and f x^6 in FP32 without FP64 conversions: x_i
+                // truncated to 24 bits by integer operations, f from the
+                // stored deviation with FP32 storage (one more unit in the
+                // last place, within the bound above)
+                const float xf = narrow_trunc(x[i]);
                 float pwf;
                 if constexpr (sizeof(R) == 4) {
                     const float x3 = xf * xf * xf;
@@ -1171,7 +1181,7 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
                 sy = fma(Dl[i], yi * fma(-yi, fma(-yi, fma(-0.25, yi, 1.0 / 3.0), 0.5), 1.0), sy);
             }
 #pragma unroll
-            for (int k = 0; k < kSeriesK - kSeriesK64; ++k) a[kSeriesK64 + 1 + k] = (double)ahi[k];
+            for (int k = 0; k < kSeriesK - kSeriesK64; ++k) a[kSeriesK64 + 1 + k] = widen(ahi[k]);
             // A = sum Delta ln(f_eq/w) - sum Delta log1p(x), with
             // sum Delta ln(f_eq/w) = ln c0 (1 - sum w) + sum Delta log1p(y)
             // (the ln r_a sum e_a Delta terms vanish, see above) and
