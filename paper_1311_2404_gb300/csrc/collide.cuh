@@ -1025,6 +1025,17 @@ __host__ __device__ __forceinline__ double recip_nr(double f)
     return r;
 }
 
+// An FP64 result in the compute type R; to FP32 rounded to nearest on the
+// integer pipes (the value of the conversion instruction).
+template <class R>
+__host__ __device__ __forceinline__ R to_compute(double v)
+{
+    if constexpr (sizeof(R) == 4)
+        return narrow(v);
+    else
+        return (R)v;
+}
+
 // ELBM collision of one node.  d (deviations, compute type R) in/out.
 // Returns the per-node outcome for the counters.
 template <class L, class R>
@@ -1038,7 +1049,10 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         double di;
-        di = (double)d[i];
+        if constexpr (sizeof(R) == 4)
+            di = widen(d[i]);       // exact, on the integer pipes
+        else
+            di = (double)d[i];
         f[i] = L::w(i) + di;
         drho += di;
         j[0] += L::ex(i) * di;
@@ -1255,10 +1269,10 @@ __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const
         elbm_feq<L>(rho, us, p.feq_variant, fs);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)   // f_eq(u + F/rho) - f_eq(u) added
-            d[i] = (R)(fma(ab, Dl[i], f[i] - L::w(i)) + (fs[i] - (f[i] + Dl[i])));
+            d[i] = to_compute<R>(fma(ab, Dl[i], f[i] - L::w(i)) + (fs[i] - (f[i] + Dl[i])));
     } else {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) d[i] = (R)fma(ab, Dl[i], f[i] - L::w(i));
+        for (int i = 0; i < L::Q; ++i) d[i] = to_compute<R>(fma(ab, Dl[i], f[i] - L::w(i)));
     }
     drho_out = (R)drho;
     vout[0] = (R)(u[0] + 0.5 * p.F[0] * irho);

@@ -1,13 +1,13 @@
-// Conversions between binary32 and binary64 and an ordering of binary64
-// values, done with integer operations on the IEEE 754 encodings.
+// Conversions between binary32 and binary64 done with integer operations on
+// the IEEE 754 encodings.
 //
 // The ELBM collision is bound by the FP64 pipe, which also executes the
-// FP32 <-> FP64 conversion instructions and FP64 comparisons; the integer
-// pipes beside it are nearly idle.  These helpers move that work there.
+// FP32 <-> FP64 conversion instructions; the integer pipes beside it are
+// nearly idle.  These helpers move that work there.
 // Encodings: binary32 = 1 sign bit, 8 exponent bits biased by 127, 23
 // fraction bits; binary64 = 1, 11 biased by 1023, 52.  Each function
 // states its domain and how its result relates to the conversion
-// instruction or the comparison it replaces.
+// instruction it replaces.
 //
 // The header also compiles as plain C++ (no CUDA), so that host tests can
 // check these functions against the C conversions.
@@ -108,20 +108,32 @@ LBM_BITS_FN float narrow_trunc(double x)
     return f32_from_bits(sign | r);
 }
 
-// A signed integer that orders binary64 values as < does (for non-NaN x;
-// -0 sorts just below +0): the encoding itself for x >= +0, and the
-// encoding with every non-sign bit flipped for negative x.
-LBM_BITS_FN int64_t f64_order_key(double x)
+// (float)x, rounded to nearest with ties to even, for every x (the value
+// of the conversion instruction; NaN gives a NaN).  For a normal result the
+// 52-bit fraction is rounded at bit 29: adding 2^28 - 1 plus the lowest kept
+// bit and dropping 29 bits, where a carry steps the exponent (up to
+// infinity, which is then the correctly rounded result); the exponent is
+// rebiased by -896.  For a subnormal result (|x| < 2^-126) the significand
+// 2^52 + fraction is shifted right by 926 - e (e the biased exponent) and
+// rounded the same way by its remainder; below 2^-150 that is zero.
+LBM_BITS_FN float narrow(double x)
 {
-    const int64_t b = (int64_t)f64_bits(x);
-    return b ^ (int64_t)((uint64_t)(b >> 63) >> 1);
-}
-
-// The value whose order key is k (the inverse of f64_order_key).
-LBM_BITS_FN double f64_from_order_key(int64_t k)
-{
-    const uint64_t b = (uint64_t)(k ^ (int64_t)((uint64_t)(k >> 63) >> 1));
-    return f64_from_words((uint32_t)(b >> 32), (uint32_t)b);
+    const uint64_t b = f64_bits(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
+    const uint32_t e = (uint32_t)(mag >> 52);
+    const uint32_t rn = (uint32_t)((mag + 0x0FFFFFFFull + ((mag >> 29) & 1u)) >> 29) - (896u << 23);
+    const uint32_t sh = e >= 873u ? 926u - e : 54u;       // 30..53 for subnormal results
+    const uint32_t s = sh > 53u ? 53u : sh;
+    const uint64_t sig = (mag & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const uint64_t q = sig >> s;
+    const uint64_t rem = sig & ((1ull << s) - 1u);
+    const uint64_t half = 1ull << (s - 1u);
+    const uint32_t rs = (uint32_t)q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+    const uint32_t sub = (sh > 53u || e == 0u) ? 0u : rs;
+    const bool nan = e == 2047u && (mag & 0xFFFFFFFFFFFFFull) != 0u;
+    const uint32_t r = e >= 897u ? (e >= 1151u ? (nan ? 0x7FC00000u : 0x7F800000u) : rn) : sub;
+    return f32_from_bits(sign | r);
 }
 
 }  // namespace lbm
