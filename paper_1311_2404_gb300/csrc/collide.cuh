@@ -826,27 +826,29 @@ struct SeriesEval {
 // moments a_k = sum f x^k (k = 2..6), the extremes of x and A:
 // t_k = (a_k / rho) / eps^k (k = 3..6), eps = sqrt(a_2 / rho),
 // max x / eps, min x / eps, A / a_2.
+// The features are inputs of an FP32 network and are stored as FP32 pairs,
+// so they are formed in FP32 from the FP64 moments rounded to FP32.
 __host__ __device__ __forceinline__ void elbm_features(const double (&ak)[7], double xmax,
                                                        double xmin, double rho, double A,
-                                                       double (&feat)[8])
+                                                       float (&feat)[8])
 {
-    const double eps = sqrt(ak[2] / rho);
-    const double ie = 1.0 / eps;
-    const double ie2 = ie * ie;
-    const double ir = 1.0 / rho;
-    feat[0] = ak[3] * ir * ie2 * ie;
-    feat[1] = ak[4] * ir * ie2 * ie2;
-    feat[2] = ak[5] * ir * ie2 * ie2 * ie;
-    feat[3] = ak[6] * ir * ie2 * ie2 * ie2;
+    const float a2 = narrow(ak[2]), ir = 1.0f / narrow(rho);
+    const float eps = sqrtf(a2 * ir);
+    const float ie = 1.0f / eps;
+    const float ie2 = ie * ie;
+    feat[0] = narrow(ak[3]) * ir * ie2 * ie;
+    feat[1] = narrow(ak[4]) * ir * ie2 * ie2;
+    feat[2] = narrow(ak[5]) * ir * ie2 * ie2 * ie;
+    feat[3] = narrow(ak[6]) * ir * ie2 * ie2 * ie2;
     feat[4] = eps;
-    feat[5] = xmax * ie;
-    feat[6] = xmin * ie;
-    feat[7] = A / ak[2];
+    feat[5] = narrow(xmax) * ie;
+    feat[6] = narrow(xmin) * ie;
+    feat[7] = narrow(A) / a2;
 }
 
 // MLP 8 -> 32 -> 32 -> 1 (tanh), parameters in shared memory (FP32 holding
 // BF16-rounded weights), FP32 accumulation.  Returns the raw output.
-__host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, const double (&feat)[8])
+__host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, const float (&feat)[8])
 {
     const float* mean = P;
     const float* istd = P + 8;
@@ -858,7 +860,7 @@ __host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, 
     const float* b3 = W3 + 32;
     float z[8], h1[32];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) z[k] = ((float)feat[k] - mean[k]) * istd[k];
+    for (int k = 0; k < 8; ++k) z[k] = (feat[k] - mean[k]) * istd[k];
 #pragma unroll
     for (int o = 0; o < 32; ++o) {
         float s = b1[o];
@@ -893,7 +895,7 @@ __host__ __device__ __forceinline__ float mlp_eval(const float* __restrict__ P, 
 // Below a_2 = 1e-30 (FP32's normal range ends at 1.2e-38) the guess is 2.
 __host__ __device__ __forceinline__ double alpha_guess(const StepParams& p, const float* smlp,
                                                        const double (&ak)[7], double A1,
-                                                       const double (&feat)[8])
+                                                       const float (&feat)[8])
 {
     const float a2 = (float)ak[2];
     if (!(a2 > 1e-30f)) return 2.0;
@@ -1041,7 +1043,7 @@ __host__ __device__ __forceinline__ R to_compute(double v)
 template <class L, class R>
 __host__ __device__ __forceinline__ AlphaResult elbm_collide(R (&d)[L::Q], const StepParams& p,
                                                              const float* smlp, R& drho_out,
-                                                             R (&vout)[3], double (&feat)[8],
+                                                             R (&vout)[3], float (&feat)[8],
                                                              bool& have_feat)
 {
     double f[L::Q], x[L::Q], fe[L::Q], y[L::Q];

@@ -132,7 +132,7 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
                            sel<R>(p.F_f[0], p.F[0]), sel<R>(p.F_f[1], p.F[1]),
                            sel<R>(p.F_f[2], p.F[2]));
         R drho, v[3];
-        double feat[8];
+        float feat[8];
         bool have_feat = false;
         AlphaResult ar{2.0, 0, -1};
         if (MODEL == MODEL_BGK) {
@@ -186,7 +186,7 @@ __device__ __forceinline__ void stream_collide_body(const StepParams& p)
             const int slot = atomicAdd(p.pairs_count, 1);
             if (slot < p.pairs_cap) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) p.pairs_X[(size_t)slot * 8 + k] = (float)feat[k];
+                for (int k = 0; k < 8; ++k) p.pairs_X[(size_t)slot * 8 + k] = feat[k];
                 p.pairs_y[slot] = ar.alpha;
             }
         }
