@@ -141,17 +141,18 @@ def source_sha(names=KERNEL_SOURCES):
     return h.hexdigest()[:16]
 
 
-def fp64_inst_for(alpha, dtype):
+def fp64_inst_for(alpha, dtype, nodes):
     """FP64-pipe warp instructions per node of the ELBM kernel from the
     committed ncu record (profiles/fp64_elbm.json), if the ELBM sources are
-    unchanged since that capture; else None."""
+    unchanged since that capture and the workload has the record's node
+    count (the count per node depends on the field); else None."""
     path = os.path.join(ROOT, "profiles", "fp64_elbm.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     e = d.get(f"elbm:{alpha}:{dtype}")
-    if not e or e.get("source_sha") != source_sha(ELBM_SOURCES):
+    if not e or e.get("source_sha") != source_sha(ELBM_SOURCES) or e.get("nodes") != nodes:
         return None
     return float(e["fp64_warp_inst_per_node"])
 
@@ -748,7 +749,7 @@ def run_ours(args):
         # warp-instruction rate, its work the ncu count of FP64-pipe
         # instructions per node; the HBM figures stay beside it
         w_rate, f_rate = lbm.lbm_probe_fp64_rate(stream.cuda_stream)
-        ipn = fp64_inst_for(args.alpha, args.dtype)
+        ipn = fp64_inst_for(args.alpha, args.dtype, nodes)
         hbm = line["roofline"]
         line["roofline"] = {
             "bound": "fp64", "unit": "G warp-inst/s",
