@@ -163,16 +163,17 @@ def traffic_key(workload, dtype, model, lattice):
     return f"{workload}:{dtype}:{MODEL_NAME[model]}:{LATTICE_NAME[lattice]}"
 
 
-def traffic_for(workload, dtype, model, lattice):
+def traffic_for(workload, dtype, model, lattice, nodes):
     """DRAM bytes per launch from the committed ncu summary for this kernel,
-    if its sources are unchanged since that capture; else None."""
+    if its sources are unchanged since that capture and the workload has the
+    captured node count; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     e = d.get(traffic_key(workload, dtype, model, lattice))
-    if not e or e.get("source_sha") != source_sha():
+    if not e or e.get("source_sha") != source_sha() or e.get("nodes") != nodes:
         return None
     return float(e["bytes_per_launch"])
 
@@ -696,7 +697,7 @@ def run_ours(args):
     alg = algorithmic_bytes(nodes, fluid, bpn, 4)
     achieved = alg / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(args.workload, args.dtype, spec["model"], spec["lattice"])
+    traffic = traffic_for(args.workload, args.dtype, spec["model"], spec["lattice"], nodes)
     line = {
         "metric": "D3Q19 GLUPS & % HBM roofline; FP16/learned vs plain FP32 at fixed error",
         "value": round(glups, 4),
